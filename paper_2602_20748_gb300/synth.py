@@ -1,0 +1,204 @@
+"""Seeded synthetic inputs: labeled graphs, source samples and query strings.
+
+This module holds no RPQ arithmetic; it only draws inputs.  Both the CUDA
+path and the CPU oracle consume what it returns, so the two sides always see
+identical inputs.  Random numbers come from numpy's PCG64 bit generator
+through ``random_raw`` (a stable bit stream), never from distribution
+methods whose algorithms may change between numpy versions.
+
+Workloads (stand-ins for the paper's LDBC SNB / StackOverflow datasets,
+which are not available; see Section 7.1 of the paper for those):
+
+* ``er_graph``   -- directed Erdos-Renyi G(n, m): m distinct ordered pairs
+  uniform over n x n (self-loops allowed), edge labels uniform.
+* ``rmat_graph`` -- R-MAT with quadrant probabilities (a, b, c, d), a seeded
+  Graph500-style vertex permutation, i.i.d. Zipf(s) edge labels.  Duplicate
+  (src, dst, label) triples are left in; loading removes them.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+BASE_SEED = 0x260220748
+
+__all__ = [
+    "BASE_SEED",
+    "zipf_probs",
+    "er_graph",
+    "rmat_graph",
+    "vertex_labels",
+    "sample_sources",
+    "random_regex",
+    "random_graph",
+]
+
+
+def _raw(seed: int, n: int) -> np.ndarray:
+    return np.random.Generator(np.random.PCG64(seed)).bit_generator.random_raw(n).astype(np.uint64)
+
+
+class _Stream:
+    """Chunked access to one PCG64 raw stream."""
+
+    def __init__(self, seed: int):
+        self.bg = np.random.PCG64(seed)
+
+    def raw(self, n: int) -> np.ndarray:
+        return self.bg.random_raw(n).astype(np.uint64)
+
+    def unit(self, n: int) -> np.ndarray:
+        """Uniform doubles in [0, 1) from the top 53 bits."""
+        return (self.raw(n) >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+
+    def below(self, n: int, k: int) -> np.ndarray:
+        """Integers in [0, k) by the multiply-shift map of the top 32 bits."""
+        hi = self.raw(n) >> np.uint64(32)
+        return ((hi * np.uint64(k)) >> np.uint64(32)).astype(np.int64)
+
+
+def zipf_probs(n_labels: int, s: float) -> np.ndarray:
+    """P(label i) proportional to 1 / (i + 1)^s, i = 0 .. n_labels - 1."""
+    w = 1.0 / np.arange(1, n_labels + 1, dtype=np.float64) ** s
+    return w / w.sum()
+
+
+def _zipf_labels(stream: _Stream, m: int, n_labels: int, s: float) -> np.ndarray:
+    cdf = np.cumsum(zipf_probs(n_labels, s))
+    cdf[-1] = 1.0
+    lab = np.searchsorted(cdf, stream.unit(m), side="right")
+    return np.minimum(lab, n_labels - 1).astype(np.uint16)
+
+
+def er_graph(n: int, m: int, n_labels: int, seed: int):
+    """m distinct ordered pairs uniform over n x n, labels uniform."""
+    if m > n * n:
+        raise ValueError("m exceeds n^2")
+    st = _Stream(seed)
+    chosen = np.empty(0, dtype=np.int64)
+    while len(chosen) < m:
+        cand = st.below(2 * (m - len(chosen)) + 16, n * n)
+        merged = np.concatenate([chosen, cand])
+        _, first = np.unique(merged, return_index=True)
+        first.sort()
+        chosen = merged[first][:m]
+    src = (chosen // n).astype(np.uint32)
+    dst = (chosen % n).astype(np.uint32)
+    lab = st.below(m, n_labels).astype(np.uint16)
+    return src, dst, lab
+
+
+def rmat_graph(scale: int, n_edges: int, n_labels: int, zipf_s: float, seed: int,
+               probs=(0.57, 0.19, 0.19, 0.05), permute: bool = True, chunk: int = 1 << 22):
+    """R-MAT edges (src, dst, label) over 2^scale vertices."""
+    a, b, c, _ = probs
+    t1 = np.uint64(int(a * 2**32))
+    t2 = np.uint64(int((a + b) * 2**32))
+    t3 = np.uint64(int((a + b + c) * 2**32))
+    st = _Stream(seed)
+    src = np.empty(n_edges, dtype=np.uint32)
+    dst = np.empty(n_edges, dtype=np.uint32)
+    words = (scale + 1) // 2
+    lo_mask = np.uint64(0xFFFFFFFF)
+    for c0 in range(0, n_edges, chunk):
+        k = min(chunk, n_edges - c0)
+        s = np.zeros(k, dtype=np.uint32)
+        d = np.zeros(k, dtype=np.uint32)
+        level = 0
+        for _ in range(words):
+            r = st.raw(k)
+            for u in (r >> np.uint64(32), r & lo_mask):
+                if level == scale:
+                    break
+                bit = np.uint32(1 << level)
+                # quadrants: u < a -> (0,0); < a+b -> (0,1); < a+b+c -> (1,0); else (1,1)
+                sb = u >= t2
+                db = ((u >= t1) & (u < t2)) | (u >= t3)
+                s |= sb.astype(np.uint32) * bit
+                d |= db.astype(np.uint32) * bit
+                level += 1
+        src[c0:c0 + k] = s
+        dst[c0:c0 + k] = d
+    if permute:
+        perm = np.argsort(_raw(seed ^ 0x5EED_0001, 1 << scale), kind="stable").astype(np.uint32)
+        src = perm[src]
+        dst = perm[dst]
+    lab = _zipf_labels(_Stream(seed ^ 0x5EED_0002), n_edges, n_labels, zipf_s)
+    return src, dst, lab
+
+
+def vertex_labels(n: int, n_vlabels: int, seed: int) -> np.ndarray:
+    return _Stream(seed ^ 0x5EED_0003).below(n, n_vlabels).astype(np.uint8)
+
+
+def sample_sources(n_vertices: int, src: np.ndarray, seed: int, n_strat: int = 256, n_hubs: int = 128,
+                   n_uniform: int = 128) -> np.ndarray:
+    """Seeded source sample: ``n_strat`` stratified by out-degree decile (over
+    vertices with out-degree > 0), the ``n_hubs`` highest out-degree vertices
+    and ``n_uniform`` uniform vertices.  Sorted, distinct."""
+    deg = np.bincount(np.asarray(src, dtype=np.int64), minlength=n_vertices)
+    st = _Stream(seed ^ 0x5EED_0004)
+    picked = []
+    nz = np.nonzero(deg)[0]
+    if len(nz):
+        order = nz[np.argsort(deg[nz], kind="stable")]
+        deciles = np.array_split(order, 10)
+        per = max(1, n_strat // 10)
+        for dec in deciles:
+            if len(dec):
+                picked.append(dec[st.below(per, len(dec))])
+    hubs = np.argsort(-deg, kind="stable")[:n_hubs]
+    picked.append(hubs)
+    picked.append(st.below(n_uniform, n_vertices))
+    return np.unique(np.concatenate(picked)).astype(np.uint32)
+
+
+def random_graph(n: int, m: int, n_labels: int, seed: int):
+    """Small multigraph for brute-force checks: m uniform (src, dst, label)
+    draws (duplicates and self-loops possible)."""
+    st = _Stream(seed)
+    return (st.below(m, n).astype(np.uint32), st.below(m, n).astype(np.uint32),
+            st.below(m, n_labels).astype(np.uint16))
+
+
+def random_regex(seed: int, n_labels: int, max_symbols: int = 5, p_star: float = 0.35,
+                 p_alt: float = 0.25) -> str:
+    """A random regex over single-letter labels: 1..max_symbols symbols, each
+    optionally starred / plussed / optional, adjacent pairs sometimes grouped
+    as an alternation, an occasional outer group with a postfix."""
+    st = _Stream(seed)
+    u = st.unit(64)
+    idx = [0]
+
+    def nxt():
+        x = u[idx[0] % 64]
+        idx[0] += 1
+        return x
+
+    k = 1 + int(nxt() * max_symbols)
+    parts = []
+    i = 0
+    while i < k:
+        sym = chr(ord("a") + int(nxt() * n_labels))
+        if i + 1 < k and nxt() < p_alt:
+            sym2 = chr(ord("a") + int(nxt() * n_labels))
+            tok = f"({sym}|{sym2})"
+            i += 2
+        else:
+            tok = sym
+            i += 1
+        r = nxt()
+        if r < p_star:
+            tok += "*"
+        elif r < p_star + 0.1:
+            tok += "+"
+        elif r < p_star + 0.18:
+            tok += "?"
+        parts.append(tok)
+    text = ".".join(parts)
+    r = nxt()
+    if len(parts) > 1 and r < 0.15:
+        text = f"({text})*"
+    elif len(parts) > 1 and r < 0.22:
+        text = f"({text})+"
+    return text
