@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Benchmark of all-pairs RPQ evaluation on the large R-MAT workload.
+
+Workload: R-MAT scale 20 (1,048,576 vertices), 2^24 generated edges with
+(a, b, c, d) = (0.57, 0.19, 0.19, 0.05), 8 edge labels Zipf(s = 1.2), seeded;
+queries a*, (a|b)+.c, a.b*.c, (a.b)*, all-pairs.  One step evaluates all
+four queries from one batch of consecutive start vertices (a slice of the
+all-pairs job) and materializes the distinct (src, dst) rows on the device.
+Steps take successive batches; with N ranks, rank r takes every N-th batch
+(the start vertices partition the job; no data-path collective).
+
+Metric: product-edge relaxations per second (the work of a per-start-vertex
+traversal of G x minimal DFA, counted exactly by the engine and checked
+against the CPU oracle in the tests), plus result pairs per second.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import signal
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "rmat20-allpairs"
+QUERIES = ["a*", "(a|b)+·c", "a·b*·c", "(a·b)*"]
+SCALE = 20
+N_EDGES = 1 << 24
+N_LABELS = 8
+ZIPF_S = 1.2
+METRIC = "product_edges_per_s"
+UNIT = "product-edges/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=4096, help="start vertices per step")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def make_graph():
+    from paper_2602_20748_gb300 import synth
+
+    src, dst, lab = synth.rmat_graph(SCALE, N_EDGES, N_LABELS, ZIPF_S, seed=synth.BASE_SEED + 1)
+    return 1 << SCALE, src, dst, lab
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.send_signal(signal.SIGTERM)
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                t = [x.strip() for x in line.split(",")]
+                if len(t) >= 9:
+                    rows.append(t)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def algorithmic_bytes(st: dict) -> float:
+    """Bytes the traversal must move for the work it did (per launch sums):
+    per top-down edge relaxation a 4-byte column id and the target's visited
+    word (8 * NW bytes); per adjacency row opened the two 4-byte offsets; per
+    lane-group product vertex discovered its 8-byte list entry; per bottom-up
+    in-edge a column id and one gathered frontier word; per bottom-up
+    (vertex, state) word examined its visited word."""
+    nw = st["lane_words"]
+    return ((4 + 8 * nw) * st["group_edges"] + 8 * st["group_rows"] + 8 * st["group_vertices"]
+            + (4 + 8 * nw) * st["pull_edges"] + 8 * nw * st["pull_vertices"])
+
+
+def cpu_oracle_sample(n, src, dst, lab, seconds: float, batch0: int):
+    """Times the CPU oracle (as it stands) on start vertices of the workload,
+    in chunks of one source per host core, until `seconds` have passed."""
+    import oracle
+
+    og = oracle.Graph(n, N_LABELS, src, dst, lab)
+    cores = os.cpu_count() or 1
+    W = 0
+    used = 0
+    t_total = 0.0
+    done = 0
+    per_query = []
+    rng = np.random.Generator(np.random.PCG64(batch0))
+    for regex in QUERIES:
+        t_q = 0.0
+        while t_q < seconds / len(QUERIES):
+            srcs = np.sort(rng.integers(0, n, cores)).astype(np.uint32)
+            t0 = time.perf_counter()
+            r = oracle.rpq(og, regex, sources=srcs, threads=cores)
+            dt = time.perf_counter() - t0
+            t_q += dt
+            W += r.W
+            done += len(srcs)
+            used = max(used, r.threads)
+        per_query.append(regex)
+        t_total += t_q
+    return W, t_total, used, done
+
+
+def reference_arm(args, rank: int, world: int):
+    if rank != 0:
+        return 0
+    n, src, dst, lab = make_graph()
+    # each step: a bounded sample of the same workload on the host cores
+    per_step = max(2.0, min(12.0, 150.0 / max(1, args.steps + args.warmup)))
+    for i in range(args.warmup):
+        cpu_oracle_sample(n, src, dst, lab, per_step / 2, 1000 + i)
+    Ws, ts, cores, srcs = 0, 0.0, 1, 0
+    for i in range(args.steps):
+        W, t, cores, k = cpu_oracle_sample(n, src, dst, lab, per_step, 2000 + i)
+        Ws += W
+        ts += t
+        srcs += k
+    value = Ws / ts
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * ts / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "queries": QUERIES, "vertices": n, "generated_edges": N_EDGES,
+                   "labels": N_LABELS, "zipf_s": ZIPF_S},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{srcs} random start vertices over the 4 queries, {ts:.1f} s of CPU oracle time"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def ours(args, rank: int, world: int, local_rank: int):
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_2602_20748_gb300 import rpq
+
+    n, src, dst, lab = make_graph()
+    ctx = rpq.Context(device=local_rank)
+    t0 = time.perf_counter()
+    g = rpq.load_graph(ctx, n, N_LABELS, src, dst, lab)
+    torch.cuda.synchronize()
+    load_s = time.perf_counter() - t0
+    _, _, m_unique = g.info()
+    qs = [rpq.compile_rpq(ctx, r) for r in QUERIES]
+    B = args.batch
+    n_batches = n // B
+
+    def batch_of(step_index: int) -> int:
+        return (step_index * world + rank) % n_batches
+
+    def run_step(step_index: int, acc: dict):
+        b0 = batch_of(step_index) * B
+        for q in qs:
+            r = rpq.run_rpq_range(ctx, g, q, b0, b0 + B, rpq.RPQ_MATERIALIZE)
+            st = rpq.result_stats(r)
+            cnt = rpq.result_info(r)[0]
+            acc["W"] += st["product_edges"]
+            acc["pairs"] += cnt
+            acc["bfs_ms"] += st["bfs_ms"]
+            acc["bfs_launches"] += st["bfs_launches"]
+            acc["launches"] += st["launches"]
+            acc["alg_bytes"] += algorithmic_bytes(st)
+            for k in ("push_levels", "pull_levels", "levels"):
+                acc[k] += st[k]
+            r.free()
+
+    def new_acc():
+        return dict(W=0, pairs=0, bfs_ms=0.0, bfs_launches=0, launches=0, alg_bytes=0.0, push_levels=0,
+                    pull_levels=0, levels=0)
+
+    for i in range(args.warmup):
+        run_step(i, new_acc())
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    acc = new_acc()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for i in range(args.steps):
+        run_step(args.warmup + i, acc)
+    ev1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    W_all, pairs_all, ms_max = acc["W"], acc["pairs"], ms
+    if dist:
+        t = torch.tensor([acc["W"], acc["pairs"]], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t)
+        W_all, pairs_all = int(t[0].item()), int(t[1].item())
+        tm = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        ms_max = float(tm.item())
+        dist.barrier()
+    value = W_all / (ms_max / 1000.0)
+
+    # end to end through the public API: host source list in, rows out to pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        buf = None
+        h2d = d2h = 0
+        W_e2e = 0
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            b0 = batch_of(args.warmup + args.steps + i) * B
+            sources = np.arange(b0, b0 + B, dtype=np.uint32)
+            for q in qs:
+                r = rpq.run_rpq(ctx, g, q, sources, rpq.RPQ_MATERIALIZE)
+                cnt = rpq.result_info(r)[0]
+                if buf is None or buf.numel() < 2 * cnt:
+                    buf = torch.empty(max(2 * cnt, 1 << 20), dtype=torch.int32, pin_memory=True)
+                rows = rpq.fetch_pairs(r, 0, cnt, out=buf.numpy().view(np.uint32))
+                assert len(rows) == cnt
+                W_e2e += rpq.result_stats(r)["product_edges"]
+                h2d += sources.nbytes
+                d2h += rows.nbytes
+                r.free()
+        t_e2e = time.perf_counter() - t0
+        if dist:
+            tt = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_e2e = float(tt.item())
+            tw = torch.tensor([W_e2e], dtype=torch.float64, device="cuda")
+            dist.all_reduce(tw)
+            W_e2e = int(tw.item())
+        e2e = {"value": W_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
+               "d2h_bytes_per_step": d2h // args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        Wc, tc, cores, k = cpu_oracle_sample(n, src, dst, lab, args.cpu_seconds, 7)
+        cpu = {"value": Wc / tc, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{k} random start vertices over the 4 queries ({tc:.1f} s of oracle time)"}
+
+    peak, peak_kind = peaks()
+    achieved = acc["alg_bytes"] / max(1, acc["bfs_launches"]) / (acc["bfs_ms"] / max(1, acc["bfs_launches"]) / 1e3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "msbfs_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            with open(tpath) as f:
+                traffic = json.load(f).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "queries": QUERIES, "vertices": n, "generated_edges": N_EDGES,
+                       "distinct_edges": m_unique, "labels": N_LABELS, "zipf_s": ZIPF_S,
+                       "batch_sources_per_step": B, "parallelism": f"sources/{world}",
+                       "l2": "inputs larger than L2 (graph CSR ~200 MB, traversal state ~4.6 GB per launch)",
+                       "graph_load_s": round(load_s, 3)},
+            "result_pairs_per_s": pairs_all / (ms_max / 1000.0),
+            "result_pairs": pairs_all,
+            "product_edges": W_all,
+            "levels": {"push": acc["push_levels"], "pull": acc["pull_levels"]},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": "msbfs_kernel<4>",
+                         "peak_kind": peak_kind, "bfs_ms": acc["bfs_ms"], "bfs_launches": acc["bfs_launches"]},
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": acc["launches"],
+        }
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+    return ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,236 @@
+/*
+ * rpq.h -- C ABI of the GB300 regular path query engine.
+ *
+ * The engine evaluates regular path queries (RPQs) and conjunctive regular
+ * path queries (CRPQs) over a labeled directed graph resident in GPU memory,
+ * following the problem statement of cuRPQ (arXiv 2602.20748):
+ *
+ *   * Data graph G = (V, E, L), directed, with vertex and edge labels
+ *     (Section 2.1).  Vertices are 0 .. n_vertices-1; an edge is a
+ *     (src, dst, label) triple; identical triples count once; self-loops are
+ *     kept; edges with the same endpoints and different labels are distinct.
+ *   * RPQ x -rho-> y (Definition 1): the set of distinct pairs (x, y) joined
+ *     by a directed path whose label word is in L(rho).  Paths of any length,
+ *     including length 0 when the empty word is in L(rho) (then (v, v) is a
+ *     result for every start vertex v).
+ *   * CRPQ (Definition 2): all maps f from query variables to vertices such
+ *     that labeled variables map to vertices with that label and every atom
+ *     x -rho-> y holds for (f(x), f(y)).  Homomorphism (not injective)
+ *     semantics, set results.
+ *
+ * Evaluation is the automata-based method of Section 2.2: a traversal of the
+ * product of G with the query automaton (here a minimal DFA), with a visited
+ * set per start vertex.  All traversal, deduplication, emission and join work
+ * runs in CUDA kernels on the device; the host parses the regex and drives
+ * batches.
+ *
+ * Conventions for every function:
+ *   * Return RPQ_OK (0) on success or a negative RPQ_ERR_* code.  On error
+ *     the out-pointer is left NULL and rpq_last_error(ctx) describes the
+ *     failure (for PARSE errors it contains the byte position).
+ *   * Input arrays are host pointers, read during the call and never kept:
+ *     the caller keeps ownership.  Handles (rpq_graph, rpq_query, rpq_result)
+ *     are owned by the caller after creation and must be released with the
+ *     matching free_* function before rpq_destroy of their context.
+ *   * Result rows are distinct and sorted ascending lexicographically as
+ *     unsigned 32-bit values: (src, dst) for an RPQ, the variables in
+ *     declaration order for a CRPQ.
+ *   * A context is not thread-safe; calls on one context are serialized by
+ *     the caller.  All device work of a context is ordered on its stream.
+ */
+#ifndef GB300_RPQ_H
+#define GB300_RPQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes -------------------------------------------------------- */
+#define RPQ_OK 0
+#define RPQ_ERR_INVALID_ARG -1   /* NULL pointer, id out of range, bad size  */
+#define RPQ_ERR_PARSE -2         /* regex syntax error                       */
+#define RPQ_ERR_UNKNOWN_LABEL -3 /* regex names a label not in the table     */
+#define RPQ_ERR_TOO_COMPLEX -4   /* automaton beyond the engine's limits     */
+#define RPQ_ERR_OUT_OF_BUDGET -5 /* device memory budget exceeded            */
+#define RPQ_ERR_CUDA -6          /* a CUDA runtime call failed               */
+#define RPQ_ERR_TIMEOUT -7       /* a device-side wait ran out of time       */
+#define RPQ_ERR_NO_DEVICE -8     /* context has no GPU (host-only context)   */
+
+/* ---- limits ------------------------------------------------------------- */
+#define RPQ_MAX_LABELS 64      /* edge labels per graph                      */
+#define RPQ_MAX_STATES 32      /* states of the minimal DFA of one regex     */
+#define RPQ_MAX_POSITIONS 63   /* label occurrences in one regex             */
+#define RPQ_MAX_TRANSITIONS 256
+#define RPQ_MAX_VARS 8         /* CRPQ variables                             */
+#define RPQ_MAX_ATOMS 16       /* CRPQ atoms                                 */
+
+/* ---- flags for run_rpq / run_rpq_range / run_crpq ------------------------ */
+#define RPQ_MATERIALIZE 0x1u   /* keep result rows on the device (fetch_pairs) */
+#define RPQ_COUNT_ONLY 0x2u    /* count rows and digest them; keep no rows    */
+#define RPQ_FORCE_PUSH 0x100u  /* every level expands top-down (testing)      */
+#define RPQ_FORCE_PULL 0x200u  /* every level expands bottom-up (testing)     */
+
+typedef struct rpq_ctx rpq_ctx;
+typedef struct rpq_graph rpq_graph;
+typedef struct rpq_query rpq_query;
+typedef struct rpq_result rpq_result;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Creates a context on CUDA device `device`.  `mem_budget_bytes` caps the
+ * device memory the context allocates for graphs, traversal workspace and
+ * results (0: 90% of the device memory free at creation).  `cuda_stream` is
+ * a cudaStream_t on that device on which all work is issued (NULL: the
+ * legacy default stream).  device = -1 creates a host-only context on which
+ * only compile_rpq / query_info work (for tooling without a GPU).
+ * Errors: INVALID_ARG (out == NULL), CUDA (device unavailable). */
+int rpq_create(rpq_ctx **out, int device, uint64_t mem_budget_bytes, void *cuda_stream);
+
+/* Waits for the context's stream and releases its workspace.  Handles made
+ * with the context must have been freed.  NULL is ignored. */
+void rpq_destroy(rpq_ctx *ctx);
+
+/* Text of the last error on this context ("" if none).  Valid until the next
+ * call on the context.  ctx == NULL gives the last error of rpq_create. */
+const char *rpq_last_error(const rpq_ctx *ctx);
+
+/* Replaces the stream all later work is issued on (NULL: default stream). */
+int rpq_set_stream(rpq_ctx *ctx, void *cuda_stream);
+
+/* ---- graph store (Section 2.1 data graph; Section 2.4 keeps one grid per
+ *      edge label -- here one CSR per edge label) ----------------------------- */
+
+/* Copies n_edges (src[i], dst[i], label[i]) triples to the device, removes
+ * identical triples and builds per-label out- and in-adjacency (CSR, 32-bit
+ * ids) resident in device memory.  vertex_label (n_vertices bytes) may be
+ * NULL.  Requires n_vertices < 2^31, n_labels in 1 .. RPQ_MAX_LABELS,
+ * n_edges < 2^32; every id and label in range.
+ * Errors: INVALID_ARG, OUT_OF_BUDGET, CUDA. */
+int load_graph(rpq_ctx *ctx, uint32_t n_vertices, uint32_t n_labels, uint64_t n_edges, const uint32_t *src,
+               const uint32_t *dst, const uint16_t *label, const uint8_t *vertex_label, rpq_graph **out);
+
+/* Sizes of a loaded graph; n_edges counts distinct triples.  Any out pointer
+ * may be NULL. */
+int graph_info(const rpq_graph *g, uint32_t *n_vertices, uint32_t *n_labels, uint64_t *n_edges);
+
+void free_graph(rpq_graph *g);
+
+/* ---- query compilation (Section 2.2 automata-based plan; Section 4.1 uses the
+ *      minimal DFA of the expression) --------------------------------------- */
+
+/* Parses `regex` and builds its minimal DFA on the host.
+ * Syntax: '|' alternation, postfix '*', '+', '?', concatenation by '.',
+ * U+00B7 (middle dot, UTF-8) or juxtaposition, parentheses, blanks ignored.
+ * With label_names == NULL a label is one lowercase letter, 'a' = 0 ...
+ * 'z' = 25.  Otherwise a label is a maximal identifier [A-Za-z0-9_]+ whose
+ * index in label_names[0 .. n_names-1] is its label id.  Label ids at or
+ * above a graph's n_labels are legal and match no edge of that graph.
+ * Errors: INVALID_ARG, PARSE, UNKNOWN_LABEL, TOO_COMPLEX (more than
+ * RPQ_MAX_POSITIONS label occurrences, RPQ_MAX_STATES DFA states, or
+ * RPQ_MAX_TRANSITIONS transitions, or a label id >= RPQ_MAX_LABELS). */
+int compile_rpq(rpq_ctx *ctx, const char *regex, const char *const *label_names, uint32_t n_names,
+                rpq_query **out);
+
+/* The compiled minimal DFA: state 0 is the start state; bit q of *final_mask
+ * marks accepting states; next[q * n_labels_out + l] is the target of label l
+ * from state q or -1.  `next` may be NULL (then only sizes are returned); it
+ * must hold n_states * n_labels_out entries, where n_labels_out = (largest
+ * label id used) + 1.  Any other out pointer may be NULL. */
+int query_info(const rpq_query *q, uint32_t *n_states, uint32_t *n_labels_out, uint64_t *final_mask,
+               int32_t *next);
+
+void free_query(rpq_query *q);
+
+/* ---- RPQ evaluation (Definition 1; Section 2.2 product-graph traversal) ---- */
+
+/* Single-source / multi-source RPQ: the result pairs (s, y) for every s in
+ * sources[0 .. n_sources-1] (duplicates ignored).  sources == NULL with
+ * n_sources == 0 means every vertex (all-pairs).  flags: exactly one of
+ * RPQ_MATERIALIZE or RPQ_COUNT_ONLY, optionally one RPQ_FORCE_* (testing).
+ * Errors: INVALID_ARG (source out of range, bad flags), OUT_OF_BUDGET,
+ * CUDA, TIMEOUT. */
+int run_rpq(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, const uint32_t *sources, uint32_t n_sources,
+            uint32_t flags, rpq_result **out);
+
+/* All-pairs restricted to the start vertices src_begin <= s < src_end (one
+ * batch of an all-pairs evaluation; batches in increasing order concatenate
+ * to the sorted all-pairs result).  Same flags and errors as run_rpq. */
+int run_rpq_range(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, uint32_t src_begin, uint32_t src_end,
+                  uint32_t flags, rpq_result **out);
+
+/* ---- CRPQ evaluation (Definition 2; Section 6.3 joins atom results) ------- */
+
+typedef struct {
+  uint32_t x;         /* source variable index                             */
+  uint32_t y;         /* target variable index                             */
+  const rpq_query *q; /* the atom's compiled regex                         */
+} crpq_atom;
+
+/* Evaluates a CRPQ with n_vars variables (1 .. RPQ_MAX_VARS) and n_atoms
+ * atoms (1 .. RPQ_MAX_ATOMS).  var_label[i] >= 0 requires f(i) to carry that
+ * vertex label (needs a graph loaded with vertex labels); -1 or a NULL array
+ * means no constraint.  Every variable must occur in some atom, and the
+ * atoms must connect all variables.  restrict0 (may be NULL) limits
+ * variable 0 to the listed vertices -- a batch of the full query.  Rows are
+ * n_vars-tuples in declaration order.  flags as for run_rpq.
+ * Errors: INVALID_ARG, OUT_OF_BUDGET, CUDA, TIMEOUT. */
+int run_crpq(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_vars, const int32_t *var_label, const crpq_atom *atoms,
+             uint32_t n_atoms, const uint32_t *restrict0, uint32_t n_restrict0, uint32_t flags,
+             rpq_result **out);
+
+/* ---- results ------------------------------------------------------------ */
+
+/* Row count, arity (2 for RPQ) and the order-independent digest of the rows:
+ * sum (mod 2^64) and xor of h(row) over all rows.  For a row t[0 .. k-1]:
+ * k == 1: h = s(t[0]); k >= 2: h = s(t[0] << 32 | t[1]), then for each
+ * further column i, h = s(h ^ t[i]).  s(x) is the SplitMix64 output for
+ * state x: z = x + 0x9E3779B97F4A7C15, z = (z ^ z >> 30) * 0xBF58476D1CE4E5B9,
+ * z = (z ^ z >> 27) * 0x94D049BB133111EB, s = z ^ z >> 31 (mod 2^64).
+ * Any out pointer may be NULL. */
+int result_info(const rpq_result *r, uint64_t *count, uint32_t *arity, uint64_t *digest_sum,
+                uint64_t *digest_xor);
+
+/* Work counters of the evaluation that made the result.  product_edges is
+ * the number of product-edge relaxations of a per-start-vertex traversal
+ * over the minimal DFA: for every start s, every product vertex (v, q)
+ * reachable from (s, q0), every label l leaving q, deg_l(v) -- a measure of
+ * the work that does not depend on the engine's design.
+ * product_vertices counts the (s, v, q) visited.  The remaining fields
+ * describe what the kernels did. */
+typedef struct {
+  uint64_t product_edges;    /* W                                              */
+  uint64_t product_vertices; /* N                                              */
+  uint64_t levels;           /* BFS levels summed over lane groups            */
+  uint64_t push_levels;      /* levels expanded top-down                      */
+  uint64_t pull_levels;      /* levels expanded bottom-up                     */
+  uint64_t group_edges;      /* edges read by top-down levels (per lane group) */
+  uint64_t group_rows;       /* adjacency rows opened by top-down levels      */
+  uint64_t group_vertices;   /* lane-group product vertices discovered        */
+  uint64_t pull_edges;       /* in-edges read by bottom-up levels             */
+  uint64_t pull_vertices;    /* (vertex, state) words examined bottom-up      */
+  uint64_t lane_words;       /* 64-bit words per lane group (1 or 4)          */
+  uint64_t lane_groups;      /* lane groups evaluated                         */
+  double bfs_ms;             /* device time of the traversal kernels          */
+  double emit_ms;            /* device time of the emission kernels           */
+  uint64_t bfs_launches;     /* traversal kernel launches                     */
+  uint64_t launches;         /* all kernel launches of the evaluation         */
+} rpq_stats;
+
+int result_stats(const rpq_result *r, rpq_stats *out);
+
+/* Copies rows [offset, offset + max_rows) (clipped to the row count) into
+ * host memory out[arity * k], k rows, and stores k in *n_rows.
+ * Requires a result made with RPQ_MATERIALIZE.
+ * Errors: INVALID_ARG, CUDA. */
+int fetch_pairs(const rpq_result *r, uint64_t offset, uint64_t max_rows, uint32_t *out, uint64_t *n_rows);
+
+void free_result(rpq_result *r);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_RPQ_H */

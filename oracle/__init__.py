@@ -205,14 +205,29 @@ def splitmix64(x):
     return z ^ (z >> 31)
 
 
-def pair_digest(rows: np.ndarray):
-    """Order-independent digest of a set of (src, dst) rows:
-    (count, sum mod 2^64, xor) of splitmix64(src << 32 | dst)."""
-    rows = np.asarray(rows, dtype=np.uint64).reshape(-1, 2)
+def row_digest(rows: np.ndarray):
+    """Order-independent digest of a set of rows t[0..k-1]:
+    (count, sum mod 2^64, xor) of h(row), where h = s(t0) for k = 1 and
+    h = s(t0 << 32 | t1) folded with s(h ^ t_i) for each further column
+    (s = splitmix64)."""
+    rows = np.asarray(rows, dtype=np.uint64)
+    if rows.ndim == 1:
+        rows = rows.reshape(-1, 1)
     if len(rows) == 0:
         return 0, 0, 0
-    h = splitmix64((rows[:, 0] << np.uint64(32)) | rows[:, 1])
+    k = rows.shape[1]
+    if k == 1:
+        h = splitmix64(rows[:, 0])
+    else:
+        h = splitmix64((rows[:, 0] << np.uint64(32)) | rows[:, 1])
+        for i in range(2, k):
+            h = splitmix64(h ^ rows[:, i])
     with np.errstate(over="ignore"):
         s = int(np.add.reduce(h, dtype=np.uint64))
     x = int(np.bitwise_xor.reduce(h))
     return len(rows), s, x
+
+
+def pair_digest(rows: np.ndarray):
+    """``row_digest`` of (src, dst) rows."""
+    return row_digest(np.asarray(rows).reshape(-1, 2))

@@ -9,7 +9,8 @@
 //     directed path from x to y spells a word of L(rho).  Evaluated the
 //     automata way (Section 2.2, "Automata-based approach"): for every start
 //     vertex, a breadth-first search over product vertices
-//     (data vertex, automaton state) with a per-start visited set, adding
+//     (data vertex, automaton state) with a per-start visited set (one flag
+//     per product vertex), adding
 //     (start, v) whenever an accepting state is reached.  The automaton is a
 //     Thompson epsilon-NFA with explicit epsilon-closures, so no DFA is
 //     involved in the result.  There is no hop limit: the search runs until
@@ -222,7 +223,7 @@ struct Parser {
       return add(K_LABEL, c - 'a', -1, -1);
     }
     size_t start = pos;
-    while (at_atom_start()) pos++;
+    while (pos < s.size() && s[pos] != '(' && at_atom_start()) pos++;
     std::string ident = s.substr(start, pos - start);
     for (size_t i = 0; i < names->size(); i++)
       if ((*names)[i] == ident) return add(K_LABEL, (int)i, -1, -1);
@@ -512,27 +513,39 @@ inline std::pair<const std::pair<uint32_t, uint32_t> *, const std::pair<uint32_t
 // Single-source evaluation
 // --------------------------------------------------------------------------
 
-// Definition 1 for one start vertex, by BFS over (vertex, NFA state).
+// Definition 1 for one start vertex, by BFS over (vertex, NFA state).  The
+// visited set is a flag per product vertex (v, q), index v * |NFA| + q; the
+// result set is a flag per vertex, read out in vertex order.
 void rpq_from_nfa(const Graph &g, const Automaton &A, uint32_t s, std::vector<uint32_t> *out) {
-  std::set<std::pair<uint32_t, int>> visited;
+  const size_t S = A.nfa.eps.size();
+  std::vector<uint8_t> visited((size_t)g.n * S, 0);
+  std::vector<uint8_t> result(g.n, 0);
   std::deque<std::pair<uint32_t, int>> queue;
-  std::set<uint32_t> result;
-  for (int q : A.closure[A.nfa.start])
-    if (visited.insert({s, q}).second) queue.push_back({s, q});
+  for (int q : A.closure[A.nfa.start]) {
+    visited[(size_t)s * S + q] = 1;
+    queue.push_back({s, q});
+  }
   while (!queue.empty()) {
     auto [v, q] = queue.front();
     queue.pop_front();
-    if (q == A.nfa.accept) result.insert(v);
+    if (q == A.nfa.accept) result[v] = 1;
     for (auto &m : A.nfa.moves[q]) {
       uint32_t l = (uint32_t)m.first;
       if (l >= g.n_labels) continue;
       auto [lo, hi] = out_edges(g, v, l);
       for (auto e = lo; e != hi; ++e)
-        for (int q3 : A.closure[m.second])
-          if (visited.insert({e->second, q3}).second) queue.push_back({e->second, q3});
+        for (int q3 : A.closure[m.second]) {
+          uint8_t &seen = visited[(size_t)e->second * S + q3];
+          if (!seen) {
+            seen = 1;
+            queue.push_back({e->second, q3});
+          }
+        }
     }
   }
-  out->assign(result.begin(), result.end());
+  out->clear();
+  for (uint32_t v = 0; v < g.n; v++)
+    if (result[v]) out->push_back(v);
 }
 
 // Same start vertex over the minimal DFA: counts the product vertices N and
@@ -544,27 +557,34 @@ void rpq_from_dfa(const Graph &g, const Automaton &A, uint32_t s, std::vector<ui
   *N = 0;
   out->clear();
   if (A.dfa_states == 0) return;
-  std::set<std::pair<uint32_t, int>> visited;
+  const size_t S = (size_t)A.dfa_states;
+  std::vector<uint8_t> visited((size_t)g.n * S, 0);
+  std::vector<uint8_t> result(g.n, 0);
   std::deque<std::pair<uint32_t, int>> queue;
-  std::set<uint32_t> result;
-  visited.insert({s, A.dfa_start});
+  visited[(size_t)s * S + A.dfa_start] = 1;
   queue.push_back({s, A.dfa_start});
   int nl = (int)A.dfa_next[0].size();
   while (!queue.empty()) {
     auto [v, q] = queue.front();
     queue.pop_front();
     *N += 1;
-    if (A.dfa_final[q]) result.insert(v);
+    if (A.dfa_final[q]) result[v] = 1;
     for (int l = 0; l < nl; l++) {
       int t = A.dfa_next[q][l];
       if (t < 0 || (uint32_t)l >= g.n_labels) continue;
       auto [lo, hi] = out_edges(g, v, (uint32_t)l);
       *W += (uint64_t)(hi - lo);
-      for (auto e = lo; e != hi; ++e)
-        if (visited.insert({e->second, t}).second) queue.push_back({e->second, t});
+      for (auto e = lo; e != hi; ++e) {
+        uint8_t &seen = visited[(size_t)e->second * S + t];
+        if (!seen) {
+          seen = 1;
+          queue.push_back({e->second, t});
+        }
+      }
     }
   }
-  out->assign(result.begin(), result.end());
+  for (uint32_t v = 0; v < g.n; v++)
+    if (result[v]) out->push_back(v);
 }
 
 // --------------------------------------------------------------------------

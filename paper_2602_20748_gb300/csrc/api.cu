@@ -1,0 +1,814 @@
+// Host side of the C ABI declared in include/rpq.h: contexts, device memory
+// budget, graph loading, query compilation, batched evaluation driving the
+// traversal and emission kernels, results and fetch.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "crpq.h"
+#include "device_common.cuh"
+#include "rpq_internal.h"
+
+using namespace rpq;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr int BFS_THREADS_HOST = 256;
+
+struct Workspace {
+  uint64_t vis_words = 0;   // capacity of vis / fr0 / fr1 in u64 words
+  uint64_t list_cap = 0;    // capacity of list0 / list1 in entries
+  uint64_t claim_cap = 0;   // capacity of claim in u32
+  uint32_t lane_cap = 0;    // lanesrc / empty-mask staging capacity (lanes)
+  u64 *vis = nullptr, *fr0 = nullptr, *fr1 = nullptr, *list0 = nullptr, *list1 = nullptr;
+  u32 *claim = nullptr;
+  u32 *lanesrc = nullptr;
+  u64 *empty = nullptr;
+};
+
+}  // namespace
+
+struct rpq_ctx {
+  int device = -1;
+  cudaStream_t stream = nullptr;
+  uint64_t budget = 0;
+  uint64_t used = 0;
+  std::string err;
+  Workspace ws;
+  BfsCtl *ctl = nullptr;
+  u64 *small = nullptr;  // [0..1] digest, [2] total, [3..7] spare
+  uint32_t stamp = 0;
+  int sms = 0;
+  int bpsm[2] = {0, 0};  // resident traversal blocks per SM for NW = 1, 4
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  float alpha = 4.0f;
+  uint64_t time_limit_ns = 20ull * 1000 * 1000 * 1000;
+  uint32_t max_groups = 16;
+};
+
+struct rpq_graph {
+  rpq_ctx *ctx = nullptr;
+  DevGraph g;
+  uint64_t bytes = 0;
+};
+
+struct rpq_query {
+  HostQuery hq;
+};
+
+namespace {
+
+struct Chunk {
+  u32 *lanesrc = nullptr;
+  u64 *lane_off = nullptr;
+  u32 *dst = nullptr;
+  uint64_t rows = 0;
+  uint32_t n_lanes = 0;
+  uint64_t bytes = 0;
+};
+
+}  // namespace
+
+struct rpq_result {
+  rpq_ctx *ctx = nullptr;
+  uint32_t arity = 2;
+  uint64_t count = 0;
+  uint64_t dsum = 0, dxor = 0;
+  bool materialized = false;
+  std::vector<Chunk> chunks;
+  u32 *tuples = nullptr;  // CRPQ rows, arity values each
+  uint64_t tuple_bytes = 0;
+  rpq_stats stats;
+};
+
+namespace {
+
+int set_err(rpq_ctx *c, int code, const std::string &msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_err(rpq_ctx *c, cudaError_t e, const char *what) {
+  return set_err(c, RPQ_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(expr)                                          \
+  do {                                                    \
+    cudaError_t _e = (expr);                              \
+    if (_e != cudaSuccess) return cuda_err(ctx, _e, #expr); \
+  } while (0)
+
+int dev_alloc(rpq_ctx *ctx, void **p, uint64_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (ctx->used + bytes > ctx->budget)
+    return set_err(ctx, RPQ_ERR_OUT_OF_BUDGET,
+                   "device memory budget exceeded (" + std::to_string(ctx->used + bytes) + " > " +
+                       std::to_string(ctx->budget) + " bytes)");
+  cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_err(ctx, e, "cudaMallocAsync");
+  }
+  ctx->used += bytes;
+  return RPQ_OK;
+}
+
+void dev_free(rpq_ctx *ctx, void *p, uint64_t bytes) {
+  if (!p) return;
+  if (bytes == 0) bytes = 16;
+  cudaFreeAsync(p, ctx->stream);
+  ctx->used -= std::min(ctx->used, bytes);
+}
+
+template <typename T>
+int dalloc(rpq_ctx *ctx, T **p, uint64_t count) {
+  return dev_alloc(ctx, (void **)p, count * sizeof(T));
+}
+
+template <typename T>
+void dfree(rpq_ctx *ctx, T *&p, uint64_t count) {
+  dev_free(ctx, (void *)p, count * sizeof(T));
+  p = nullptr;
+}
+
+bool usable(rpq_ctx *ctx) {
+  if (!ctx) return false;
+  if (ctx->device < 0) {
+    set_err(ctx, RPQ_ERR_NO_DEVICE, "host-only context has no GPU");
+    return false;
+  }
+  cudaSetDevice(ctx->device);
+  return true;
+}
+
+void free_workspace(rpq_ctx *ctx) {
+  Workspace &w = ctx->ws;
+  dfree(ctx, w.vis, w.vis_words);
+  dfree(ctx, w.fr0, w.vis_words);
+  dfree(ctx, w.fr1, w.vis_words);
+  dfree(ctx, w.list0, w.list_cap);
+  dfree(ctx, w.list1, w.list_cap);
+  dfree(ctx, w.claim, w.claim_cap);
+  dfree(ctx, w.lanesrc, w.lane_cap);
+  dfree(ctx, w.empty, w.lane_cap / 64);
+  w = Workspace();
+}
+
+uint64_t workspace_bytes(uint64_t words, uint64_t lists, uint64_t claims, uint32_t lanes) {
+  return words * 8 * 3 + lists * 8 * 2 + claims * 4 + (uint64_t)lanes * 4 + (uint64_t)lanes / 64 * 8;
+}
+
+// Makes sure the traversal workspace holds at least the given capacities.
+// Frontier arrays must be zero on entry to a search; they are zeroed when
+// allocated and the search leaves them zero.
+int ensure_workspace(rpq_ctx *ctx, uint64_t words, uint64_t lists, uint64_t claims, uint32_t lanes) {
+  Workspace &w = ctx->ws;
+  if (w.vis_words >= words && w.list_cap >= lists && w.claim_cap >= claims && w.lane_cap >= lanes) return RPQ_OK;
+  words = std::max(words, w.vis_words);
+  lists = std::max(lists, w.list_cap);
+  claims = std::max(claims, w.claim_cap);
+  lanes = std::max(lanes, w.lane_cap);
+  free_workspace(ctx);
+  int rc;
+  if ((rc = dalloc(ctx, &w.vis, words)) || (rc = dalloc(ctx, &w.fr0, words)) || (rc = dalloc(ctx, &w.fr1, words)) ||
+      (rc = dalloc(ctx, &w.list0, lists)) || (rc = dalloc(ctx, &w.list1, lists)) ||
+      (rc = dalloc(ctx, &w.claim, claims ? claims : 1)) || (rc = dalloc(ctx, &w.lanesrc, lanes)) ||
+      (rc = dalloc(ctx, &w.empty, lanes / 64 + 1))) {
+    free_workspace(ctx);
+    return rc;
+  }
+  w.vis_words = words;
+  w.list_cap = lists;
+  w.claim_cap = claims ? claims : 1;
+  w.lane_cap = lanes;
+  CK(cudaMemsetAsync(w.fr0, 0, words * 8, ctx->stream));
+  CK(cudaMemsetAsync(w.fr1, 0, words * 8, ctx->stream));
+  CK(cudaMemsetAsync(w.claim, 0, w.claim_cap * 4, ctx->stream));
+  ctx->stamp = 0;
+  return RPQ_OK;
+}
+
+void free_chunk(rpq_ctx *ctx, Chunk &c) {
+  dfree(ctx, c.lanesrc, c.n_lanes);
+  dfree(ctx, c.lane_off, (uint64_t)c.n_lanes + 1);
+  dfree(ctx, c.dst, c.rows);
+}
+
+// Evaluates one RPQ from the sorted, distinct start vertices `srcs`.
+int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::vector<uint32_t> &srcs,
+             uint32_t flags, rpq_result *res) {
+  const DevGraph &g = gr->g;
+  const QueryDesc &qd = qr->hq.d;
+  const uint32_t Q = qd.n_states;
+  const bool materialize = (flags & RPQ_MATERIALIZE) != 0;
+  res->stats.lane_words = srcs.size() <= 64 ? 1 : 4;
+  if (Q == 0 || srcs.empty()) return RPQ_OK;
+  const int nw = srcs.size() <= 64 ? 1 : 4;
+  const uint32_t K = 64u * nw;
+  const uint32_t n = g.n;
+  const uint64_t groups_total = (srcs.size() + K - 1) / K;
+
+  // lane groups per launch: bounded by max_groups and by the budget
+  uint32_t G = (uint32_t)std::min<uint64_t>(groups_total, ctx->max_groups);
+  for (;;) {
+    uint64_t words = (uint64_t)G * Q * n * nw;
+    uint64_t need = workspace_bytes(words, (uint64_t)G * Q * n, nw > 1 ? (uint64_t)G * Q * n : 0, G * K);
+    uint64_t have = ctx->budget - ctx->used +
+                    workspace_bytes(ctx->ws.vis_words, ctx->ws.list_cap, ctx->ws.claim_cap, ctx->ws.lane_cap);
+    if (need + (64ull << 20) <= have || G == 1) break;
+    G--;
+  }
+  {
+    uint64_t words = (uint64_t)G * Q * n * nw;
+    int rc = ensure_workspace(ctx, words, (uint64_t)G * Q * n, nw > 1 ? (uint64_t)G * Q * n : 0, G * K);
+    if (rc) return rc;
+  }
+  Workspace &w = ctx->ws;
+
+  // bottom-up cost per level, in bytes, for the direction choice
+  double pull_fixed = 0;
+  for (uint32_t q2 = 0; q2 < Q; q2++) {
+    if (qd.in_begin[q2] == qd.in_begin[q2 + 1]) continue;
+    pull_fixed += (double)n * 8.0 * nw;
+    for (uint32_t j = qd.in_begin[q2]; j < qd.in_begin[q2 + 1]; j++) {
+      uint32_t l = qd.in_label[j];
+      double el = l < g.L ? (double)g.label_edges[l] : 0.0;
+      pull_fixed += (double)n * 8.0 + el * (4.0 + 8.0 * nw * __builtin_popcount(qd.in_from[j]));
+    }
+  }
+
+  const int force = (flags & RPQ_FORCE_PUSH) ? 1 : (flags & RPQ_FORCE_PULL) ? 2 : 0;
+  const int blocks = ctx->sms * ctx->bpsm[nw == 1 ? 0 : 1];
+  if (blocks <= 0) return set_err(ctx, RPQ_ERR_CUDA, "traversal kernel cannot be made resident");
+  const uint32_t segs = (n + EMIT_SEG - 1) / EMIT_SEG;
+
+  std::vector<uint32_t> lanes;
+  std::vector<uint64_t> empty;
+  for (uint64_t g0 = 0; g0 < groups_total; g0 += G) {
+    const uint32_t Gb = (uint32_t)std::min<uint64_t>(G, groups_total - g0);
+    const uint32_t n_lanes = Gb * K;
+    lanes.assign(n_lanes, NO_SOURCE);
+    empty.assign((size_t)Gb * nw, 0);
+    for (uint32_t i = 0; i < n_lanes; i++) {
+      uint64_t si = g0 * K + i;
+      if (si < srcs.size()) lanes[i] = srcs[si];
+      if (lanes[i] == NO_SOURCE) empty[(i / K) * nw + (i % K) / 64] |= 1ull << (i % 64);
+    }
+    CK(cudaMemcpyAsync(w.lanesrc, lanes.data(), n_lanes * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(w.empty, empty.data(), empty.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+
+    BfsParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.out_off = g.out_off;
+    p.out_col = g.out_col;
+    p.in_off = g.in_off;
+    p.in_col = g.in_col;
+    p.n = n;
+    p.L = g.L;
+    p.G = Gb;
+    p.Q = Q;
+    p.lanesrc = w.lanesrc;
+    p.vis = w.vis;
+    p.fr0 = w.fr0;
+    p.fr1 = w.fr1;
+    p.claim = w.claim;
+    p.list0 = w.list0;
+    p.list1 = w.list1;
+    p.ctl = ctx->ctl;
+    p.stamp_base = ctx->stamp;
+    p.nblocks = (unsigned)blocks;
+    p.force = force;
+    p.alpha = ctx->alpha;
+    p.pull_cost_fixed = pull_fixed * Gb;
+    p.time_limit_ns = ctx->time_limit_ns;
+    p.q = qd;
+
+    CK(launch_vis_init(nw, p, w.empty, ctx->stream));
+    CK(cudaMemsetAsync(ctx->ctl, 0, sizeof(BfsCtl), ctx->stream));
+    CK(cudaEventRecord(ctx->ev[0], ctx->stream));
+    CK(launch_msbfs(nw, p, blocks, BFS_THREADS_HOST, ctx->stream));
+    CK(cudaEventRecord(ctx->ev[1], ctx->stream));
+    res->stats.launches += 3;
+    res->stats.bfs_launches += 1;
+
+    // emission pass 1: counts and digest
+    u32 *cnt = nullptr;
+    u64 *off = nullptr, *tmp = nullptr;
+    const uint64_t ncnt = (uint64_t)n_lanes * segs;
+    const uint64_t tmpw = scan_tmp_words(ncnt);
+    int rc;
+    if ((rc = dalloc(ctx, &cnt, ncnt)) || (rc = dalloc(ctx, &off, ncnt)) || (rc = dalloc(ctx, &tmp, tmpw))) {
+      dfree(ctx, cnt, ncnt);
+      dfree(ctx, off, ncnt);
+      dfree(ctx, tmp, tmpw);
+      return rc;
+    }
+    EmitParams ep;
+    ep.vis = w.vis;
+    ep.n = n;
+    ep.G = Gb;
+    ep.Q = Q;
+    ep.final_mask = qd.final_mask;
+    ep.lanesrc = w.lanesrc;
+    ep.segs = segs;
+    ep.cnt = cnt;
+    ep.off = off;
+    ep.dst = nullptr;
+    ep.digest = ctx->small;
+    CK(cudaMemsetAsync(ctx->small, 0, 3 * 8, ctx->stream));
+    CK(cudaEventRecord(ctx->ev[2], ctx->stream));
+    CK(launch_emit(nw, false, ep, ctx->stream));
+    CK(exclusive_scan_u32_to_u64(cnt, off, ncnt, ctx->small + 2, tmp, ctx->stream));
+    res->stats.launches += 2;
+    BfsCtl hctl;
+    u64 hsmall[3];
+    CK(cudaMemcpyAsync(&hctl, ctx->ctl, sizeof(BfsCtl), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(hsmall, ctx->small, 3 * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (hctl.err) {
+      dfree(ctx, cnt, ncnt);
+      dfree(ctx, off, ncnt);
+      dfree(ctx, tmp, tmpw);
+      // an interrupted search may leave frontier words set: clear them
+      cudaMemsetAsync(w.fr0, 0, w.vis_words * 8, ctx->stream);
+      cudaMemsetAsync(w.fr1, 0, w.vis_words * 8, ctx->stream);
+      return set_err(ctx, RPQ_ERR_TIMEOUT, "traversal grid barrier wait ran out of time");
+    }
+    const uint64_t total = hsmall[2];
+    res->count += total;
+    res->dsum += hsmall[0];
+    res->dxor ^= hsmall[1];
+    rpq_stats &s = res->stats;
+    s.product_edges += hctl.stats[ST_W];
+    s.product_vertices += hctl.stats[ST_N];
+    s.levels += hctl.levels;
+    s.push_levels += hctl.stats[ST_PUSH_LEVELS];
+    s.pull_levels += hctl.stats[ST_PULL_LEVELS];
+    s.group_edges += hctl.stats[ST_GROUP_EDGES];
+    s.group_rows += hctl.stats[ST_GROUP_ROWS];
+    s.group_vertices += hctl.stats[ST_GROUP_VERTICES];
+    s.pull_edges += hctl.stats[ST_PULL_EDGES];
+    s.pull_vertices += hctl.stats[ST_PULL_VERTICES];
+    s.lane_groups += Gb;
+    ctx->stamp += (uint32_t)hctl.levels + 2;
+
+    if (materialize) {
+      Chunk c;
+      c.n_lanes = n_lanes;
+      c.rows = total;
+      if ((rc = dalloc(ctx, &c.lanesrc, n_lanes)) || (rc = dalloc(ctx, &c.lane_off, (uint64_t)n_lanes + 1)) ||
+          (rc = dalloc(ctx, &c.dst, total))) {
+        free_chunk(ctx, c);
+        dfree(ctx, cnt, ncnt);
+        dfree(ctx, off, ncnt);
+        dfree(ctx, tmp, tmpw);
+        return rc;
+      }
+      ep.dst = c.dst;
+      CK(launch_emit(nw, true, ep, ctx->stream));
+      CK(launch_gather_lane_off(off, segs, n_lanes, ctx->small + 2, c.lane_off, ctx->stream));
+      CK(cudaMemcpyAsync(c.lanesrc, w.lanesrc, n_lanes * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+      res->stats.launches += 2;
+      res->chunks.push_back(c);
+    }
+    CK(cudaEventRecord(ctx->ev[3], ctx->stream));
+    dfree(ctx, cnt, ncnt);
+    dfree(ctx, off, ncnt);
+    dfree(ctx, tmp, tmpw);
+    CK(cudaEventSynchronize(ctx->ev[3]));
+    float ms_bfs = 0, ms_emit = 0;
+    cudaEventElapsedTime(&ms_bfs, ctx->ev[0], ctx->ev[1]);
+    cudaEventElapsedTime(&ms_emit, ctx->ev[2], ctx->ev[3]);
+    s.bfs_ms += ms_bfs;
+    s.emit_ms += ms_emit;
+  }
+  return RPQ_OK;
+}
+
+int check_rpq_flags(rpq_ctx *ctx, uint32_t flags) {
+  uint32_t mode = flags & (RPQ_MATERIALIZE | RPQ_COUNT_ONLY);
+  if (mode != RPQ_MATERIALIZE && mode != RPQ_COUNT_ONLY)
+    return set_err(ctx, RPQ_ERR_INVALID_ARG, "flags need exactly one of RPQ_MATERIALIZE, RPQ_COUNT_ONLY");
+  if ((flags & RPQ_FORCE_PUSH) && (flags & RPQ_FORCE_PULL))
+    return set_err(ctx, RPQ_ERR_INVALID_ARG, "RPQ_FORCE_PUSH and RPQ_FORCE_PULL are exclusive");
+  if (flags & ~(RPQ_MATERIALIZE | RPQ_COUNT_ONLY | RPQ_FORCE_PUSH | RPQ_FORCE_PULL))
+    return set_err(ctx, RPQ_ERR_INVALID_ARG, "unknown flag bits");
+  return RPQ_OK;
+}
+
+int run_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, std::vector<uint32_t> &srcs, uint32_t flags,
+                rpq_result **out) {
+  rpq_result *r = new rpq_result;
+  r->ctx = ctx;
+  r->arity = 2;
+  r->materialized = (flags & RPQ_MATERIALIZE) != 0;
+  std::memset(&r->stats, 0, sizeof(r->stats));
+  int rc = eval_rpq(ctx, g, q, srcs, flags, r);
+  if (rc) {
+    free_result(r);
+    return rc;
+  }
+  *out = r;
+  return RPQ_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int rpq_create(rpq_ctx **out, int device, uint64_t mem_budget_bytes, void *cuda_stream) {
+  if (!out) {
+    g_create_error = "out is NULL";
+    return RPQ_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  rpq_ctx *c = new rpq_ctx;
+  c->device = device;
+  if (device < 0) {
+    *out = c;
+    return RPQ_OK;
+  }
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaFree(0);
+  size_t free_b = 0, total_b = 0;
+  if (e == cudaSuccess) e = cudaMemGetInfo(&free_b, &total_b);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("CUDA device unavailable: ") + cudaGetErrorString(e);
+    delete c;
+    return RPQ_ERR_CUDA;
+  }
+  c->stream = (cudaStream_t)cuda_stream;
+  c->budget = mem_budget_bytes ? mem_budget_bytes : (uint64_t)(free_b * 0.9);
+  for (int i = 0; i < 4; i++) cudaEventCreate(&c->ev[i]);
+  if (msbfs_max_blocks(1, BFS_THREADS_HOST, &c->bpsm[0], &c->sms) || msbfs_max_blocks(4, BFS_THREADS_HOST, &c->bpsm[1], &c->sms)) {
+    g_create_error = "occupancy query failed";
+    rpq_destroy(c);
+    return RPQ_ERR_CUDA;
+  }
+  if (const char *a = std::getenv("RPQ_ALPHA")) c->alpha = (float)std::atof(a);
+  if (const char *m = std::getenv("RPQ_MAX_GROUPS")) c->max_groups = (uint32_t)std::max(1, std::atoi(m));
+  if (dalloc(c, &c->ctl, 1) || dalloc(c, &c->small, 8)) {
+    g_create_error = c->err;
+    rpq_destroy(c);
+    return RPQ_ERR_CUDA;
+  }
+  *out = c;
+  return RPQ_OK;
+}
+
+void rpq_destroy(rpq_ctx *c) {
+  if (!c) return;
+  if (c->device >= 0) {
+    cudaSetDevice(c->device);
+    free_workspace(c);
+    dfree(c, c->ctl, 1);
+    dfree(c, c->small, 8);
+    cudaStreamSynchronize(c->stream);
+    for (int i = 0; i < 4; i++)
+      if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  }
+  delete c;
+}
+
+const char *rpq_last_error(const rpq_ctx *c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+int rpq_set_stream(rpq_ctx *ctx, void *stream) {
+  if (!ctx) return RPQ_ERR_INVALID_ARG;
+  if (!usable(ctx)) return RPQ_ERR_NO_DEVICE;
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->stream = (cudaStream_t)stream;
+  return RPQ_OK;
+}
+
+int load_graph(rpq_ctx *ctx, uint32_t n_vertices, uint32_t n_labels, uint64_t n_edges, const uint32_t *src,
+               const uint32_t *dst, const uint16_t *label, const uint8_t *vertex_label, rpq_graph **out) {
+  if (!ctx || !out) return set_err(ctx, RPQ_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (!usable(ctx)) return RPQ_ERR_NO_DEVICE;
+  if (n_edges && (!src || !dst || !label)) return set_err(ctx, RPQ_ERR_INVALID_ARG, "null edge array");
+  if (n_vertices == 0 || n_vertices >= (1u << 31)) return set_err(ctx, RPQ_ERR_INVALID_ARG, "bad n_vertices");
+  if (n_labels == 0 || n_labels > RPQ_MAX_LABELS) return set_err(ctx, RPQ_ERR_INVALID_ARG, "bad n_labels");
+  if (n_edges >= (1ull << 32)) return set_err(ctx, RPQ_ERR_INVALID_ARG, "n_edges must be < 2^32");
+  if (graph_key_bits(n_vertices, n_labels) > 64)
+    return set_err(ctx, RPQ_ERR_INVALID_ARG, "graph too large for 64-bit edge keys");
+  rpq_graph *gr = new rpq_graph;
+  gr->ctx = ctx;
+  uint32_t *d_src = nullptr, *d_dst = nullptr;
+  uint16_t *d_lab = nullptr;
+  int rc = RPQ_OK;
+  const uint64_t m = n_edges;
+  const uint64_t rows = (uint64_t)n_labels * (n_vertices + 1);
+  // the graph arrays: 2 offset arrays + 2 column arrays (+ vertex labels)
+  const uint64_t gbytes = rows * 8 + m * 8 + (vertex_label ? n_vertices : 0);
+  // sort scratch (keys x3, flags, histograms) comes from the same budget
+  const uint64_t scratch = m * 30 + (64ull << 20);
+  if (ctx->used + gbytes + scratch + m * 10 > ctx->budget) {
+    delete gr;
+    return set_err(ctx, RPQ_ERR_OUT_OF_BUDGET, "graph does not fit the device memory budget");
+  }
+  cudaStream_t st = ctx->stream;
+  std::string msg;
+  if ((rc = dalloc(ctx, &d_src, m)) || (rc = dalloc(ctx, &d_dst, m)) || (rc = dalloc(ctx, &d_lab, m))) goto fail;
+  if (m) {
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(d_src, src, m * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d_dst, dst, m * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d_lab, label, m * 2, cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+      rc = cuda_err(ctx, e, "cudaMemcpyAsync");
+      goto fail;
+    }
+  }
+  rc = build_graph(&gr->g, n_vertices, n_labels, m, d_src, d_dst, d_lab, st, &msg);
+  if (rc) {
+    set_err(ctx, rc, msg);
+    goto fail;
+  }
+  if (vertex_label) {
+    rc = dalloc(ctx, &gr->g.vlabel, n_vertices);
+    if (rc) goto fail;
+    cudaError_t e = cudaMemcpyAsync(gr->g.vlabel, vertex_label, n_vertices, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+      rc = cuda_err(ctx, e, "cudaMemcpyAsync");
+      goto fail;
+    }
+  }
+  {
+    // the graph arrays were allocated inside build_graph outside the budget
+    // accounting; account for them now
+    uint64_t b = rows * 8 + gr->g.m * 8;
+    ctx->used += b;
+    gr->bytes = b;
+  }
+  dfree(ctx, d_src, m);
+  dfree(ctx, d_dst, m);
+  dfree(ctx, d_lab, m);
+  {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      rc = cuda_err(ctx, e, "load_graph");
+      free_graph(gr);
+      return rc;
+    }
+  }
+  *out = gr;
+  return RPQ_OK;
+fail:
+  dfree(ctx, d_src, m);
+  dfree(ctx, d_dst, m);
+  dfree(ctx, d_lab, m);
+  if (gr->g.out_off) cudaFreeAsync(gr->g.out_off, st);
+  if (gr->g.in_off) cudaFreeAsync(gr->g.in_off, st);
+  if (gr->g.out_col) cudaFreeAsync(gr->g.out_col, st);
+  if (gr->g.in_col) cudaFreeAsync(gr->g.in_col, st);
+  if (gr->g.vlabel) dfree(ctx, gr->g.vlabel, n_vertices);
+  delete gr;
+  return rc;
+}
+
+int graph_info(const rpq_graph *g, uint32_t *n_vertices, uint32_t *n_labels, uint64_t *n_edges) {
+  if (!g) return RPQ_ERR_INVALID_ARG;
+  if (n_vertices) *n_vertices = g->g.n;
+  if (n_labels) *n_labels = g->g.L;
+  if (n_edges) *n_edges = g->g.m;
+  return RPQ_OK;
+}
+
+void free_graph(rpq_graph *g) {
+  if (!g) return;
+  rpq_ctx *ctx = g->ctx;
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = ctx->stream;
+  cudaFreeAsync(g->g.out_off, st);
+  cudaFreeAsync(g->g.in_off, st);
+  cudaFreeAsync(g->g.out_col, st);
+  cudaFreeAsync(g->g.in_col, st);
+  ctx->used -= std::min(ctx->used, g->bytes);
+  if (g->g.vlabel) dfree(ctx, g->g.vlabel, g->g.n);
+  delete g;
+}
+
+int compile_rpq(rpq_ctx *ctx, const char *regex, const char *const *label_names, uint32_t n_names,
+                rpq_query **out) {
+  if (!ctx || !out || !regex) return set_err(ctx, RPQ_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (label_names == nullptr && n_names != 0) return set_err(ctx, RPQ_ERR_INVALID_ARG, "names NULL but n_names > 0");
+  rpq_query *q = new rpq_query;
+  std::string msg;
+  int rc = compile_regex(regex, label_names, n_names, &q->hq, &msg);
+  if (rc) {
+    delete q;
+    return set_err(ctx, rc, msg);
+  }
+  *out = q;
+  return RPQ_OK;
+}
+
+int query_info(const rpq_query *q, uint32_t *n_states, uint32_t *n_labels_out, uint64_t *final_mask, int32_t *next) {
+  if (!q) return RPQ_ERR_INVALID_ARG;
+  if (n_states) *n_states = q->hq.d.n_states;
+  if (n_labels_out) *n_labels_out = q->hq.d.n_labels;
+  if (final_mask) *final_mask = q->hq.d.final_mask;
+  if (next && !q->hq.next.empty()) std::memcpy(next, q->hq.next.data(), q->hq.next.size() * 4);
+  return RPQ_OK;
+}
+
+void free_query(rpq_query *q) { delete q; }
+
+int run_rpq(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, const uint32_t *sources, uint32_t n_sources,
+            uint32_t flags, rpq_result **out) {
+  if (!ctx || !g || !q || !out) return set_err(ctx, RPQ_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (!usable(ctx)) return RPQ_ERR_NO_DEVICE;
+  int rc = check_rpq_flags(ctx, flags);
+  if (rc) return rc;
+  if (!sources && n_sources) return set_err(ctx, RPQ_ERR_INVALID_ARG, "sources NULL but n_sources > 0");
+  std::vector<uint32_t> srcs;
+  if (!sources) {
+    srcs.resize(g->g.n);
+    for (uint32_t v = 0; v < g->g.n; v++) srcs[v] = v;
+  } else {
+    srcs.assign(sources, sources + n_sources);
+    for (uint32_t s : srcs)
+      if (s >= g->g.n) return set_err(ctx, RPQ_ERR_INVALID_ARG, "source id out of range");
+    std::sort(srcs.begin(), srcs.end());
+    srcs.erase(std::unique(srcs.begin(), srcs.end()), srcs.end());
+  }
+  return run_sources(ctx, g, q, srcs, flags, out);
+}
+
+int run_rpq_range(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, uint32_t src_begin, uint32_t src_end,
+                  uint32_t flags, rpq_result **out) {
+  if (!ctx || !g || !q || !out) return set_err(ctx, RPQ_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (!usable(ctx)) return RPQ_ERR_NO_DEVICE;
+  int rc = check_rpq_flags(ctx, flags);
+  if (rc) return rc;
+  if (src_begin > src_end || src_end > g->g.n) return set_err(ctx, RPQ_ERR_INVALID_ARG, "bad source range");
+  std::vector<uint32_t> srcs(src_end - src_begin);
+  for (uint32_t i = 0; i < srcs.size(); i++) srcs[i] = src_begin + i;
+  return run_sources(ctx, g, q, srcs, flags, out);
+}
+
+int run_crpq(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_vars, const int32_t *var_label, const crpq_atom *atoms,
+             uint32_t n_atoms, const uint32_t *restrict0, uint32_t n_restrict0, uint32_t flags, rpq_result **out) {
+  if (!ctx || !g || !atoms || !out) return set_err(ctx, RPQ_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (!usable(ctx)) return RPQ_ERR_NO_DEVICE;
+  int rc = check_rpq_flags(ctx, flags);
+  if (rc) return rc;
+  return crpq_eval(ctx, g, n_vars, var_label, atoms, n_atoms, restrict0, n_restrict0, flags, out);
+}
+
+int result_info(const rpq_result *r, uint64_t *count, uint32_t *arity, uint64_t *digest_sum, uint64_t *digest_xor) {
+  if (!r) return RPQ_ERR_INVALID_ARG;
+  if (count) *count = r->count;
+  if (arity) *arity = r->arity;
+  if (digest_sum) *digest_sum = r->dsum;
+  if (digest_xor) *digest_xor = r->dxor;
+  return RPQ_OK;
+}
+
+int result_stats(const rpq_result *r, rpq_stats *out) {
+  if (!r || !out) return RPQ_ERR_INVALID_ARG;
+  *out = r->stats;
+  return RPQ_OK;
+}
+
+int fetch_pairs(const rpq_result *r, uint64_t offset, uint64_t max_rows, uint32_t *out, uint64_t *n_rows) {
+  if (!r || (!out && max_rows) || !n_rows) return set_err(r ? r->ctx : nullptr, RPQ_ERR_INVALID_ARG, "null argument");
+  rpq_ctx *ctx = r->ctx;
+  *n_rows = 0;
+  if (!r->materialized) return set_err(ctx, RPQ_ERR_INVALID_ARG, "result was made with RPQ_COUNT_ONLY");
+  if (offset >= r->count || max_rows == 0) return RPQ_OK;
+  cudaSetDevice(ctx->device);
+  const uint64_t want = std::min<uint64_t>(max_rows, r->count - offset);
+  if (r->arity != 2 || r->tuples) {
+    CK(cudaMemcpyAsync(out, r->tuples + offset * r->arity, want * r->arity * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *n_rows = want;
+    return RPQ_OK;
+  }
+  const uint64_t piece = 1ull << 24;
+  u32 *stage = nullptr;
+  int rc = dalloc(ctx, &stage, 2 * std::min(piece, want));
+  if (rc) return rc;
+  uint64_t done = 0, base = 0;
+  for (const Chunk &c : r->chunks) {
+    uint64_t c_end = base + c.rows;
+    while (done < want && offset + done < c_end) {
+      uint64_t first = offset + done - base;
+      uint64_t k = std::min<uint64_t>({piece, want - done, c.rows - first});
+      cudaError_t e = launch_expand_pairs(c.lanesrc, c.lane_off, c.n_lanes, c.dst, first, k, stage, ctx->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out + 2 * done, stage, k * 8, cudaMemcpyDeviceToHost, ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) {
+        dfree(ctx, stage, 2 * std::min(piece, want));
+        return cuda_err(ctx, e, "fetch_pairs");
+      }
+      done += k;
+    }
+    base = c_end;
+    if (done >= want) break;
+  }
+  dfree(ctx, stage, 2 * std::min(piece, want));
+  *n_rows = done;
+  return RPQ_OK;
+}
+
+void free_result(rpq_result *r) {
+  if (!r) return;
+  rpq_ctx *ctx = r->ctx;
+  if (ctx && ctx->device >= 0) {
+    cudaSetDevice(ctx->device);
+    for (Chunk &c : r->chunks) free_chunk(ctx, c);
+    if (r->tuples) dev_free(ctx, r->tuples, r->tuple_bytes);
+  }
+  delete r;
+}
+
+}  // extern "C"
+
+// Helpers exported to the CRPQ module (same library).
+namespace rpq {
+
+int ctx_alloc(rpq_ctx *ctx, void **p, uint64_t bytes) { return dev_alloc(ctx, p, bytes); }
+void ctx_free(rpq_ctx *ctx, void *p, uint64_t bytes) { dev_free(ctx, p, bytes); }
+cudaStream_t ctx_stream(rpq_ctx *ctx) { return ctx->stream; }
+int ctx_error(rpq_ctx *ctx, int code, const std::string &msg) { return set_err(ctx, code, msg); }
+const DevGraph &graph_dev(const rpq_graph *g) { return g->g; }
+const HostQuery &query_host(const rpq_query *q) { return q->hq; }
+
+// Runs an RPQ from the given sorted distinct sources, materialized, and hands
+// back the per-lane CSR chunks (ownership passes to the caller).
+int rpq_rows_for_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, std::vector<uint32_t> &srcs,
+                         std::vector<RowChunk> *chunks, rpq_stats *stats) {
+  rpq_result r;
+  r.ctx = ctx;
+  r.materialized = true;
+  std::memset(&r.stats, 0, sizeof(r.stats));
+  int rc = eval_rpq(ctx, g, q, srcs, RPQ_MATERIALIZE, &r);
+  if (stats) {
+    stats->product_edges += r.stats.product_edges;
+    stats->product_vertices += r.stats.product_vertices;
+    stats->levels += r.stats.levels;
+    stats->push_levels += r.stats.push_levels;
+    stats->pull_levels += r.stats.pull_levels;
+    stats->group_edges += r.stats.group_edges;
+    stats->group_rows += r.stats.group_rows;
+    stats->group_vertices += r.stats.group_vertices;
+    stats->pull_edges += r.stats.pull_edges;
+    stats->pull_vertices += r.stats.pull_vertices;
+    stats->lane_groups += r.stats.lane_groups;
+    stats->bfs_ms += r.stats.bfs_ms;
+    stats->emit_ms += r.stats.emit_ms;
+    stats->bfs_launches += r.stats.bfs_launches;
+    stats->launches += r.stats.launches;
+  }
+  for (Chunk &c : r.chunks) {
+    if (rc == RPQ_OK) {
+      RowChunk rc_;
+      rc_.lanesrc = c.lanesrc;
+      rc_.lane_off = c.lane_off;
+      rc_.dst = c.dst;
+      rc_.rows = c.rows;
+      rc_.n_lanes = c.n_lanes;
+      chunks->push_back(rc_);
+    } else {
+      free_chunk(ctx, c);
+    }
+  }
+  r.chunks.clear();
+  return rc;
+}
+
+void free_row_chunk(rpq_ctx *ctx, RowChunk &c) {
+  dfree(ctx, c.lanesrc, c.n_lanes);
+  dfree(ctx, c.lane_off, (uint64_t)c.n_lanes + 1);
+  dfree(ctx, c.dst, c.rows);
+}
+
+int make_tuple_result(rpq_ctx *ctx, uint32_t arity, u32 *tuples, uint64_t rows, uint64_t dsum, uint64_t dxor,
+                      bool materialized, const rpq_stats &stats, rpq_result **out) {
+  rpq_result *r = new rpq_result;
+  r->ctx = ctx;
+  r->arity = arity;
+  r->count = rows;
+  r->dsum = dsum;
+  r->dxor = dxor;
+  r->materialized = materialized;
+  r->tuples = tuples;
+  r->tuple_bytes = tuples ? rows * arity * 4 : 0;
+  r->stats = stats;
+  *out = r;
+  return RPQ_OK;
+}
+
+}  // namespace rpq

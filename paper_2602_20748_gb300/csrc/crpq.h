@@ -1,0 +1,38 @@
+// Interface between the host API and the CRPQ join module.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "device_common.cuh"
+#include "rpq_internal.h"
+
+namespace rpq {
+
+// Per-source result rows of one RPQ evaluation (device memory): lane i of
+// the chunk is start vertex lanesrc[i] (0xFFFFFFFF = unused lane); its
+// destinations, ascending, are dst[lane_off[i] .. lane_off[i + 1]).
+struct RowChunk {
+  u32 *lanesrc = nullptr;
+  u64 *lane_off = nullptr;
+  u32 *dst = nullptr;
+  uint64_t rows = 0;
+  uint32_t n_lanes = 0;
+};
+
+int ctx_alloc(rpq_ctx *ctx, void **p, uint64_t bytes);
+void ctx_free(rpq_ctx *ctx, void *p, uint64_t bytes);
+cudaStream_t ctx_stream(rpq_ctx *ctx);
+int ctx_error(rpq_ctx *ctx, int code, const std::string &msg);
+const DevGraph &graph_dev(const rpq_graph *g);
+const HostQuery &query_host(const rpq_query *q);
+int rpq_rows_for_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, std::vector<uint32_t> &srcs,
+                         std::vector<RowChunk> *chunks, rpq_stats *stats);
+void free_row_chunk(rpq_ctx *ctx, RowChunk &c);
+int make_tuple_result(rpq_ctx *ctx, uint32_t arity, u32 *tuples, uint64_t rows, uint64_t dsum, uint64_t dxor,
+                      bool materialized, const rpq_stats &stats, rpq_result **out);
+
+int crpq_eval(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_vars, const int32_t *var_label, const crpq_atom *atoms,
+              uint32_t n_atoms, const uint32_t *restrict0, uint32_t n_restrict0, uint32_t flags, rpq_result **out);
+
+}  // namespace rpq

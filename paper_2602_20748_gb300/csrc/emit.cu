@@ -1,0 +1,132 @@
+// Result emission: visited words -> distinct (src, dst) rows in sorted order.
+//
+// After the search, the result set of start vertex s (Definition 1) is the
+// set of v with some accepting state q such that s's lane is set in
+// VIS[g][q][v].  For lane group g, OR the accepting states' words into a
+// K-bit result word per vertex.  A block owns a segment of EMIT_SEG vertices
+// of one group; warp c handles lane column c (32 lanes) and walks the segment
+// in 32-vertex tiles: the 32 x 32 bit tile is transposed with 32 ballots so
+// that thread j holds the 32 membership bits of lane 32c + j, in vertex
+// order.  Pass 1 counts per (lane, segment) and folds the row digest; an
+// exclusive scan over the counts laid out [lane][segment] gives every row its
+// output position directly (lanes are in source order, segments in vertex
+// order), and pass 2 writes the destinations.
+#include "device_common.cuh"
+#include "rpq_internal.h"
+
+namespace rpq {
+
+template <int NW, bool WRITE>
+__global__ void emit_kernel(const EmitParams p) {
+  const u32 seg = blockIdx.x, g = blockIdx.y;
+  const u32 col = threadIdx.x >> 5, lane = lane_id();
+  const u32 K = 64 * NW;
+  const u64 glane = (u64)g * K + col * 32 + lane;
+  const u32 src = p.lanesrc[glane];
+  const u32 valid_cols = __ballot_sync(FULL_MASK, src != NO_SOURCE);
+  const u32 *vis32 = reinterpret_cast<const u32 *>(p.vis);
+  u64 cnt = 0, hsum = 0, hxor = 0;
+  u64 pos = 0;
+  if (WRITE) pos = p.off[glane * p.segs + seg];
+  const u32 w_begin = seg * EMIT_SEG;
+  for (u32 t = 0; t < EMIT_TILES; t++) {
+    const u32 w0 = w_begin + t * 32;
+    if (w0 >= p.n) break;
+    const u32 w = w0 + lane;
+    u32 x = 0;
+    if (w < p.n) {
+      for (u32 fm = p.final_mask; fm; fm &= fm - 1) {
+        u32 q = __ffs(fm) - 1;
+        u64 word = (((u64)g * p.Q + q) * p.n + w) * NW;
+        x |= __ldcg(vis32 + word * 2 + col);
+      }
+    }
+    x &= valid_cols;
+    // transpose the 32 x 32 tile: thread j receives bit k = (w0 + k in lane 32*col + j)
+    u32 mine = 0;
+#pragma unroll
+    for (int j = 0; j < 32; j++) {
+      u32 b = __ballot_sync(FULL_MASK, (x >> j) & 1u);
+      if (lane == (u32)j) mine = b;
+    }
+    if (!mine) continue;
+    if (WRITE) {
+      for (u32 b = mine; b; b &= b - 1) p.dst[pos++] = w0 + (__ffs(b) - 1);
+    } else {
+      cnt += __popc(mine);
+      for (u32 b = mine; b; b &= b - 1) {
+        u64 h = splitmix64(((u64)src << 32) | (u64)(w0 + (__ffs(b) - 1)));
+        hsum += h;
+        hxor ^= h;
+      }
+    }
+  }
+  if (!WRITE) {
+    p.cnt[glane * p.segs + seg] = (u32)cnt;
+    hsum = warp_sum(hsum);
+    hxor = warp_xor(hxor);
+    if (lane == 0 && (hsum | hxor)) {
+      atomicAdd(&p.digest[0], hsum);
+      atomicXor(&p.digest[1], hxor);
+    }
+  }
+}
+
+cudaError_t launch_emit(int nw, bool write, const EmitParams &p, cudaStream_t st) {
+  dim3 grid(p.segs, p.G);
+  if (nw == 1) {
+    if (write)
+      emit_kernel<1, true><<<grid, 64, 0, st>>>(p);
+    else
+      emit_kernel<1, false><<<grid, 64, 0, st>>>(p);
+  } else {
+    if (write)
+      emit_kernel<4, true><<<grid, 256, 0, st>>>(p);
+    else
+      emit_kernel<4, false><<<grid, 256, 0, st>>>(p);
+  }
+  return cudaGetLastError();
+}
+
+// lane_off[i] = off[i * segs] for every lane; lane_off[n_lanes] = total.
+__global__ void gather_lane_off(const u64 *__restrict__ off, u32 segs, u32 n_lanes, const u64 *__restrict__ total,
+                                u64 *__restrict__ lane_off) {
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i <= n_lanes; i += gridDim.x * blockDim.x)
+    lane_off[i] = (i == n_lanes) ? *total : off[(u64)i * segs];
+}
+
+cudaError_t launch_gather_lane_off(const u64 *off, u32 segs, u32 n_lanes, const u64 *total, u64 *lane_off,
+                                   cudaStream_t st) {
+  gather_lane_off<<<(n_lanes + 256) / 256, 256, 0, st>>>(off, segs, n_lanes, total, lane_off);
+  return cudaGetLastError();
+}
+
+// Interleaved (src, dst) rows first .. first+count-1 of one chunk.
+__global__ void expand_pairs(const u32 *__restrict__ lanesrc, const u64 *__restrict__ lane_off, u32 n_lanes,
+                             const u32 *__restrict__ dst, u64 first, u64 count, u32 *__restrict__ out) {
+  for (u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (u64)gridDim.x * blockDim.x) {
+    u64 r = first + k;
+    // owner lane: the largest i with lane_off[i] <= r
+    u32 lo = 0, hi = n_lanes;  // lane_off[lo] <= r < lane_off[hi]
+    while (hi - lo > 1) {
+      u32 mid = (lo + hi) >> 1;
+      if (lane_off[mid] <= r)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    out[2 * k] = lanesrc[lo];
+    out[2 * k + 1] = dst[r];
+  }
+}
+
+cudaError_t launch_expand_pairs(const uint32_t *lanesrc, const u64 *lane_off, uint32_t n_lanes, const uint32_t *dst,
+                                u64 first, u64 count, uint32_t *out, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  u64 blocks = (count + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  expand_pairs<<<(unsigned)blocks, 256, 0, st>>>(lanesrc, lane_off, n_lanes, dst, first, count, out);
+  return cudaGetLastError();
+}
+
+}  // namespace rpq

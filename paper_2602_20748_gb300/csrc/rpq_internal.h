@@ -1,0 +1,159 @@
+// Internal declarations shared by the host API and the CUDA kernels of the
+// RPQ engine.  Not part of the public ABI (see include/rpq.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rpq.h"
+
+namespace rpq {
+
+// ---------------------------------------------------------------------------
+// Compiled query: the minimal DFA in the forms the kernels use.
+// ---------------------------------------------------------------------------
+struct QueryDesc {
+  uint32_t n_states;    // 0 means the empty language
+  uint32_t final_mask;  // bit q: state q accepts
+  uint32_t n_labels;    // largest label id used + 1
+  uint32_t n_trans;
+  // Top-down form: transitions leaving state q are [out_begin[q], out_begin[q+1]).
+  uint16_t out_begin[RPQ_MAX_STATES + 1];
+  uint8_t out_label[RPQ_MAX_TRANSITIONS];
+  uint8_t out_to[RPQ_MAX_TRANSITIONS];
+  // Bottom-up form: for target state q, groups [in_begin[q], in_begin[q+1]) of
+  // (label, bitmask of source states that reach q on that label).
+  uint16_t in_begin[RPQ_MAX_STATES + 1];
+  uint8_t in_label[RPQ_MAX_TRANSITIONS];
+  uint32_t in_from[RPQ_MAX_TRANSITIONS];
+};
+
+// Host-side compiled query.
+struct HostQuery {
+  QueryDesc d;
+  std::vector<int32_t> next;  // n_states * n_labels, -1 = none
+};
+
+// Parses and compiles; returns RPQ_OK or an error code with *msg set.
+int compile_regex(const char *regex, const char *const *names, uint32_t n_names, HostQuery *out, std::string *msg);
+
+// ---------------------------------------------------------------------------
+// Device-resident graph: one CSR per edge label over the full id space, for
+// out-edges (sorted by label, src, dst) and in-edges (label, dst, src).
+// off[l * (n + 1) + v] is the first edge of row v of label l.
+// ---------------------------------------------------------------------------
+struct DevGraph {
+  uint32_t n = 0;
+  uint32_t L = 0;
+  uint64_t m = 0;
+  uint32_t *out_off = nullptr;
+  uint32_t *out_col = nullptr;
+  uint32_t *in_off = nullptr;
+  uint32_t *in_col = nullptr;
+  uint8_t *vlabel = nullptr;
+  std::vector<uint64_t> label_edges;  // edges per label (host copy)
+};
+
+// ---------------------------------------------------------------------------
+// Traversal control block (device memory, one per launch).
+// ---------------------------------------------------------------------------
+enum StatIdx {
+  ST_W = 0,          // product-edge relaxations (per start vertex)
+  ST_N,              // product vertices visited (per start vertex)
+  ST_PUSH_LEVELS,
+  ST_PULL_LEVELS,
+  ST_GROUP_EDGES,    // edges read by top-down levels
+  ST_GROUP_ROWS,     // adjacency rows opened by top-down levels
+  ST_GROUP_VERTICES, // lane-group product vertices discovered
+  ST_PULL_EDGES,     // in-edges read by bottom-up levels
+  ST_PULL_VERTICES,  // (vertex, state) words examined bottom-up
+  ST_COUNT
+};
+
+struct BfsCtl {
+  unsigned int bar_count;
+  unsigned int bar_gen;
+  unsigned int err;
+  unsigned int err_where;
+  unsigned long long n_list[3];
+  unsigned long long cursor[3];
+  unsigned long long mf[3];
+  unsigned long long levels;
+  unsigned long long stats[ST_COUNT];
+};
+
+struct BfsParams {
+  // graph
+  const uint32_t *out_off;
+  const uint32_t *out_col;
+  const uint32_t *in_off;
+  const uint32_t *in_col;
+  uint32_t n;
+  uint32_t L;             // edge labels of the graph
+  // lane groups
+  uint32_t G;             // groups in this launch
+  uint32_t Q;             // DFA states
+  const uint32_t *lanesrc;  // [G * 64 * NW], 0xFFFFFFFF = empty lane
+  // workspace
+  unsigned long long *vis;     // [G][Q][n][NW]
+  unsigned long long *fr0;     // frontier ping
+  unsigned long long *fr1;     // frontier pong
+  unsigned int *claim;         // [G][Q][n] (NW > 1)
+  unsigned long long *list0;   // entries ((g*Q+q) << 32 | v)
+  unsigned long long *list1;
+  BfsCtl *ctl;
+  unsigned int stamp_base;     // claim stamps continue across launches
+  unsigned int nblocks;
+  int force;                   // 0 auto, 1 push only, 2 pull only
+  float alpha;                 // push if alpha * push_cost < pull_cost
+  double pull_cost_fixed;      // bottom-up bytes per level (all groups)
+  unsigned long long time_limit_ns;
+  QueryDesc q;
+};
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_vis_init(int nw, const BfsParams &p, const unsigned long long *empty, cudaStream_t st);
+cudaError_t launch_msbfs(int nw, const BfsParams &p, int blocks, int threads, cudaStream_t st);
+int msbfs_max_blocks(int nw, int threads, int *blocks_per_sm, int *sms);
+
+struct EmitParams {
+  const unsigned long long *vis;
+  uint32_t n;
+  uint32_t G;
+  uint32_t Q;
+  uint32_t final_mask;
+  const uint32_t *lanesrc;
+  uint32_t segs;                 // segments per group
+  uint32_t *cnt;                 // [G * K][segs]
+  const unsigned long long *off; // exclusive offsets of cnt (write pass)
+  uint32_t *dst;                 // output destinations (write pass)
+  unsigned long long *digest;    // [2]: sum, xor
+};
+constexpr int EMIT_TILES = 32;  // 32-vertex tiles per segment
+constexpr int EMIT_SEG = 32 * EMIT_TILES;
+cudaError_t launch_emit(int nw, bool write, const EmitParams &p, cudaStream_t st);
+
+cudaError_t launch_gather_lane_off(const unsigned long long *off, uint32_t segs, uint32_t n_lanes,
+                                   const unsigned long long *total, unsigned long long *lane_off, cudaStream_t st);
+
+// Pair expansion for fetch: out[2k], out[2k+1] = (src, dst) of row first + k.
+cudaError_t launch_expand_pairs(const uint32_t *lanesrc, const unsigned long long *lane_off, uint32_t n_lanes,
+                                const uint32_t *dst, unsigned long long first, unsigned long long count,
+                                uint32_t *out, cudaStream_t st);
+
+// Device-wide exclusive scans.  `tmp` must hold scan_tmp_words(n) words.
+size_t scan_tmp_words(size_t n);
+cudaError_t exclusive_scan_u32_to_u64(const uint32_t *in, unsigned long long *out, size_t n,
+                                      unsigned long long *total, unsigned long long *tmp, cudaStream_t st);
+cudaError_t exclusive_scan_u64(const unsigned long long *in, unsigned long long *out, size_t n,
+                               unsigned long long *total, unsigned long long *tmp, cudaStream_t st);
+
+// Graph construction.  Returns RPQ_OK or an error code with *msg set.
+int build_graph(DevGraph *g, uint32_t n, uint32_t L, uint64_t m, const uint32_t *d_src, const uint32_t *d_dst,
+                const uint16_t *d_lab, cudaStream_t st, std::string *msg);
+int graph_key_bits(uint32_t n, uint32_t L);
+
+}  // namespace rpq

@@ -1,0 +1,268 @@
+"""ctypes binding of the C ABI in include/rpq.h (argument marshalling only).
+
+Every computation happens in the CUDA library ``_build/librpq.so``; this
+module converts numpy arrays and Python strings to pointers and sizes and
+raises :class:`RPQError` on negative return codes.  Importing it fails
+loudly when the library has not been built: there is no fallback.
+
+The functions keep the C names (``load_graph``, ``compile_rpq``, ``run_rpq``,
+``run_rpq_range``, ``run_crpq``, ``fetch_pairs`` ...).  Handles are wrapped in
+small classes whose ``free()`` (also called on garbage collection) calls the
+matching ``free_*``.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librpq.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"the CUDA library {LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+RPQ_OK = 0
+RPQ_ERR_INVALID_ARG = -1
+RPQ_ERR_PARSE = -2
+RPQ_ERR_UNKNOWN_LABEL = -3
+RPQ_ERR_TOO_COMPLEX = -4
+RPQ_ERR_OUT_OF_BUDGET = -5
+RPQ_ERR_CUDA = -6
+RPQ_ERR_TIMEOUT = -7
+RPQ_ERR_NO_DEVICE = -8
+
+RPQ_MATERIALIZE = 0x1
+RPQ_COUNT_ONLY = 0x2
+RPQ_FORCE_PUSH = 0x100
+RPQ_FORCE_PULL = 0x200
+
+RPQ_MAX_STATES = 32
+RPQ_MAX_LABELS = 64
+
+EXPORTED = [
+    "rpq_create", "rpq_destroy", "rpq_last_error", "rpq_set_stream", "load_graph", "graph_info", "free_graph",
+    "compile_rpq", "query_info", "free_query", "run_rpq", "run_rpq_range", "run_crpq", "result_info",
+    "result_stats", "fetch_pairs", "free_result",
+]
+
+c_void_p = ctypes.c_void_p
+c_u32 = ctypes.c_uint32
+c_u64 = ctypes.c_uint64
+P = ctypes.POINTER
+
+
+class rpq_stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_uint64) for name in (
+        "product_edges", "product_vertices", "levels", "push_levels", "pull_levels", "group_edges", "group_rows",
+        "group_vertices", "pull_edges", "pull_vertices", "lane_words", "lane_groups")] + [
+        ("bfs_ms", ctypes.c_double), ("emit_ms", ctypes.c_double), ("bfs_launches", ctypes.c_uint64),
+        ("launches", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class crpq_atom(ctypes.Structure):
+    _fields_ = [("x", c_u32), ("y", c_u32), ("q", c_void_p)]
+
+
+_lib.rpq_create.argtypes = [P(c_void_p), ctypes.c_int, c_u64, c_void_p]
+_lib.rpq_destroy.argtypes = [c_void_p]
+_lib.rpq_destroy.restype = None
+_lib.rpq_last_error.argtypes = [c_void_p]
+_lib.rpq_last_error.restype = ctypes.c_char_p
+_lib.rpq_set_stream.argtypes = [c_void_p, c_void_p]
+_lib.load_graph.argtypes = [c_void_p, c_u32, c_u32, c_u64, c_void_p, c_void_p, c_void_p, c_void_p, P(c_void_p)]
+_lib.graph_info.argtypes = [c_void_p, P(c_u32), P(c_u32), P(c_u64)]
+_lib.free_graph.argtypes = [c_void_p]
+_lib.free_graph.restype = None
+_lib.compile_rpq.argtypes = [c_void_p, ctypes.c_char_p, c_void_p, c_u32, P(c_void_p)]
+_lib.query_info.argtypes = [c_void_p, P(c_u32), P(c_u32), P(c_u64), c_void_p]
+_lib.free_query.argtypes = [c_void_p]
+_lib.free_query.restype = None
+_lib.run_rpq.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_u32, c_u32, P(c_void_p)]
+_lib.run_rpq_range.argtypes = [c_void_p, c_void_p, c_void_p, c_u32, c_u32, c_u32, P(c_void_p)]
+_lib.run_crpq.argtypes = [c_void_p, c_void_p, c_u32, c_void_p, c_void_p, c_u32, c_void_p, c_u32, c_u32,
+                          P(c_void_p)]
+_lib.result_info.argtypes = [c_void_p, P(c_u64), P(c_u32), P(c_u64), P(c_u64)]
+_lib.result_stats.argtypes = [c_void_p, P(rpq_stats)]
+_lib.fetch_pairs.argtypes = [c_void_p, c_u64, c_u64, c_void_p, P(c_u64)]
+_lib.free_result.argtypes = [c_void_p]
+_lib.free_result.restype = None
+
+
+class RPQError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"rpq error {code}: {msg}")
+        self.code = code
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(c_void_p)
+
+
+class Context:
+    """rpq_create / rpq_destroy.  ``stream`` is a raw cudaStream_t handle
+    (e.g. ``torch.cuda.current_stream().cuda_stream``) or None."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, stream: int | None = None):
+        h = c_void_p()
+        rc = _lib.rpq_create(ctypes.byref(h), device, mem_budget_bytes, stream)
+        if rc != 0:
+            raise RPQError(rc, _lib.rpq_last_error(None).decode())
+        self.h = h
+        self.device = device
+
+    def check(self, rc: int):
+        if rc != 0:
+            raise RPQError(rc, _lib.rpq_last_error(self.h).decode())
+
+    def set_stream(self, stream: int | None):
+        self.check(_lib.rpq_set_stream(self.h, stream))
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.rpq_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+
+class Graph:
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+
+    def info(self):
+        n, L, m = c_u32(), c_u32(), c_u64()
+        self.ctx.check(_lib.graph_info(self.h, ctypes.byref(n), ctypes.byref(L), ctypes.byref(m)))
+        return n.value, L.value, m.value
+
+    def free(self):
+        if self.h:
+            _lib.free_graph(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.free()
+
+
+class Query:
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+
+    def free(self):
+        if self.h:
+            _lib.free_query(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.free()
+
+
+class Result:
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+
+    def free(self):
+        if self.h:
+            _lib.free_result(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.free()
+
+
+def load_graph(ctx: Context, n_vertices: int, n_labels: int, src, dst, label, vertex_label=None) -> Graph:
+    src = np.ascontiguousarray(src, dtype=np.uint32)
+    dst = np.ascontiguousarray(dst, dtype=np.uint32)
+    label = np.ascontiguousarray(label, dtype=np.uint16)
+    vl = None if vertex_label is None else np.ascontiguousarray(vertex_label, dtype=np.uint8)
+    if not (len(src) == len(dst) == len(label)):
+        raise ValueError("src, dst and label must have the same length")
+    h = c_void_p()
+    ctx.check(_lib.load_graph(ctx.h, n_vertices, n_labels, len(src), _ptr(src), _ptr(dst), _ptr(label), _ptr(vl),
+                              ctypes.byref(h)))
+    return Graph(ctx, h)
+
+
+def compile_rpq(ctx: Context, regex: str, label_names=None) -> Query:
+    h = c_void_p()
+    if label_names is None:
+        ctx.check(_lib.compile_rpq(ctx.h, regex.encode(), None, 0, ctypes.byref(h)))
+    else:
+        arr = (ctypes.c_char_p * len(label_names))(*[n.encode() for n in label_names])
+        ctx.check(_lib.compile_rpq(ctx.h, regex.encode(), ctypes.cast(arr, c_void_p), len(label_names),
+                                   ctypes.byref(h)))
+    return Query(ctx, h)
+
+
+def query_info(q: Query):
+    """(n_states, final_mask, next[n_states, n_labels_out]) of the minimal DFA."""
+    ns, nl, fm = c_u32(), c_u32(), c_u64()
+    q.ctx.check(_lib.query_info(q.h, ctypes.byref(ns), ctypes.byref(nl), ctypes.byref(fm), None))
+    nxt = np.full(max(1, ns.value * nl.value), -1, dtype=np.int32)
+    q.ctx.check(_lib.query_info(q.h, None, None, None, _ptr(nxt)))
+    return ns.value, fm.value, nxt[: ns.value * nl.value].reshape(ns.value, nl.value)
+
+
+def run_rpq(ctx: Context, g: Graph, q: Query, sources=None, flags: int = RPQ_MATERIALIZE) -> Result:
+    h = c_void_p()
+    if sources is None:
+        ctx.check(_lib.run_rpq(ctx.h, g.h, q.h, None, 0, flags, ctypes.byref(h)))
+    else:
+        s = np.ascontiguousarray(sources, dtype=np.uint32)
+        ctx.check(_lib.run_rpq(ctx.h, g.h, q.h, _ptr(s), len(s), flags, ctypes.byref(h)))
+    return Result(ctx, h)
+
+
+def run_rpq_range(ctx: Context, g: Graph, q: Query, src_begin: int, src_end: int,
+                  flags: int = RPQ_MATERIALIZE) -> Result:
+    h = c_void_p()
+    ctx.check(_lib.run_rpq_range(ctx.h, g.h, q.h, src_begin, src_end, flags, ctypes.byref(h)))
+    return Result(ctx, h)
+
+
+def run_crpq(ctx: Context, g: Graph, n_vars: int, atoms, var_label=None, restrict0=None,
+             flags: int = RPQ_MATERIALIZE) -> Result:
+    """``atoms``: list of (x, Query, y)."""
+    arr = (crpq_atom * len(atoms))(*[crpq_atom(a[0], a[2], a[1].h) for a in atoms])
+    vl = None if var_label is None else np.ascontiguousarray(var_label, dtype=np.int32)
+    r0 = None if restrict0 is None else np.ascontiguousarray(restrict0, dtype=np.uint32)
+    h = c_void_p()
+    ctx.check(_lib.run_crpq(ctx.h, g.h, n_vars, _ptr(vl), ctypes.cast(arr, c_void_p), len(atoms), _ptr(r0),
+                            0 if r0 is None else len(r0), flags, ctypes.byref(h)))
+    return Result(ctx, h)
+
+
+def result_info(r: Result):
+    """(count, arity, digest_sum, digest_xor)."""
+    n, a, s, x = c_u64(), c_u32(), c_u64(), c_u64()
+    r.ctx.check(_lib.result_info(r.h, ctypes.byref(n), ctypes.byref(a), ctypes.byref(s), ctypes.byref(x)))
+    return n.value, a.value, s.value, x.value
+
+
+def result_stats(r: Result) -> dict:
+    st = rpq_stats()
+    r.ctx.check(_lib.result_stats(r.h, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def fetch_pairs(r: Result, offset: int = 0, max_rows: int | None = None, out: np.ndarray | None = None):
+    """Rows [offset, offset + max_rows) as an (k, arity) uint32 array.  ``out``
+    may be a preallocated (pinned) uint32 buffer of at least arity*k values."""
+    count, arity, _, _ = result_info(r)
+    if max_rows is None:
+        max_rows = max(0, count - offset)
+    k = max(0, min(max_rows, count - offset))
+    if out is None:
+        out = np.empty(max(1, k * arity), dtype=np.uint32)
+    got = c_u64()
+    r.ctx.check(_lib.fetch_pairs(r.h, offset, k, _ptr(out), ctypes.byref(got)))
+    return out[: got.value * arity].reshape(got.value, arity)

@@ -315,3 +315,10 @@ def test_pair_digest_is_order_independent():
     d2 = oracle.pair_digest(rows[::-1].copy())
     assert d1 == d2 and d1[0] == 3
     assert oracle.pair_digest(np.zeros((0, 2), np.uint32)) == (0, 0, 0)
+
+
+def test_label_names_with_groups():
+    names = ["knows", "likes"]
+    g = oracle.Graph(3, 2, np.array([0, 1], np.uint32), np.array([1, 2], np.uint32), np.array([0, 1], np.uint16))
+    assert as_set(oracle.rpq(g, "knows(likes)*", names=names).rows) == {(0, 1), (0, 2)}
+    assert as_set(oracle.rpq(g, "(knows|likes)+", names=names).rows) == {(0, 1), (0, 2), (1, 2)}
