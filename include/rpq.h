@@ -30,8 +30,8 @@
  *     failure (for PARSE errors it contains the byte position).
  *   * Input arrays are host pointers, read during the call and never kept:
  *     the caller keeps ownership.  Handles (rpq_graph, rpq_query, rpq_result)
- *     are owned by the caller after creation and must be released with the
- *     matching free_* function before rpq_destroy of their context.
+ *     are owned by the caller after creation and are released with the
+ *     matching free_* function, before or after rpq_destroy of their context.
  *   * Result rows are distinct and sorted ascending lexicographically as
  *     unsigned 32-bit values: (src, dst) for an RPQ, the variables in
  *     declaration order for a CRPQ.
@@ -70,6 +70,7 @@ extern "C" {
 /* ---- flags for run_rpq / run_rpq_range / run_crpq ------------------------ */
 #define RPQ_MATERIALIZE 0x1u   /* keep result rows on the device (fetch_pairs) */
 #define RPQ_COUNT_ONLY 0x2u    /* count rows and digest them; keep no rows    */
+#define RPQ_REVERSE 0x4u       /* evaluate from the target end (see run_rpq)  */
 #define RPQ_FORCE_PUSH 0x100u  /* every level expands top-down (testing)      */
 #define RPQ_FORCE_PULL 0x200u  /* every level expands bottom-up (testing)     */
 
@@ -89,8 +90,11 @@ typedef struct rpq_result rpq_result;
  * Errors: INVALID_ARG (out == NULL), CUDA (device unavailable). */
 int rpq_create(rpq_ctx **out, int device, uint64_t mem_budget_bytes, void *cuda_stream);
 
-/* Waits for the context's stream and releases its workspace.  Handles made
- * with the context must have been freed.  NULL is ignored. */
+/* Waits for the context's stream and releases its workspace.  If graphs or
+ * results made with the context are still alive, the release is deferred
+ * until the last of them is freed (so handles may be freed in any order);
+ * the context must not be used for new work after this call.  NULL is
+ * ignored. */
 void rpq_destroy(rpq_ctx *ctx);
 
 /* Text of the last error on this context ("" if none).  Valid until the next
@@ -150,8 +154,13 @@ void free_query(rpq_query *q);
  * sources[0 .. n_sources-1] (duplicates ignored).  sources == NULL with
  * n_sources == 0 means every vertex (all-pairs).  flags: exactly one of
  * RPQ_MATERIALIZE or RPQ_COUNT_ONLY, optionally one RPQ_FORCE_* (testing).
+ * With RPQ_REVERSE the listed vertices are targets instead: the rows are the
+ * pairs (y, x) with x -rho-> y for every listed y, found by traversing
+ * in-edges with the minimal DFA of the reversed language (the reverse plan
+ * of Section 2.3 / the in-edge direction of Section 6.3); sorted by y, x.
  * Errors: INVALID_ARG (source out of range, bad flags), OUT_OF_BUDGET,
- * CUDA, TIMEOUT. */
+ * CUDA, TIMEOUT, TOO_COMPLEX (RPQ_REVERSE and the reversed language needs
+ * more than RPQ_MAX_STATES states). */
 int run_rpq(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, const uint32_t *sources, uint32_t n_sources,
             uint32_t flags, rpq_result **out);
 

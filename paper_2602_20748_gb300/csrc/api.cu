@@ -48,6 +48,8 @@ struct rpq_ctx {
   float alpha = 4.0f;
   uint64_t time_limit_ns = 20ull * 1000 * 1000 * 1000;
   uint32_t max_groups = 16;
+  int live = 0;          // graphs and results not yet freed
+  bool closing = false;  // rpq_destroy was called while handles were live
 };
 
 struct rpq_graph {
@@ -202,7 +204,10 @@ void free_chunk(rpq_ctx *ctx, Chunk &c) {
 int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::vector<uint32_t> &srcs,
              uint32_t flags, rpq_result *res) {
   const DevGraph &g = gr->g;
-  const QueryDesc &qd = qr->hq.d;
+  const bool reverse = (flags & RPQ_REVERSE) != 0;
+  if (reverse && !qr->hq.has_rev)
+    return set_err(ctx, RPQ_ERR_TOO_COMPLEX, "the reversed language needs more than RPQ_MAX_STATES states");
+  const QueryDesc &qd = reverse ? qr->hq.rev : qr->hq.d;
   const uint32_t Q = qd.n_states;
   const bool materialize = (flags & RPQ_MATERIALIZE) != 0;
   res->stats.lane_words = srcs.size() <= 64 ? 1 : 4;
@@ -263,10 +268,11 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
 
     BfsParams p;
     std::memset(&p, 0, sizeof(p));
-    p.out_off = g.out_off;
-    p.out_col = g.out_col;
-    p.in_off = g.in_off;
-    p.in_col = g.in_col;
+    // the reverse traversal is the forward one on the transposed graph
+    p.out_off = reverse ? g.in_off : g.out_off;
+    p.out_col = reverse ? g.in_col : g.out_col;
+    p.in_off = reverse ? g.out_off : g.in_off;
+    p.in_col = reverse ? g.out_col : g.in_col;
     p.n = n;
     p.L = g.L;
     p.G = Gb;
@@ -395,7 +401,7 @@ int check_rpq_flags(rpq_ctx *ctx, uint32_t flags) {
     return set_err(ctx, RPQ_ERR_INVALID_ARG, "flags need exactly one of RPQ_MATERIALIZE, RPQ_COUNT_ONLY");
   if ((flags & RPQ_FORCE_PUSH) && (flags & RPQ_FORCE_PULL))
     return set_err(ctx, RPQ_ERR_INVALID_ARG, "RPQ_FORCE_PUSH and RPQ_FORCE_PULL are exclusive");
-  if (flags & ~(RPQ_MATERIALIZE | RPQ_COUNT_ONLY | RPQ_FORCE_PUSH | RPQ_FORCE_PULL))
+  if (flags & ~(RPQ_MATERIALIZE | RPQ_COUNT_ONLY | RPQ_REVERSE | RPQ_FORCE_PUSH | RPQ_FORCE_PULL))
     return set_err(ctx, RPQ_ERR_INVALID_ARG, "unknown flag bits");
   return RPQ_OK;
 }
@@ -404,6 +410,7 @@ int run_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, std::vecto
                 rpq_result **out) {
   rpq_result *r = new rpq_result;
   r->ctx = ctx;
+  ctx->live++;
   r->arity = 2;
   r->materialized = (flags & RPQ_MATERIALIZE) != 0;
   std::memset(&r->stats, 0, sizeof(r->stats));
@@ -463,8 +470,11 @@ int rpq_create(rpq_ctx **out, int device, uint64_t mem_budget_bytes, void *cuda_
   return RPQ_OK;
 }
 
-void rpq_destroy(rpq_ctx *c) {
-  if (!c) return;
+}  // extern "C"
+
+namespace {
+
+void destroy_now(rpq_ctx *c) {
   if (c->device >= 0) {
     cudaSetDevice(c->device);
     free_workspace(c);
@@ -475,6 +485,22 @@ void rpq_destroy(rpq_ctx *c) {
       if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   }
   delete c;
+}
+
+// A graph or result was freed; finish a deferred rpq_destroy.
+void release_handle(rpq_ctx *c) {
+  c->live--;
+  if (c->closing && c->live <= 0) destroy_now(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+void rpq_destroy(rpq_ctx *c) {
+  if (!c) return;
+  c->closing = true;
+  if (c->live <= 0) destroy_now(c);
 }
 
 const char *rpq_last_error(const rpq_ctx *c) { return c ? c->err.c_str() : g_create_error.c_str(); }
@@ -500,6 +526,7 @@ int load_graph(rpq_ctx *ctx, uint32_t n_vertices, uint32_t n_labels, uint64_t n_
     return set_err(ctx, RPQ_ERR_INVALID_ARG, "graph too large for 64-bit edge keys");
   rpq_graph *gr = new rpq_graph;
   gr->ctx = ctx;
+  ctx->live++;
   uint32_t *d_src = nullptr, *d_dst = nullptr;
   uint16_t *d_lab = nullptr;
   int rc = RPQ_OK;
@@ -511,6 +538,7 @@ int load_graph(rpq_ctx *ctx, uint32_t n_vertices, uint32_t n_labels, uint64_t n_
   const uint64_t scratch = m * 30 + (64ull << 20);
   if (ctx->used + gbytes + scratch + m * 10 > ctx->budget) {
     delete gr;
+    release_handle(ctx);
     return set_err(ctx, RPQ_ERR_OUT_OF_BUDGET, "graph does not fit the device memory budget");
   }
   cudaStream_t st = ctx->stream;
@@ -533,6 +561,7 @@ int load_graph(rpq_ctx *ctx, uint32_t n_vertices, uint32_t n_labels, uint64_t n_
   if (vertex_label) {
     rc = dalloc(ctx, &gr->g.vlabel, n_vertices);
     if (rc) goto fail;
+    gr->g.vlabel_host.assign(vertex_label, vertex_label + n_vertices);
     cudaError_t e = cudaMemcpyAsync(gr->g.vlabel, vertex_label, n_vertices, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) {
       rc = cuda_err(ctx, e, "cudaMemcpyAsync");
@@ -569,6 +598,7 @@ fail:
   if (gr->g.in_col) cudaFreeAsync(gr->g.in_col, st);
   if (gr->g.vlabel) dfree(ctx, gr->g.vlabel, n_vertices);
   delete gr;
+  release_handle(ctx);
   return rc;
 }
 
@@ -592,6 +622,7 @@ void free_graph(rpq_graph *g) {
   ctx->used -= std::min(ctx->used, g->bytes);
   if (g->g.vlabel) dfree(ctx, g->g.vlabel, g->g.n);
   delete g;
+  release_handle(ctx);
 }
 
 int compile_rpq(rpq_ctx *ctx, const char *regex, const char *const *label_names, uint32_t n_names,
@@ -732,6 +763,7 @@ void free_result(rpq_result *r) {
     if (r->tuples) dev_free(ctx, r->tuples, r->tuple_bytes);
   }
   delete r;
+  if (ctx) release_handle(ctx);
 }
 
 }  // extern "C"
@@ -749,12 +781,12 @@ const HostQuery &query_host(const rpq_query *q) { return q->hq; }
 // Runs an RPQ from the given sorted distinct sources, materialized, and hands
 // back the per-lane CSR chunks (ownership passes to the caller).
 int rpq_rows_for_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, std::vector<uint32_t> &srcs,
-                         std::vector<RowChunk> *chunks, rpq_stats *stats) {
+                         bool reverse, std::vector<RowChunk> *chunks, rpq_stats *stats) {
   rpq_result r;
   r.ctx = ctx;
   r.materialized = true;
   std::memset(&r.stats, 0, sizeof(r.stats));
-  int rc = eval_rpq(ctx, g, q, srcs, RPQ_MATERIALIZE, &r);
+  int rc = eval_rpq(ctx, g, q, srcs, RPQ_MATERIALIZE | (reverse ? RPQ_REVERSE : 0u), &r);
   if (stats) {
     stats->product_edges += r.stats.product_edges;
     stats->product_vertices += r.stats.product_vertices;
@@ -799,6 +831,7 @@ int make_tuple_result(rpq_ctx *ctx, uint32_t arity, u32 *tuples, uint64_t rows, 
                       bool materialized, const rpq_stats &stats, rpq_result **out) {
   rpq_result *r = new rpq_result;
   r->ctx = ctx;
+  ctx->live++;
   r->arity = arity;
   r->count = rows;
   r->dsum = dsum;

@@ -1,11 +1,683 @@
-// CRPQ evaluation (Definition 2).
+// CRPQ evaluation (Definition 2, Section 2.1) on the device.
+//
+// The paper materializes the result of every RPQ atom and combines them with
+// a worst-case optimal join, choosing per atom the direction the matching
+// order needs (Section 6.3).  This module does the same kind of join,
+// variable at a time, with all data on the device:
+//
+//   * Variables are bound in a fixed order that starts with variable 0 (whose
+//     values are processed in batches, so batches come out in order) and then
+//     repeatedly takes the variable with the most atoms to bound variables.
+//   * Each atom constrains the later-bound of its two variables.  An atom
+//     x -rho-> y whose x is bound first is evaluated forward from the distinct
+//     bound x values; one whose y is bound first is evaluated from the target
+//     end (reversed language over in-edges) from the distinct y values.  Both
+//     give, per bound value, a sorted row of admissible values for the new
+//     variable.  A self-loop atom x -rho-> x is checked once x is bound.
+//   * Binding a variable: per partial tuple, the constraint with the shortest
+//     row generates the candidates (the smallest-first intersection of worst
+//     case optimal joins); every other constraint is a membership test by
+//     binary search in its sorted row; vertex labels are tested too.  The
+//     surviving (tuple, value) pairs are compacted into the next table.
+//     Candidates are processed in slices of bounded size.
+//   * Complete tuples of a batch are sorted lexicographically in declaration
+//     order (stable LSD passes over the columns) and digested.
+#include <algorithm>
+#include <cstring>
+#include <functional>
+#include <numeric>
+#include <vector>
+
 #include "crpq.h"
 
 namespace rpq {
+namespace {
 
-int crpq_eval(rpq_ctx *ctx, const rpq_graph *, uint32_t, const int32_t *, const crpq_atom *, uint32_t,
-              const uint32_t *, uint32_t, uint32_t, rpq_result **) {
-  return ctx_error(ctx, RPQ_ERR_INVALID_ARG, "run_crpq is not available yet");
+constexpr uint64_t CAND_CAP = 1ull << 26;  // candidate pairs per expansion slice
+constexpr uint32_t BATCH0 = 4096;          // values of variable 0 per batch
+constexpr int MAXC = RPQ_MAX_ATOMS;
+
+struct DevRows {  // sorted rows of one atom for a sorted set of endpoint values
+  const u32 *src;
+  const u64 *beg;
+  const u32 *len;
+  const u32 *dst;
+  u32 ns;
+};
+
+struct Cons {
+  DevRows rows;
+  const u32 *col;  // bound endpoint's column; nullptr: the variable being bound
+};
+
+struct StepParams {
+  u32 nc;
+  u32 gen_mask;  // constraints that may generate candidates
+  int want_label;
+  const uint8_t *vlabel;
+  Cons c[MAXC];
+};
+
+struct ColPtrs {
+  const u32 *in[RPQ_MAX_VARS];
+  u32 *out[RPQ_MAX_VARS + 1];
+};
+
+__device__ __forceinline__ bool lookup(const DevRows &r, u32 v, u64 *b, u32 *l) {
+  u32 lo = 0, hi = r.ns;
+  while (lo < hi) {
+    u32 mid = (lo + hi) >> 1;
+    u32 s = r.src[mid];
+    if (s < v)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  if (lo < r.ns && r.src[lo] == v) {
+    *b = r.beg[lo];
+    *l = r.len[lo];
+    return true;
+  }
+  *b = 0;
+  *l = 0;
+  return false;
+}
+
+__device__ __forceinline__ bool row_has(const u32 *dst, u64 b, u32 l, u32 y) {
+  u32 lo = 0, hi = l;
+  while (lo < hi) {
+    u32 mid = (lo + hi) >> 1;
+    u32 s = dst[b + mid];
+    if (s < y)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo < l && dst[b + lo] == y;
+}
+
+// Per tuple: the generating constraint (shortest row) and its length.
+__global__ void choose_gen(const StepParams p, u64 nT, u32 *__restrict__ cnt, uint8_t *__restrict__ which) {
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < nT; i += (u64)gridDim.x * blockDim.x) {
+    u32 best = 0xffffffffu, w = 0xff;
+    for (u32 k = 0; k < p.nc; k++) {
+      if (!(p.gen_mask >> k & 1u)) continue;
+      u64 b;
+      u32 l;
+      lookup(p.c[k].rows, p.c[k].col[i], &b, &l);
+      if (l < best) {
+        best = l;
+        w = k;
+      }
+    }
+    cnt[i] = (w == 0xff) ? 0u : best;
+    which[i] = (uint8_t)w;
+  }
+}
+
+// Candidates first .. first+n-1 of the expansion (global candidate index j
+// belongs to the tuple i with off[i] <= j < off[i+1]).
+__global__ void expand_cands(const StepParams p, u64 nT, const u64 *__restrict__ off,
+                             const uint8_t *__restrict__ which, u64 first, u64 n, u32 *__restrict__ cand_t,
+                             u32 *__restrict__ cand_v) {
+  for (u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (u64)gridDim.x * blockDim.x) {
+    u64 j = first + k;
+    u64 lo = 0, hi = nT;  // off[lo] <= j < off[hi]
+    while (hi - lo > 1) {
+      u64 mid = (lo + hi) >> 1;
+      if (off[mid] <= j)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    const Cons &c = p.c[which[lo]];
+    u64 b;
+    u32 l;
+    lookup(c.rows, c.col[lo], &b, &l);
+    cand_t[k] = (u32)lo;
+    cand_v[k] = c.rows.dst[b + (j - off[lo])];
+  }
+}
+
+// flag[j] = candidate j passes the label test and every constraint except
+// its generator.
+__global__ void filter_cands(const StepParams p, u64 n, const u32 *__restrict__ cand_t, const u32 *__restrict__ cand_v,
+                             const uint8_t *__restrict__ which, u32 *__restrict__ flag) {
+  for (u64 j = (u64)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (u64)gridDim.x * blockDim.x) {
+    u32 y = cand_v[j];
+    bool ok = p.want_label < 0 || p.vlabel[y] == (uint8_t)p.want_label;
+    u32 skip = which ? which[cand_t[j]] : 0xffu;
+    for (u32 k = 0; k < p.nc && ok; k++) {
+      if (k == skip) continue;
+      u32 x = p.c[k].col ? p.c[k].col[cand_t[j]] : y;
+      u64 b;
+      u32 l;
+      lookup(p.c[k].rows, x, &b, &l);
+      ok = row_has(p.c[k].rows.dst, b, l, y);
+    }
+    flag[j] = ok ? 1u : 0u;
+  }
+}
+
+__global__ void compact_cands(u64 n, const u32 *__restrict__ flag, const u64 *__restrict__ pos,
+                              const u32 *__restrict__ cand_t, const u32 *__restrict__ cand_v, u32 ncols,
+                              const ColPtrs cols) {
+  for (u64 j = (u64)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (u64)gridDim.x * blockDim.x) {
+    if (!flag[j]) continue;
+    u64 o = pos[j];
+    u32 t = cand_t ? cand_t[j] : 0;
+    for (u32 c = 0; c < ncols; c++) cols.out[c][o] = cols.in[c][t];
+    cols.out[ncols][o] = cand_v[j];
+  }
+}
+
+__global__ void rows_index(const u32 *__restrict__ lanesrc, const u64 *__restrict__ lane_off, u32 n_lanes,
+                           u32 lane_base, u64 dst_base, u32 *__restrict__ src, u64 *__restrict__ beg,
+                           u32 *__restrict__ len) {
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n_lanes; i += gridDim.x * blockDim.x) {
+    u32 s = lanesrc[i];
+    if (s == NO_SOURCE) continue;
+    src[lane_base + i] = s;
+    beg[lane_base + i] = dst_base + lane_off[i];
+    len[lane_base + i] = (u32)(lane_off[i + 1] - lane_off[i]);
+  }
+}
+
+__global__ void widen_u32(const u32 *__restrict__ v, u64 n, u64 *__restrict__ keys) {
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) keys[i] = v[i];
+}
+
+__global__ void narrow_u64(const u64 *__restrict__ keys, u64 n, u32 *__restrict__ v) {
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
+    v[i] = (u32)keys[i];
+}
+
+__global__ void sort_keys_from_perm(const u32 *__restrict__ col, const u32 *__restrict__ perm, u64 n,
+                                    u64 *__restrict__ keys) {
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
+    u32 r = perm ? perm[i] : (u32)i;
+    keys[i] = ((u64)col[r] << 32) | r;
+  }
+}
+
+__global__ void gather_rows(const ColPtrs cols, u32 arity, const u32 *__restrict__ perm, u64 n,
+                            u32 *__restrict__ out) {
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
+    u32 r = perm[i];
+    for (u32 c = 0; c < arity; c++) out[i * arity + c] = cols.in[c][r];
+  }
+}
+
+// Digest of tuples given as declaration-order columns (see result_info).
+__global__ void digest_rows(const ColPtrs cols, u32 arity, u64 n, u64 *__restrict__ digest) {
+  u64 s = 0, x = 0;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
+    u64 h;
+    if (arity == 1) {
+      h = splitmix64((u64)cols.in[0][i]);
+    } else {
+      h = splitmix64(((u64)cols.in[0][i] << 32) | (u64)cols.in[1][i]);
+      for (u32 c = 2; c < arity; c++) h = splitmix64(h ^ (u64)cols.in[c][i]);
+    }
+    s += h;
+    x ^= h;
+  }
+  s = warp_sum(s);
+  x = warp_xor(x);
+  if (lane_id() == 0 && (s | x)) {
+    atomicAdd(&digest[0], s);
+    atomicXor(&digest[1], x);
+  }
+}
+
+unsigned grid1(u64 n) {
+  u64 b = (n + 255) / 256;
+  if (b > 152ull * 32) b = 152ull * 32;
+  return (unsigned)(b ? b : 1);
+}
+
+// Device buffer owned through the context's budget.
+template <typename T>
+struct Buf {
+  rpq_ctx *ctx = nullptr;
+  T *p = nullptr;
+  uint64_t n = 0;
+  int alloc(rpq_ctx *c, uint64_t count) {
+    release();
+    ctx = c;
+    n = count;
+    return ctx_alloc(c, (void **)&p, std::max<uint64_t>(count, 1) * sizeof(T));
+  }
+  void release() {
+    if (p) ctx_free(ctx, p, std::max<uint64_t>(n, 1) * sizeof(T));
+    p = nullptr;
+    n = 0;
+  }
+  ~Buf() { release(); }
+};
+
+struct OwnedRows {
+  Buf<u32> src, len, dst;
+  Buf<u64> beg;
+  u32 ns = 0;
+  DevRows view() const { return DevRows{src.p, beg.p, len.p, dst.p, ns}; }
+};
+
+struct Table {
+  std::vector<Buf<u32>> cols;  // binding order
+  uint64_t n = 0;
+};
+
+struct Engine {
+  rpq_ctx *ctx;
+  const rpq_graph *g;
+  const DevGraph &dg;
+  cudaStream_t st;
+  uint32_t n_vars;
+  const int32_t *var_label;
+  const crpq_atom *atoms;
+  bool materialize;
+  std::vector<int> order, pos;
+  struct C {
+    uint32_t atom;
+    int bound_pos;  // -1: self-loop on the variable being bound
+    bool reverse;
+  };
+  std::vector<std::vector<C>> cons;
+  rpq_stats stats;
+  uint64_t count = 0, dsum = 0, dxor = 0;
+  Buf<u64> small;                       // digest accumulators, counters
+  std::vector<Table> batch_out;         // complete tables of the current batch
+  std::vector<std::pair<u32 *, uint64_t>> out_chunks;  // sorted row-major batches
+
+  Engine(rpq_ctx *c, const rpq_graph *gr) : ctx(c), g(gr), dg(graph_dev(gr)), st(ctx_stream(c)) {
+    std::memset(&stats, 0, sizeof(stats));
+  }
+
+  int cuda(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return RPQ_OK;
+    return ctx_error(ctx, RPQ_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  }
+
+  int label_of(uint32_t var) const { return var_label ? var_label[var] : -1; }
+
+  // Distinct values of a device column, ascending, on the host.
+  int distinct(const u32 *col, uint64_t n, std::vector<uint32_t> *out) {
+    out->clear();
+    if (n == 0) return RPQ_OK;
+    Buf<u64> a, b;
+    int rc;
+    if ((rc = a.alloc(ctx, n)) || (rc = b.alloc(ctx, n))) return rc;
+    widen_u32<<<grid1(n), 256, 0, st>>>(col, n, a.p);
+    if ((rc = cuda(cudaGetLastError(), "widen_u32"))) return rc;
+    u64 *pa = a.p, *pb = b.p;
+    if ((rc = cuda(sort_keys_u64(&pa, &pb, n, 0, 32, st), "sort"))) return rc;
+    if ((rc = cuda(unique_keys_u64(pa, n, pb, small.p + 2, st), "unique"))) return rc;
+    u64 k = 0;
+    if ((rc = cuda(cudaMemcpyAsync(&k, small.p + 2, 8, cudaMemcpyDeviceToHost, st), "copy"))) return rc;
+    if ((rc = cuda(cudaStreamSynchronize(st), "sync"))) return rc;
+    std::vector<u64> tmp(k);
+    if (k && (rc = cuda(cudaMemcpyAsync(tmp.data(), pb, k * 8, cudaMemcpyDeviceToHost, st), "copy"))) return rc;
+    if ((rc = cuda(cudaStreamSynchronize(st), "sync"))) return rc;
+    out->resize(k);
+    for (u64 i = 0; i < k; i++) (*out)[i] = (uint32_t)tmp[i];
+    return RPQ_OK;
+  }
+
+  // Rows of atom `a` for the given sorted distinct values.
+  int rows_for(uint32_t a, bool reverse, std::vector<uint32_t> &vals, OwnedRows *r) {
+    std::vector<RowChunk> chunks;
+    int rc = rpq_rows_for_sources(ctx, g, atoms[a].q, vals, reverse, &chunks, &stats);
+    uint64_t total = 0;
+    for (auto &c : chunks) total += c.rows;
+    r->ns = (u32)vals.size();
+    if (!rc && ((rc = r->src.alloc(ctx, r->ns)) || (rc = r->beg.alloc(ctx, r->ns)) ||
+                (rc = r->len.alloc(ctx, r->ns)) || (rc = r->dst.alloc(ctx, total)))) {
+    }
+    if (!rc && r->ns) {
+      // languages whose automaton is empty produce no chunks: all rows empty
+      cudaMemsetAsync(r->len.p, 0, (uint64_t)r->ns * 4, st);
+      cudaMemsetAsync(r->beg.p, 0, (uint64_t)r->ns * 8, st);
+      cudaMemsetAsync(r->src.p, 0xff, (uint64_t)r->ns * 4, st);
+      if (chunks.empty()) {
+        // keep the source column sorted so lookups find every value
+        Buf<u32> tmp;
+        if (!(rc = tmp.alloc(ctx, r->ns)))
+          rc = cuda(cudaMemcpyAsync(r->src.p, vals.data(), (uint64_t)r->ns * 4, cudaMemcpyHostToDevice, st), "copy");
+        if (!rc) rc = cuda(cudaStreamSynchronize(st), "sync");
+      }
+    }
+    uint64_t base = 0;
+    uint32_t lane_base = 0;
+    for (auto &c : chunks) {
+      if (!rc) {
+        rows_index<<<grid1(c.n_lanes), 256, 0, st>>>(c.lanesrc, c.lane_off, c.n_lanes, lane_base, base, r->src.p,
+                                                     r->beg.p, r->len.p);
+        rc = cuda(cudaGetLastError(), "rows_index");
+        if (!rc && c.rows)
+          rc = cuda(cudaMemcpyAsync(r->dst.p + base, c.dst, c.rows * 4, cudaMemcpyDeviceToDevice, st), "copy");
+      }
+      base += c.rows;
+      lane_base += c.n_lanes;
+      free_row_chunk(ctx, c);
+    }
+    return rc;
+  }
+
+  // Binds variable order[k] from the candidates (cand_t, cand_v) of table T
+  // (cand_t == nullptr when T has no columns), filtering with `p`.
+  int bind(int k, Table &T, const u32 *cand_t, const u32 *cand_v, uint64_t nc, StepParams &p,
+           const uint8_t *which) {
+    if (nc == 0) return RPQ_OK;
+    Buf<u32> flag;
+    Buf<u64> posb, tmp;
+    int rc;
+    if ((rc = flag.alloc(ctx, nc)) || (rc = posb.alloc(ctx, nc)) || (rc = tmp.alloc(ctx, scan_tmp_words(nc))))
+      return rc;
+    filter_cands<<<grid1(nc), 256, 0, st>>>(p, nc, cand_t, cand_v, which, flag.p);
+    if ((rc = cuda(cudaGetLastError(), "filter_cands"))) return rc;
+    if ((rc = cuda(exclusive_scan_u32_to_u64(flag.p, posb.p, nc, small.p + 3, tmp.p, st), "scan"))) return rc;
+    u64 kept = 0;
+    if ((rc = cuda(cudaMemcpyAsync(&kept, small.p + 3, 8, cudaMemcpyDeviceToHost, st), "copy"))) return rc;
+    if ((rc = cuda(cudaStreamSynchronize(st), "sync"))) return rc;
+    stats.launches += 3;
+    if (kept == 0) return RPQ_OK;
+    Table N;
+    N.n = kept;
+    N.cols.resize(k + 1);
+    ColPtrs cp;
+    std::memset(&cp, 0, sizeof(cp));
+    for (int c = 0; c <= k; c++) {
+      if ((rc = N.cols[c].alloc(ctx, kept))) return rc;
+      cp.out[c] = N.cols[c].p;
+      if (c < k) cp.in[c] = T.cols[c].p;
+    }
+    compact_cands<<<grid1(nc), 256, 0, st>>>(nc, flag.p, posb.p, cand_t, cand_v, (u32)k, cp);
+    if ((rc = cuda(cudaGetLastError(), "compact_cands"))) return rc;
+    stats.launches += 1;
+    flag.release();
+    posb.release();
+    tmp.release();
+    return extend(k + 1, N);
+  }
+
+  // Fills p.c for the constraints of position k; self-loop rows come from
+  // the candidate values.
+  int prepare(int k, Table &T, const u32 *cand_v, uint64_t nc, std::vector<OwnedRows> &rows, StepParams &p,
+              bool self_only) {
+    std::memset(&p, 0, sizeof(p));
+    p.want_label = label_of((uint32_t)order[k]);
+    p.vlabel = dg.vlabel;
+    rows.resize(cons[k].size());
+    int rc;
+    for (size_t i = 0; i < cons[k].size(); i++) {
+      const C &c = cons[k][i];
+      if ((c.bound_pos < 0) != self_only) continue;
+      std::vector<uint32_t> vals;
+      if (c.bound_pos < 0)
+        rc = distinct(cand_v, nc, &vals);
+      else
+        rc = distinct(T.cols[c.bound_pos].p, T.n, &vals);
+      if (rc) return rc;
+      if ((rc = rows_for(c.atom, c.reverse, vals, &rows[i]))) return rc;
+    }
+    p.nc = (u32)cons[k].size();
+    for (size_t i = 0; i < cons[k].size(); i++) {
+      p.c[i].rows = rows[i].view();
+      p.c[i].col = cons[k][i].bound_pos < 0 ? nullptr : T.cols[cons[k][i].bound_pos].p;
+      if (cons[k][i].bound_pos >= 0) p.gen_mask |= 1u << i;
+    }
+    return RPQ_OK;
+  }
+
+  int extend(int k, Table &T) {
+    if (T.n == 0) return RPQ_OK;
+    if (k == (int)n_vars) return emit(T);
+    std::vector<OwnedRows> rows;
+    StepParams p;
+    int rc = prepare(k, T, nullptr, 0, rows, p, false);
+    if (rc) return rc;
+    Buf<u32> cnt;
+    Buf<uint8_t> which;
+    Buf<u64> off, tmp;
+    if ((rc = cnt.alloc(ctx, T.n)) || (rc = which.alloc(ctx, T.n)) || (rc = off.alloc(ctx, T.n + 1)) ||
+        (rc = tmp.alloc(ctx, scan_tmp_words(T.n + 1))))
+      return rc;
+    choose_gen<<<grid1(T.n), 256, 0, st>>>(p, T.n, cnt.p, which.p);
+    if ((rc = cuda(cudaGetLastError(), "choose_gen"))) return rc;
+    if ((rc = cuda(exclusive_scan_u32_to_u64(cnt.p, off.p, T.n, small.p + 4, tmp.p, st), "scan"))) return rc;
+    u64 total = 0;
+    if ((rc = cuda(cudaMemcpyAsync(&total, small.p + 4, 8, cudaMemcpyDeviceToHost, st), "copy"))) return rc;
+    if ((rc = cuda(cudaMemcpyAsync(off.p + T.n, small.p + 4, 8, cudaMemcpyDeviceToDevice, st), "copy"))) return rc;
+    if ((rc = cuda(cudaStreamSynchronize(st), "sync"))) return rc;
+    stats.launches += 2;
+    for (u64 c0 = 0; c0 < total; c0 += CAND_CAP) {
+      u64 nc = std::min<u64>(CAND_CAP, total - c0);
+      Buf<u32> ct, cv;
+      if ((rc = ct.alloc(ctx, nc)) || (rc = cv.alloc(ctx, nc))) return rc;
+      expand_cands<<<grid1(nc), 256, 0, st>>>(p, T.n, off.p, which.p, c0, nc, ct.p, cv.p);
+      if ((rc = cuda(cudaGetLastError(), "expand_cands"))) return rc;
+      stats.launches += 1;
+      // self-loop constraints need the candidate values
+      std::vector<OwnedRows> self_rows;
+      StepParams ps = p;
+      bool has_self = false;
+      for (auto &c : cons[k]) has_self |= c.bound_pos < 0;
+      if (has_self) {
+        StepParams tmpp;
+        if ((rc = prepare(k, T, cv.p, nc, self_rows, tmpp, true))) return rc;
+        for (size_t i = 0; i < cons[k].size(); i++)
+          if (cons[k][i].bound_pos < 0) ps.c[i].rows = self_rows[i].view();
+      }
+      if ((rc = bind(k, T, ct.p, cv.p, nc, ps, which.p))) return rc;
+    }
+    return RPQ_OK;
+  }
+
+  int emit(Table &T) {
+    ColPtrs cp;
+    std::memset(&cp, 0, sizeof(cp));
+    for (uint32_t v = 0; v < n_vars; v++) cp.in[v] = T.cols[pos[v]].p;
+    digest_rows<<<grid1(T.n), 256, 0, st>>>(cp, n_vars, T.n, small.p);
+    int rc = cuda(cudaGetLastError(), "digest_rows");
+    if (rc) return rc;
+    stats.launches += 1;
+    count += T.n;
+    if (materialize) batch_out.push_back(std::move(T));
+    return RPQ_OK;
+  }
+
+  // Sorts the complete tuples of a batch and appends them row-major.
+  int flush_batch() {
+    uint64_t n = 0;
+    for (auto &t : batch_out) n += t.n;
+    if (n == 0 || !materialize) {
+      batch_out.clear();
+      return RPQ_OK;
+    }
+    if (n >= (1ull << 32)) return ctx_error(ctx, RPQ_ERR_OUT_OF_BUDGET, "more than 2^32 tuples in one batch");
+    int rc;
+    // concatenate declaration-order columns
+    std::vector<Buf<u32>> cols(n_vars);
+    for (uint32_t v = 0; v < n_vars; v++) {
+      if ((rc = cols[v].alloc(ctx, n))) return rc;
+      uint64_t o = 0;
+      for (auto &t : batch_out) {
+        if ((rc = cuda(cudaMemcpyAsync(cols[v].p + o, t.cols[pos[v]].p, t.n * 4, cudaMemcpyDeviceToDevice, st),
+                       "copy")))
+          return rc;
+        o += t.n;
+      }
+    }
+    batch_out.clear();
+    // LSD over columns: last column first, each pass stable on the high word
+    Buf<u64> ka, kb;
+    Buf<u32> perm;
+    if ((rc = ka.alloc(ctx, n)) || (rc = kb.alloc(ctx, n)) || (rc = perm.alloc(ctx, n))) return rc;
+    for (int v = (int)n_vars - 1; v >= 0; v--) {
+      sort_keys_from_perm<<<grid1(n), 256, 0, st>>>(cols[v].p, v == (int)n_vars - 1 ? nullptr : perm.p, n, ka.p);
+      if ((rc = cuda(cudaGetLastError(), "sort_keys"))) return rc;
+      u64 *pa = ka.p, *pb = kb.p;
+      if ((rc = cuda(sort_keys_u64(&pa, &pb, n, 32, 64, st), "sort"))) return rc;
+      narrow_u64<<<grid1(n), 256, 0, st>>>(pa, n, perm.p);
+      if ((rc = cuda(cudaGetLastError(), "narrow"))) return rc;
+      stats.launches += 2;
+    }
+    u32 *rowsp = nullptr;
+    if ((rc = ctx_alloc(ctx, (void **)&rowsp, n * n_vars * 4))) return rc;
+    ColPtrs cp;
+    std::memset(&cp, 0, sizeof(cp));
+    for (uint32_t v = 0; v < n_vars; v++) cp.in[v] = cols[v].p;
+    gather_rows<<<grid1(n), 256, 0, st>>>(cp, n_vars, perm.p, n, rowsp);
+    if ((rc = cuda(cudaGetLastError(), "gather_rows"))) {
+      ctx_free(ctx, rowsp, n * n_vars * 4);
+      return rc;
+    }
+    stats.launches += 1;
+    out_chunks.push_back({rowsp, n});
+    return RPQ_OK;
+  }
+
+  int plan(const crpq_atom *at, uint32_t n_atoms) {
+    order.assign(1, 0);
+    pos.assign(n_vars, -1);
+    pos[0] = 0;
+    while (order.size() < n_vars) {
+      int best = -1, best_score = -1;
+      for (uint32_t v = 0; v < n_vars; v++) {
+        if (pos[v] >= 0) continue;
+        int score = 0;
+        for (uint32_t a = 0; a < n_atoms; a++) {
+          if (at[a].y == v && at[a].x != v && pos[at[a].x] >= 0) score += 3;  // forward
+          if (at[a].x == v && at[a].y != v && pos[at[a].y] >= 0) score += 2;  // reverse
+        }
+        if (score > best_score) {
+          best = (int)v;
+          best_score = score;
+        }
+      }
+      if (best_score <= 0) return ctx_error(ctx, RPQ_ERR_INVALID_ARG, "the atoms do not connect all variables");
+      pos[best] = (int)order.size();
+      order.push_back(best);
+    }
+    cons.assign(n_vars, {});
+    for (uint32_t a = 0; a < n_atoms; a++) {
+      int px = pos[at[a].x], py = pos[at[a].y];
+      if (at[a].x == at[a].y)
+        cons[px].push_back(C{a, -1, false});
+      else if (py > px)
+        cons[py].push_back(C{a, px, false});
+      else
+        cons[px].push_back(C{a, py, true});
+      if (cons[std::max(px, py)].size() > (size_t)MAXC) return ctx_error(ctx, RPQ_ERR_TOO_COMPLEX, "too many atoms");
+    }
+    for (int k = 1; k < (int)n_vars; k++) {
+      bool gen = false;
+      for (auto &c : cons[k]) gen |= c.bound_pos >= 0;
+      if (!gen) return ctx_error(ctx, RPQ_ERR_INVALID_ARG, "the atoms do not connect all variables");
+    }
+    return RPQ_OK;
+  }
+};
+
+}  // namespace
+
+int crpq_eval(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_vars, const int32_t *var_label, const crpq_atom *atoms,
+              uint32_t n_atoms, const uint32_t *restrict0, uint32_t n_restrict0, uint32_t flags, rpq_result **out) {
+  if (n_vars == 0 || n_vars > RPQ_MAX_VARS) return ctx_error(ctx, RPQ_ERR_INVALID_ARG, "n_vars out of range");
+  if (n_atoms == 0 || n_atoms > RPQ_MAX_ATOMS) return ctx_error(ctx, RPQ_ERR_INVALID_ARG, "n_atoms out of range");
+  if (flags & (RPQ_REVERSE | RPQ_FORCE_PUSH | RPQ_FORCE_PULL))
+    return ctx_error(ctx, RPQ_ERR_INVALID_ARG, "run_crpq takes RPQ_MATERIALIZE or RPQ_COUNT_ONLY only");
+  const DevGraph &dg = graph_dev(g);
+  std::vector<char> used(n_vars, 0);
+  for (uint32_t a = 0; a < n_atoms; a++) {
+    if (atoms[a].x >= n_vars || atoms[a].y >= n_vars || !atoms[a].q)
+      return ctx_error(ctx, RPQ_ERR_INVALID_ARG, "bad atom");
+    used[atoms[a].x] = used[atoms[a].y] = 1;
+  }
+  for (uint32_t v = 0; v < n_vars; v++) {
+    if (!used[v]) return ctx_error(ctx, RPQ_ERR_INVALID_ARG, "a variable occurs in no atom");
+    if (var_label && var_label[v] >= 0 && dg.vlabel_host.empty())
+      return ctx_error(ctx, RPQ_ERR_INVALID_ARG, "vertex label constraint on a graph without vertex labels");
+  }
+  Engine E(ctx, g);
+  E.n_vars = n_vars;
+  E.var_label = var_label;
+  E.atoms = atoms;
+  E.materialize = (flags & RPQ_MATERIALIZE) != 0;
+  int rc = E.plan(atoms, n_atoms);
+  if (rc) return rc;
+  for (uint32_t k = 0; k < n_vars; k++)
+    for (auto &c : E.cons[k])
+      if (c.reverse && !query_host(atoms[c.atom].q).has_rev)
+        return ctx_error(ctx, RPQ_ERR_TOO_COMPLEX, "an atom needs its reversed language, which is too large");
+  if ((rc = E.small.alloc(ctx, 8))) return rc;
+  cudaStream_t st = ctx_stream(ctx);
+  cudaMemsetAsync(E.small.p, 0, 64, st);
+
+  // values of variable 0
+  std::vector<uint32_t> first;
+  if (restrict0) {
+    first.assign(restrict0, restrict0 + n_restrict0);
+    for (uint32_t v : first)
+      if (v >= dg.n) return ctx_error(ctx, RPQ_ERR_INVALID_ARG, "restricted vertex out of range");
+    std::sort(first.begin(), first.end());
+    first.erase(std::unique(first.begin(), first.end()), first.end());
+  } else {
+    first.resize(dg.n);
+    std::iota(first.begin(), first.end(), 0u);
+  }
+  if (E.label_of(0) >= 0) {
+    std::vector<uint32_t> keep;
+    for (uint32_t v : first)
+      if (dg.vlabel_host[v] == (uint8_t)E.label_of(0)) keep.push_back(v);
+    first.swap(keep);
+  }
+
+  for (size_t b0 = 0; b0 < first.size() && rc == RPQ_OK; b0 += BATCH0) {
+    uint64_t nb = std::min<size_t>(BATCH0, first.size() - b0);
+    Buf<u32> vals;
+    if ((rc = vals.alloc(ctx, nb))) break;
+    if ((rc = E.cuda(cudaMemcpyAsync(vals.p, first.data() + b0, nb * 4, cudaMemcpyHostToDevice, st), "copy"))) break;
+    Table T0;  // no columns yet
+    std::vector<OwnedRows> rows;
+    StepParams p;
+    if ((rc = E.prepare(0, T0, vals.p, nb, rows, p, true))) break;
+    if ((rc = E.bind(0, T0, nullptr, vals.p, nb, p, nullptr))) break;
+    rc = E.flush_batch();
+  }
+  if (rc) {
+    for (auto &c : E.out_chunks) ctx_free(ctx, c.first, c.second * n_vars * 4);
+    return rc;
+  }
+  // digest and final rows
+  u64 dig[2] = {0, 0};
+  if ((rc = E.cuda(cudaMemcpyAsync(dig, E.small.p, 16, cudaMemcpyDeviceToHost, st), "copy")) ||
+      (rc = E.cuda(cudaStreamSynchronize(st), "sync"))) {
+    for (auto &c : E.out_chunks) ctx_free(ctx, c.first, c.second * n_vars * 4);
+    return rc;
+  }
+  u32 *tuples = nullptr;
+  if (E.materialize && E.count) {
+    if (E.out_chunks.size() == 1) {
+      tuples = E.out_chunks[0].first;
+    } else {
+      if ((rc = ctx_alloc(ctx, (void **)&tuples, E.count * n_vars * 4))) {
+        for (auto &c : E.out_chunks) ctx_free(ctx, c.first, c.second * n_vars * 4);
+        return rc;
+      }
+      uint64_t o = 0;
+      for (auto &c : E.out_chunks) {
+        cudaMemcpyAsync(tuples + o * n_vars, c.first, c.second * n_vars * 4, cudaMemcpyDeviceToDevice, st);
+        o += c.second;
+      }
+      for (auto &c : E.out_chunks) ctx_free(ctx, c.first, c.second * n_vars * 4);
+    }
+    cudaStreamSynchronize(st);
+  } else {
+    for (auto &c : E.out_chunks) ctx_free(ctx, c.first, c.second * n_vars * 4);
+  }
+  return make_tuple_result(ctx, n_vars, tuples, E.count, dig[0], dig[1], E.materialize, E.stats, out);
 }
 
 }  // namespace rpq

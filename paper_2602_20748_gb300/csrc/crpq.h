@@ -27,7 +27,7 @@ int ctx_error(rpq_ctx *ctx, int code, const std::string &msg);
 const DevGraph &graph_dev(const rpq_graph *g);
 const HostQuery &query_host(const rpq_query *q);
 int rpq_rows_for_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, std::vector<uint32_t> &srcs,
-                         std::vector<RowChunk> *chunks, rpq_stats *stats);
+                         bool reverse, std::vector<RowChunk> *chunks, rpq_stats *stats);
 void free_row_chunk(rpq_ctx *ctx, RowChunk &c);
 int make_tuple_result(rpq_ctx *ctx, uint32_t arity, u32 *tuples, uint64_t rows, uint64_t dsum, uint64_t dxor,
                       bool materialized, const rpq_stats &stats, rpq_result **out);

@@ -155,12 +155,13 @@ static unsigned grid_for(size_t n, int threads) {
     }                                                                  \
   } while (0)
 
-// LSD radix sort of m keys over their low `total_bits` bits; the sorted keys
-// end up in *a (a and b are swapped as needed).
-static cudaError_t radix_sort(u64 **a, u64 **b, size_t m, int total_bits, u32 *hist, u64 *offs, u64 *tmp,
-                              cudaStream_t st) {
+// LSD radix sort of m keys over bits [lo_bit, hi_bit) (stable, so bits
+// below lo_bit keep their order); the sorted keys end up in *a (a and b are
+// swapped as needed).
+static cudaError_t radix_sort_range(u64 **a, u64 **b, size_t m, int lo_bit, int hi_bit, u32 *hist, u64 *offs,
+                                    u64 *tmp, cudaStream_t st) {
   u32 nb = (u32)((m + RS_TILE - 1) / RS_TILE);
-  for (int shift = 0; shift < total_bits; shift += 8) {
+  for (int shift = lo_bit; shift < hi_bit; shift += 8) {
     rs_hist<<<nb, RS_THREADS, 0, st>>>(*a, m, shift, hist, nb);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -174,6 +175,49 @@ static cudaError_t radix_sort(u64 **a, u64 **b, size_t m, int total_bits, u32 *h
     *b = t;
   }
   return cudaSuccess;
+}
+
+static cudaError_t radix_sort(u64 **a, u64 **b, size_t m, int total_bits, u32 *hist, u64 *offs, u64 *tmp,
+                              cudaStream_t st) {
+  return radix_sort_range(a, b, m, 0, total_bits, hist, offs, tmp, st);
+}
+
+cudaError_t sort_keys_u64(u64 **a, u64 **b, size_t m, int lo_bit, int hi_bit, cudaStream_t st) {
+  if (m <= 1) return cudaSuccess;
+  u32 nb = (u32)((m + RS_TILE - 1) / RS_TILE);
+  size_t hist_n = (size_t)nb * 256;
+  u32 *hist = nullptr;
+  u64 *offs = nullptr, *tmp = nullptr;
+  cudaError_t e = cudaMallocAsync(&hist, hist_n * 4, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&offs, hist_n * 8, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&tmp, scan_tmp_words(hist_n) * 8, st);
+  if (e == cudaSuccess) e = radix_sort_range(a, b, m, lo_bit, hi_bit, hist, offs, tmp, st);
+  if (hist) cudaFreeAsync(hist, st);
+  if (offs) cudaFreeAsync(offs, st);
+  if (tmp) cudaFreeAsync(tmp, st);
+  return e;
+}
+
+cudaError_t unique_keys_u64(const u64 *sorted, size_t m, u64 *out, u64 *d_count, cudaStream_t st) {
+  if (m == 0) return cudaMemsetAsync(d_count, 0, 8, st);
+  u32 *flag = nullptr;
+  u64 *pos = nullptr, *tmp = nullptr;
+  cudaError_t e = cudaMallocAsync(&flag, m * 4, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&pos, m * 8, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&tmp, scan_tmp_words(m) * 8, st);
+  if (e == cudaSuccess) {
+    mark_unique<<<grid_for(m, 256), 256, 0, st>>>(sorted, m, flag);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = exclusive_scan_u32_to_u64(flag, pos, m, d_count, tmp, st);
+  if (e == cudaSuccess) {
+    compact_unique<<<grid_for(m, 256), 256, 0, st>>>(sorted, m, flag, pos, out);
+    e = cudaGetLastError();
+  }
+  if (flag) cudaFreeAsync(flag, st);
+  if (pos) cudaFreeAsync(pos, st);
+  if (tmp) cudaFreeAsync(tmp, st);
+  return e;
 }
 
 static int bits_for(uint64_t n) {

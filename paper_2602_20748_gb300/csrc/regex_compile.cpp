@@ -299,6 +299,98 @@ std::vector<int> hopcroft(int N, int A, const std::vector<int> &delta, const std
   return cls;
 }
 
+// Completes a partial DFA (n states, A symbols, raw[s * A + c] = target or -1,
+// state 0 the start) with a dead state, minimizes it, drops the dead class
+// and numbers the classes breadth-first from the start (symbols ascending),
+// which makes the table canonical.  Fills the kernel descriptor.
+int finish_dfa(int n, int A, const std::vector<int> &raw, const std::vector<char> &acc_raw, QueryDesc *out,
+               std::vector<int32_t> *next_out, std::string *msg) {
+  int N = n + 1, dead = n;
+  std::vector<int> delta((size_t)N * A, dead);
+  std::vector<char> accepting(N, 0);
+  for (int s = 0; s < n; s++) {
+    accepting[s] = acc_raw[s];
+    for (int c = 0; c < A; c++)
+      if (raw[(size_t)s * A + c] >= 0) delta[(size_t)s * A + c] = raw[(size_t)s * A + c];
+  }
+  std::vector<int> cls = hopcroft(N, A, delta, accepting);
+  int dead_cls = cls[dead];
+
+  std::map<int, int> num;
+  std::vector<int> rep;  // representative raw state of each numbered class
+  if (cls[0] != dead_cls) {
+    std::deque<int> bfs;
+    num[cls[0]] = 0;
+    rep.push_back(0);
+    bfs.push_back(0);
+    while (!bfs.empty()) {
+      int r = bfs.front();
+      bfs.pop_front();
+      for (int c = 0; c < A; c++) {
+        int t = delta[(size_t)r * A + c];
+        int tc = cls[t];
+        if (tc == dead_cls || num.count(tc)) continue;
+        num[tc] = (int)rep.size();
+        rep.push_back(t);
+        bfs.push_back(t);
+      }
+    }
+  }
+  int Q = (int)rep.size();
+  if (Q > RPQ_MAX_STATES) {
+    *msg = "minimal DFA has " + std::to_string(Q) + " states (limit " + std::to_string(RPQ_MAX_STATES) + ")";
+    return RPQ_ERR_TOO_COMPLEX;
+  }
+  std::vector<int32_t> next((size_t)Q * A, -1);
+  uint32_t fmask = 0;
+  for (int q = 0; q < Q; q++) {
+    if (accepting[rep[q]]) fmask |= 1u << q;
+    for (int c = 0; c < A; c++) {
+      int tc = cls[delta[(size_t)rep[q] * A + c]];
+      if (tc != dead_cls) next[(size_t)q * A + c] = num[tc];
+    }
+  }
+  QueryDesc d;
+  std::memset(&d, 0, sizeof(d));
+  d.n_states = (uint32_t)Q;
+  d.final_mask = fmask;
+  d.n_labels = (uint32_t)A;
+  int nt = 0;
+  for (int q = 0; q < Q; q++) {
+    d.out_begin[q] = (uint16_t)nt;
+    for (int c = 0; c < A; c++) {
+      int t = next[(size_t)q * A + c];
+      if (t < 0) continue;
+      if (nt >= RPQ_MAX_TRANSITIONS) {
+        *msg = "too many DFA transitions";
+        return RPQ_ERR_TOO_COMPLEX;
+      }
+      d.out_label[nt] = (uint8_t)c;
+      d.out_to[nt] = (uint8_t)t;
+      nt++;
+    }
+  }
+  for (int q = Q; q <= RPQ_MAX_STATES; q++) d.out_begin[q] = (uint16_t)nt;
+  d.n_trans = (uint32_t)nt;
+  int ng = 0;
+  for (int q2 = 0; q2 < Q; q2++) {
+    d.in_begin[q2] = (uint16_t)ng;
+    for (int c = 0; c < A; c++) {
+      uint32_t from = 0;
+      for (int q = 0; q < Q; q++)
+        if (next[(size_t)q * A + c] == q2) from |= 1u << q;
+      if (!from) continue;
+      d.in_label[ng] = (uint8_t)c;
+      d.in_from[ng] = from;
+      ng++;
+    }
+  }
+  for (int q = Q; q <= RPQ_MAX_STATES; q++) d.in_begin[q] = (uint16_t)ng;
+  *out = d;
+  *next_out = next;
+  return RPQ_OK;
+}
+
 }  // namespace
 
 int compile_regex(const char *regex, const char *const *names, uint32_t n_names, HostQuery *out, std::string *msg) {
@@ -367,91 +459,53 @@ int compile_regex(const char *regex, const char *const *names, uint32_t n_names,
       raw.push_back(t);
     }
   }
-  // Complete with a dead state and minimize.
-  int n = (int)sets.size();
-  int N = n + 1, dead = n;
-  std::vector<int> delta((size_t)N * A, dead);
-  std::vector<char> accepting(N, 0);
-  for (int s = 0; s < n; s++) {
-    accepting[s] = (sets[s] & accept_set) != 0;
-    for (int c = 0; c < A; c++)
-      if (raw[(size_t)s * A + c] >= 0) delta[(size_t)s * A + c] = raw[(size_t)s * A + c];
-  }
-  std::vector<int> cls = hopcroft(N, A, delta, accepting);
-  int dead_cls = cls[dead];
-
-  // Canonical numbering: breadth-first from the start class, symbols ascending.
-  std::map<int, int> num;
-  std::vector<int> rep;  // representative raw state of each numbered class
+  std::vector<char> acc_raw(sets.size(), 0);
+  for (size_t k = 0; k < sets.size(); k++) acc_raw[k] = (sets[k] & accept_set) != 0;
   HostQuery hq;
-  std::memset(&hq.d, 0, sizeof(hq.d));
-  if (cls[0] != dead_cls) {
-    std::deque<int> bfs;
-    num[cls[0]] = 0;
-    rep.push_back(0);
-    bfs.push_back(0);
-    while (!bfs.empty()) {
-      int r = bfs.front();
-      bfs.pop_front();
+  rc = finish_dfa((int)sets.size(), A, raw, acc_raw, &hq.d, &hq.next, msg);
+  if (rc) return rc;
+
+  // The reversed language (for evaluation from the target end over in-edges):
+  // subset construction over the reversed minimal DFA, starting from its
+  // accepting states; a set accepts when it holds the forward start state.
+  hq.has_rev = false;
+  std::memset(&hq.rev, 0, sizeof(hq.rev));
+  const int Q = (int)hq.d.n_states;
+  if (Q > 0) {
+    std::map<uint32_t, int> rindex;
+    std::vector<uint32_t> rsets{hq.d.final_mask};
+    rindex[hq.d.final_mask] = 0;
+    std::vector<int> rraw;
+    bool too_big = false;
+    for (size_t k = 0; k < rsets.size() && !too_big; k++) {
       for (int c = 0; c < A; c++) {
-        int t = delta[(size_t)r * A + c];
-        int tc = cls[t];
-        if (tc == dead_cls || num.count(tc)) continue;
-        num[tc] = (int)rep.size();
-        rep.push_back(t);
-        bfs.push_back(t);
+        uint32_t T = 0;
+        for (int q = 0; q < Q; q++) {
+          int t = hq.next[(size_t)q * A + c];
+          if (t >= 0 && (rsets[k] >> t & 1u)) T |= 1u << q;
+        }
+        int id = -1;
+        if (T) {
+          auto it = rindex.find(T);
+          if (it == rindex.end()) {
+            id = (int)rsets.size();
+            rindex[T] = id;
+            rsets.push_back(T);
+            if (rsets.size() > 4096) too_big = true;
+          } else {
+            id = it->second;
+          }
+        }
+        rraw.push_back(id);
       }
     }
-  }
-  int Q = (int)rep.size();
-  if (Q > RPQ_MAX_STATES) {
-    *msg = "minimal DFA has " + std::to_string(Q) + " states (limit " + std::to_string(RPQ_MAX_STATES) + ")";
-    return RPQ_ERR_TOO_COMPLEX;
-  }
-  hq.next.assign((size_t)Q * A, -1);
-  uint32_t fmask = 0;
-  for (int q = 0; q < Q; q++) {
-    if (accepting[rep[q]]) fmask |= 1u << q;
-    for (int c = 0; c < A; c++) {
-      int tc = cls[delta[(size_t)rep[q] * A + c]];
-      if (tc != dead_cls) hq.next[(size_t)q * A + c] = num[tc];
+    if (!too_big) {
+      std::vector<char> racc(rsets.size(), 0);
+      for (size_t k = 0; k < rsets.size(); k++) racc[k] = (rsets[k] & 1u) != 0;
+      std::string rmsg;
+      if (finish_dfa((int)rsets.size(), A, rraw, racc, &hq.rev, &hq.rev_next, &rmsg) == RPQ_OK) hq.has_rev = true;
     }
   }
-  QueryDesc &d = hq.d;
-  d.n_states = (uint32_t)Q;
-  d.final_mask = fmask;
-  d.n_labels = (uint32_t)A;
-  int nt = 0;
-  for (int q = 0; q < Q; q++) {
-    d.out_begin[q] = (uint16_t)nt;
-    for (int c = 0; c < A; c++) {
-      int t = hq.next[(size_t)q * A + c];
-      if (t < 0) continue;
-      if (nt >= RPQ_MAX_TRANSITIONS) {
-        *msg = "too many DFA transitions";
-        return RPQ_ERR_TOO_COMPLEX;
-      }
-      d.out_label[nt] = (uint8_t)c;
-      d.out_to[nt] = (uint8_t)t;
-      nt++;
-    }
-  }
-  for (int q = Q; q <= RPQ_MAX_STATES; q++) d.out_begin[q] = (uint16_t)nt;
-  d.n_trans = (uint32_t)nt;
-  int ng = 0;
-  for (int q2 = 0; q2 < Q; q2++) {
-    d.in_begin[q2] = (uint16_t)ng;
-    for (int c = 0; c < A; c++) {
-      uint32_t from = 0;
-      for (int q = 0; q < Q; q++)
-        if (hq.next[(size_t)q * A + c] == q2) from |= 1u << q;
-      if (!from) continue;
-      d.in_label[ng] = (uint8_t)c;
-      d.in_from[ng] = from;
-      ng++;
-    }
-  }
-  for (int q = Q; q <= RPQ_MAX_STATES; q++) d.in_begin[q] = (uint16_t)ng;
   *out = hq;
   return RPQ_OK;
 }

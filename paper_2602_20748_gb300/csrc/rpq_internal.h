@@ -35,6 +35,11 @@ struct QueryDesc {
 struct HostQuery {
   QueryDesc d;
   std::vector<int32_t> next;  // n_states * n_labels, -1 = none
+  // Minimal DFA of the reversed language, for evaluation from the target end
+  // over in-edges (absent when it would exceed RPQ_MAX_STATES).
+  bool has_rev = false;
+  QueryDesc rev;
+  std::vector<int32_t> rev_next;
 };
 
 // Parses and compiles; returns RPQ_OK or an error code with *msg set.
@@ -54,6 +59,7 @@ struct DevGraph {
   uint32_t *in_off = nullptr;
   uint32_t *in_col = nullptr;
   uint8_t *vlabel = nullptr;
+  std::vector<uint8_t> vlabel_host;   // vertex labels (host copy), empty if none
   std::vector<uint64_t> label_edges;  // edges per label (host copy)
 };
 
@@ -155,5 +161,13 @@ cudaError_t exclusive_scan_u64(const unsigned long long *in, unsigned long long 
 int build_graph(DevGraph *g, uint32_t n, uint32_t L, uint64_t m, const uint32_t *d_src, const uint32_t *d_dst,
                 const uint16_t *d_lab, cudaStream_t st, std::string *msg);
 int graph_key_bits(uint32_t n, uint32_t L);
+
+// Stable LSD radix sort of 64-bit keys over bits [lo_bit, hi_bit); the result
+// is in *a afterwards (the two buffers are swapped as needed).
+cudaError_t sort_keys_u64(unsigned long long **a, unsigned long long **b, size_t m, int lo_bit, int hi_bit,
+                          cudaStream_t st);
+// Distinct keys of a sorted array, in order; *d_count (device) gets their number.
+cudaError_t unique_keys_u64(const unsigned long long *sorted, size_t m, unsigned long long *out,
+                            unsigned long long *d_count, cudaStream_t st);
 
 }  // namespace rpq

@@ -39,6 +39,7 @@ RPQ_ERR_NO_DEVICE = -8
 
 RPQ_MATERIALIZE = 0x1
 RPQ_COUNT_ONLY = 0x2
+RPQ_REVERSE = 0x4
 RPQ_FORCE_PUSH = 0x100
 RPQ_FORCE_PULL = 0x200
 
