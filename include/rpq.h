@@ -170,6 +170,37 @@ int run_rpq(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, const uint32_t
 int run_rpq_range(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, uint32_t src_begin, uint32_t src_end,
                   uint32_t flags, rpq_result **out);
 
+/* ---- RPQ evaluation that allocates no device memory ---------------------- */
+
+/* The paper has no counterpart to this entry point.  It serves callers that
+ * cannot allocate device memory while they query: an application that gives
+ * the whole device memory to its own pool or buffer manager at start-up, a
+ * latency-critical loop that must not take the device-wide synchronization
+ * an allocation may imply, or code hosted inside another runtime that
+ * forbids allocating on its device.  It evaluates the same RPQ as run_rpq for
+ * 1 .. 64 start vertices, but every byte of scratch it uses lives in one
+ * 64 MiB array that the library reserves on each device when it is loaded
+ * and keeps until the process exits; the call itself calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *   sources    host array of n_sources start vertices (duplicates ignored).
+ *   out_pairs  caller-owned DEVICE buffer of 2 * max_rows uint32 values; row
+ *              k is written as (src, dst) at out_pairs[2k], out_pairs[2k+1],
+ *              rows sorted as for run_rpq.
+ *   *n_rows    (host) the number of result rows.
+ * The graph and query must fit the array: about 40 * states * vertices bytes
+ * (plus a little per 1,024 vertices); larger ones are rejected with
+ * OUT_OF_BUDGET and a message naming both sizes.  If the result has more than
+ * max_rows rows, nothing is written, *n_rows holds the row count and the call
+ * returns OUT_OF_BUDGET.  The first call on a device finds the array's device
+ * address (cudaGetSymbolAddress) and must therefore come before any stream
+ * capture on that device.  All calls share the array, and each keeps the
+ * previous call's contents until it clears what it needs: calls whose GPU
+ * work overlaps (from several threads or streams on one device) race and
+ * must be serialized by the caller.  The call waits for its work to finish.
+ * Errors: INVALID_ARG, NO_DEVICE, OUT_OF_BUDGET, CUDA, TIMEOUT. */
+int run_rpq_static(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, const uint32_t *sources,
+                   uint32_t n_sources, uint32_t *out_pairs, uint64_t max_rows, uint64_t *n_rows);
+
 /* ---- CRPQ evaluation (Definition 2; Section 6.3 joins atom results) ------- */
 
 typedef struct {

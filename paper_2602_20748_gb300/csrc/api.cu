@@ -775,6 +775,10 @@ int ctx_alloc(rpq_ctx *ctx, void **p, uint64_t bytes) { return dev_alloc(ctx, p,
 void ctx_free(rpq_ctx *ctx, void *p, uint64_t bytes) { dev_free(ctx, p, bytes); }
 cudaStream_t ctx_stream(rpq_ctx *ctx) { return ctx->stream; }
 int ctx_error(rpq_ctx *ctx, int code, const std::string &msg) { return set_err(ctx, code, msg); }
+int ctx_device(rpq_ctx *ctx) { return ctx->device; }
+int ctx_bfs_blocks(rpq_ctx *ctx, int nw) { return ctx->sms * ctx->bpsm[nw == 1 ? 0 : 1]; }
+float ctx_alpha(rpq_ctx *ctx) { return ctx->alpha; }
+uint64_t ctx_time_limit_ns(rpq_ctx *ctx) { return ctx->time_limit_ns; }
 const DevGraph &graph_dev(const rpq_graph *g) { return g->g; }
 const HostQuery &query_host(const rpq_query *q) { return q->hq; }
 

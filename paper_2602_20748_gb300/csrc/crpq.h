@@ -24,6 +24,10 @@ int ctx_alloc(rpq_ctx *ctx, void **p, uint64_t bytes);
 void ctx_free(rpq_ctx *ctx, void *p, uint64_t bytes);
 cudaStream_t ctx_stream(rpq_ctx *ctx);
 int ctx_error(rpq_ctx *ctx, int code, const std::string &msg);
+int ctx_device(rpq_ctx *ctx);
+int ctx_bfs_blocks(rpq_ctx *ctx, int nw);
+float ctx_alpha(rpq_ctx *ctx);
+uint64_t ctx_time_limit_ns(rpq_ctx *ctx);
 const DevGraph &graph_dev(const rpq_graph *g);
 const HostQuery &query_host(const rpq_query *q);
 int rpq_rows_for_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, std::vector<uint32_t> &srcs,

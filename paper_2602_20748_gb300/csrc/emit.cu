@@ -88,6 +88,53 @@ cudaError_t launch_emit(int nw, bool write, const EmitParams &p, cudaStream_t st
   return cudaGetLastError();
 }
 
+// Second pass that writes interleaved (src, dst) rows straight into a
+// caller's buffer (used by the entry point that allocates nothing): same walk
+// as emit_kernel's write pass, row k at out[2k], out[2k + 1].
+template <int NW>
+__global__ void emit_pairs_kernel(const EmitParams p, u32 *__restrict__ out) {
+  const u32 seg = blockIdx.x, g = blockIdx.y;
+  const u32 col = threadIdx.x >> 5, lane = lane_id();
+  const u32 K = 64 * NW;
+  const u64 glane = (u64)g * K + col * 32 + lane;
+  const u32 src = p.lanesrc[glane];
+  const u32 valid_cols = __ballot_sync(FULL_MASK, src != NO_SOURCE);
+  const u32 *vis32 = reinterpret_cast<const u32 *>(p.vis);
+  u64 pos = p.off[glane * p.segs + seg];
+  const u32 w_begin = seg * EMIT_SEG;
+  for (u32 t = 0; t < EMIT_TILES; t++) {
+    const u32 w0 = w_begin + t * 32;
+    if (w0 >= p.n) break;
+    const u32 w = w0 + lane;
+    u32 x = 0;
+    if (w < p.n) {
+      for (u32 fm = p.final_mask; fm; fm &= fm - 1) {
+        u32 q = __ffs(fm) - 1;
+        u64 word = (((u64)g * p.Q + q) * p.n + w) * NW;
+        x |= __ldcg(vis32 + word * 2 + col);
+      }
+    }
+    x &= valid_cols;
+    u32 mine = 0;
+#pragma unroll
+    for (int j = 0; j < 32; j++) {
+      u32 b = __ballot_sync(FULL_MASK, (x >> j) & 1u);
+      if (lane == (u32)j) mine = b;
+    }
+    for (u32 b = mine; b; b &= b - 1) {
+      out[2 * pos] = src;
+      out[2 * pos + 1] = w0 + (__ffs(b) - 1);
+      pos++;
+    }
+  }
+}
+
+cudaError_t launch_emit_pairs(const EmitParams &p, uint32_t *out, cudaStream_t st) {
+  dim3 grid(p.segs, p.G);
+  emit_pairs_kernel<1><<<grid, 64, 0, st>>>(p, out);
+  return cudaGetLastError();
+}
+
 // lane_off[i] = off[i * segs] for every lane; lane_off[n_lanes] = total.
 __global__ void gather_lane_off(const u64 *__restrict__ off, u32 segs, u32 n_lanes, const u64 *__restrict__ total,
                                 u64 *__restrict__ lane_off) {

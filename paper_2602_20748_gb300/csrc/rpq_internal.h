@@ -142,6 +142,9 @@ constexpr int EMIT_TILES = 32;  // 32-vertex tiles per segment
 constexpr int EMIT_SEG = 32 * EMIT_TILES;
 cudaError_t launch_emit(int nw, bool write, const EmitParams &p, cudaStream_t st);
 
+// Write pass into interleaved (src, dst) rows of a caller's buffer (NW = 1).
+cudaError_t launch_emit_pairs(const EmitParams &p, uint32_t *out, cudaStream_t st);
+
 cudaError_t launch_gather_lane_off(const unsigned long long *off, uint32_t segs, uint32_t n_lanes,
                                    const unsigned long long *total, unsigned long long *lane_off, cudaStream_t st);
 

@@ -49,7 +49,7 @@ RPQ_MAX_LABELS = 64
 EXPORTED = [
     "rpq_create", "rpq_destroy", "rpq_last_error", "rpq_set_stream", "load_graph", "graph_info", "free_graph",
     "compile_rpq", "query_info", "free_query", "run_rpq", "run_rpq_range", "run_crpq", "result_info",
-    "result_stats", "fetch_pairs", "free_result",
+    "result_stats", "fetch_pairs", "free_result", "run_rpq_static",
 ]
 
 c_void_p = ctypes.c_void_p
@@ -96,6 +96,7 @@ _lib.result_stats.argtypes = [c_void_p, P(rpq_stats)]
 _lib.fetch_pairs.argtypes = [c_void_p, c_u64, c_u64, c_void_p, P(c_u64)]
 _lib.free_result.argtypes = [c_void_p]
 _lib.free_result.restype = None
+_lib.run_rpq_static.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_u32, c_void_p, c_u64, P(c_u64)]
 
 
 class RPQError(RuntimeError):
@@ -267,3 +268,13 @@ def fetch_pairs(r: Result, offset: int = 0, max_rows: int | None = None, out: np
     got = c_u64()
     r.ctx.check(_lib.fetch_pairs(r.h, offset, k, _ptr(out), ctypes.byref(got)))
     return out[: got.value * arity].reshape(got.value, arity)
+
+
+def run_rpq_static(ctx: Context, g: Graph, q: Query, sources, out_pairs_ptr: int, max_rows: int) -> int:
+    """run_rpq_static: the RPQ for 1..64 start vertices with no device
+    allocation.  ``out_pairs_ptr`` is the address of a caller-owned device
+    buffer of 2 * max_rows uint32 values.  Returns the number of rows."""
+    s = np.ascontiguousarray(sources, dtype=np.uint32)
+    n = c_u64()
+    ctx.check(_lib.run_rpq_static(ctx.h, g.h, q.h, _ptr(s), len(s), out_pairs_ptr, max_rows, ctypes.byref(n)))
+    return n.value
