@@ -53,14 +53,16 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--scale", type=int, default=SCALE,
+                    help="R-MAT scale (vertices 2^scale, 16 * 2^scale edges); smaller cases are for profiling")
     return ap.parse_args()
 
 
-def make_graph():
+def make_graph(scale: int = SCALE):
     from paper_2602_20748_gb300 import synth
 
-    src, dst, lab = synth.rmat_graph(SCALE, N_EDGES, N_LABELS, ZIPF_S, seed=synth.BASE_SEED + 1)
-    return 1 << SCALE, src, dst, lab
+    src, dst, lab = synth.rmat_graph(scale, 16 << scale, N_LABELS, ZIPF_S, seed=synth.BASE_SEED + 1)
+    return 1 << scale, src, dst, lab
 
 
 def peaks():
@@ -200,7 +202,7 @@ def ours(args, rank: int, world: int, local_rank: int):
         dist.init_process_group("nccl")
     from paper_2602_20748_gb300 import rpq
 
-    n, src, dst, lab = make_graph()
+    n, src, dst, lab = make_graph(args.scale)
     ctx = rpq.Context(device=local_rank)
     t0 = time.perf_counter()
     g = rpq.load_graph(ctx, n, N_LABELS, src, dst, lab)
@@ -319,7 +321,8 @@ def ours(args, rank: int, world: int, local_rank: int):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "queries": QUERIES, "vertices": n, "generated_edges": N_EDGES,
+            "config": {"workload": WORKLOAD if args.scale == SCALE else f"rmat{args.scale}-allpairs",
+                       "queries": QUERIES, "vertices": n, "generated_edges": 16 * n,
                        "distinct_edges": m_unique, "labels": N_LABELS, "zipf_s": ZIPF_S,
                        "batch_sources_per_step": B, "parallelism": f"sources/{world}",
                        "l2": "inputs larger than L2 (graph CSR ~200 MB, traversal state ~4.6 GB per launch)",

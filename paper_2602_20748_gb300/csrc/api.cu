@@ -273,6 +273,9 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
     p.out_col = reverse ? g.in_col : g.out_col;
     p.in_off = reverse ? g.out_off : g.in_off;
     p.in_col = reverse ? g.out_col : g.in_col;
+    p.heavy_bits = reverse ? g.heavy_out_bits : g.heavy_in_bits;
+    p.heavy_list = reverse ? g.heavy_out_list : g.heavy_in_list;
+    p.n_heavy = reverse ? g.n_heavy_out : g.n_heavy_in;
     p.n = n;
     p.L = g.L;
     p.G = Gb;
@@ -571,7 +574,8 @@ int load_graph(rpq_ctx *ctx, uint32_t n_vertices, uint32_t n_labels, uint64_t n_
   {
     // the graph arrays were allocated inside build_graph outside the budget
     // accounting; account for them now
-    uint64_t b = rows * 8 + gr->g.m * 8;
+    uint64_t b = rows * 8 + gr->g.m * 8 + 2 * (((uint64_t)n_vertices + 31) / 32 * 4) +
+                 ((uint64_t)gr->g.n_heavy_in + gr->g.n_heavy_out) * 4;
     ctx->used += b;
     gr->bytes = b;
   }
@@ -596,6 +600,10 @@ fail:
   if (gr->g.in_off) cudaFreeAsync(gr->g.in_off, st);
   if (gr->g.out_col) cudaFreeAsync(gr->g.out_col, st);
   if (gr->g.in_col) cudaFreeAsync(gr->g.in_col, st);
+  if (gr->g.heavy_in_bits) cudaFreeAsync(gr->g.heavy_in_bits, st);
+  if (gr->g.heavy_in_list) cudaFreeAsync(gr->g.heavy_in_list, st);
+  if (gr->g.heavy_out_bits) cudaFreeAsync(gr->g.heavy_out_bits, st);
+  if (gr->g.heavy_out_list) cudaFreeAsync(gr->g.heavy_out_list, st);
   if (gr->g.vlabel) dfree(ctx, gr->g.vlabel, n_vertices);
   delete gr;
   release_handle(ctx);
@@ -619,6 +627,10 @@ void free_graph(rpq_graph *g) {
   cudaFreeAsync(g->g.in_off, st);
   cudaFreeAsync(g->g.out_col, st);
   cudaFreeAsync(g->g.in_col, st);
+  cudaFreeAsync(g->g.heavy_in_bits, st);
+  cudaFreeAsync(g->g.heavy_in_list, st);
+  cudaFreeAsync(g->g.heavy_out_bits, st);
+  cudaFreeAsync(g->g.heavy_out_list, st);
   ctx->used -= std::min(ctx->used, g->bytes);
   if (g->g.vlabel) dfree(ctx, g->g.vlabel, g->g.n);
   delete g;

@@ -128,6 +128,30 @@ __global__ void label_bounds(const uint32_t *__restrict__ off, uint32_t n, uint3
   }
 }
 
+// flag[v] = total degree of v over all labels >= thresh; bits[v / 32] holds
+// the same flags packed (n rounded up to a whole warp).
+__global__ void mark_heavy(const uint32_t *__restrict__ off, uint32_t n, uint32_t L, uint32_t thresh,
+                           u32 *__restrict__ flag, u32 *__restrict__ bits) {
+  const u64 n_pad = ((u64)n + 31) & ~31ull;
+  for (u64 v = (u64)blockIdx.x * blockDim.x + threadIdx.x; v < n_pad; v += (u64)gridDim.x * blockDim.x) {
+    bool heavy = false;
+    if (v < n) {
+      u64 d = 0;
+      for (uint32_t l = 0; l < L; l++) d += off[(u64)l * (n + 1) + v + 1] - off[(u64)l * (n + 1) + v];
+      heavy = d >= thresh;
+      flag[v] = heavy ? 1u : 0u;
+    }
+    u32 b = __ballot_sync(FULL_MASK, heavy);
+    if ((threadIdx.x & 31) == 0) bits[v / 32] = b;
+  }
+}
+
+__global__ void list_heavy(const u32 *__restrict__ flag, const u64 *__restrict__ pos, uint32_t n,
+                           uint32_t *__restrict__ list) {
+  for (u64 v = (u64)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (u64)gridDim.x * blockDim.x)
+    if (flag[v]) list[pos[v]] = (uint32_t)v;
+}
+
 // (label | src | dst) -> (label | dst | src)
 __global__ void swap_ends(const u64 *__restrict__ k, size_t m, int bits, u64 *__restrict__ out) {
   u64 mask = (1ull << bits) - 1;
@@ -226,6 +250,39 @@ static int bits_for(uint64_t n) {
   return b;
 }
 
+// Flags, packed bits and sorted list of the vertices whose total degree in
+// the CSR `off` reaches HEAVY_DEGREE.
+static cudaError_t build_heavy(const uint32_t *off, uint32_t n, uint32_t L, uint32_t **bits, uint32_t **list,
+                               uint32_t *count, cudaStream_t st) {
+  u32 *flag = nullptr;
+  u64 *pos = nullptr, *tmp = nullptr, *dcount = nullptr;
+  u64 hcount = 0;
+  const u64 words = ((u64)n + 31) / 32;
+  cudaError_t e = cudaMallocAsync(&flag, (u64)n * 4, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&pos, (u64)n * 8, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&tmp, scan_tmp_words(n) * 8, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&dcount, 8, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(bits, words * 4, st);
+  if (e == cudaSuccess) {
+    mark_heavy<<<grid_for(words * 32, 256), 256, 0, st>>>(off, n, L, HEAVY_DEGREE, flag, *bits);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = exclusive_scan_u32_to_u64(flag, pos, n, dcount, tmp, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hcount, dcount, 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMallocAsync(list, (hcount ? hcount : 1) * 4, st);
+  if (e == cudaSuccess) {
+    list_heavy<<<grid_for(n, 256), 256, 0, st>>>(flag, pos, n, *list);
+    e = cudaGetLastError();
+  }
+  *count = (uint32_t)hcount;
+  if (flag) cudaFreeAsync(flag, st);
+  if (pos) cudaFreeAsync(pos, st);
+  if (tmp) cudaFreeAsync(tmp, st);
+  if (dcount) cudaFreeAsync(dcount, st);
+  return e;
+}
+
 int graph_key_bits(uint32_t n, uint32_t L) { return ((L > 1) ? bits_for(L) : 0) + 2 * bits_for(n); }
 
 int build_graph(DevGraph *g, uint32_t n, uint32_t L, uint64_t m, const uint32_t *d_src, const uint32_t *d_dst,
@@ -316,6 +373,8 @@ int build_graph(DevGraph *g, uint32_t n, uint32_t L, uint64_t m, const uint32_t 
     g->label_edges.assign(L, 0);
     for (uint32_t l = 0; l < L; l++) g->label_edges[l] = (uint64_t)ends[2 * l + 1] - ends[2 * l];
   }
+  RPQ_TRY(build_heavy(g->in_off, n, L, &g->heavy_in_bits, &g->heavy_in_list, &g->n_heavy_in, st));
+  RPQ_TRY(build_heavy(g->out_off, n, L, &g->heavy_out_bits, &g->heavy_out_list, &g->n_heavy_out, st));
 done:
   if (ka) cudaFreeAsync(ka, st);
   if (kb) cudaFreeAsync(kb, st);

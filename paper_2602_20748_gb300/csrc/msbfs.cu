@@ -296,12 +296,22 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 nxt, u64 *stat) {
     bool valid = item < total;
     u32 g = valid ? (u32)(item / n) : 0;
     u32 w = valid ? (u32)(item - (u64)g * n) : 0;
+    // high in-degree vertices are left to the warp-per-vertex loop below
+    if (valid && p.heavy_bits && (__ldg(p.heavy_bits + (w >> 5)) >> (w & 31) & 1u)) valid = false;
     for (u32 q2 = 0; q2 < Q; q2++) {
       u32 gb = p.q.in_begin[q2], ge = p.q.in_begin[q2 + 1];
       if (gb == ge) continue;
       bool take = false;
       u64 gq2 = (u64)g * Q + q2;
-      if (valid) {
+      bool has_in = false;  // skip vertices with no in-edge on these labels
+      if (valid)
+        for (u32 j = gb; j < ge && !has_in; j++) {
+          u32 l = p.q.in_label[j];
+          if (l >= p.L) continue;
+          const u32 *off = p.in_off + (u64)l * n1 + w;
+          has_in = __ldg(off) != __ldg(off + 1);
+        }
+      if (has_in) {
         u64 wi = (gq2 * n + w) * NW;
         Word<NW> vis = load_cg<NW>(p.vis + wi);
         if (!all_bits(vis)) {
@@ -345,6 +355,62 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 nxt, u64 *stat) {
             store_w<NW>(FB + wi, nw);
             take = true;
           }
+        }
+      }
+      warp_append(take, (gq2 << 32) | w, &p.ctl->n_list[nxt], nlist);
+    }
+  }
+  // High in-degree vertices: a warp per (group, vertex); lanes stride over
+  // the in-edges and the partial words are OR-reduced across the warp.
+  const u64 n_hv = (u64)p.G * p.n_heavy;
+  const u32 lane = lane_id();
+  for (u64 it = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n_hv; it += stride >> 5) {
+    const u32 g = (u32)(it / p.n_heavy);
+    const u32 w = __ldg(p.heavy_list + (it - (u64)g * p.n_heavy));
+    for (u32 q2 = 0; q2 < Q; q2++) {
+      u32 gb = p.q.in_begin[q2], ge = p.q.in_begin[q2 + 1];
+      if (gb == ge) continue;
+      const u64 gq2 = (u64)g * Q + q2;
+      const u64 wi = (gq2 * n + w) * NW;
+      Word<NW> vis = load_cg<NW>(p.vis + wi);
+      if (all_bits(vis)) continue;
+      Word<NW> acc;
+#pragma unroll
+      for (int t = 0; t < NW; t++) acc.w[t] = 0;
+      for (u32 j = gb; j < ge; j++) {
+        u32 l = p.q.in_label[j];
+        if (l >= p.L) continue;
+        u32 from = p.q.in_from[j];
+        const u32 *off = p.in_off + (u64)l * n1 + w;
+        u32 beg = __ldg(off), end = __ldg(off + 1);
+        for (u32 i = beg + lane; i < end; i += 32) {
+          u32 v = __ldg(p.in_col + i);
+          edges++;
+          for (u32 fb = from; fb; fb &= fb - 1) {
+            u32 q = __ffs(fb) - 1;
+            Word<NW> f = load_cg<NW>(F + (((u64)g * Q + q) * n + v) * NW);
+#pragma unroll
+            for (int t = 0; t < NW; t++) acc.w[t] |= f.w[t];
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < NW; t++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc.w[t] |= __shfl_xor_sync(FULL_MASK, acc.w[t], o);
+      Word<NW> nw;
+#pragma unroll
+      for (int t = 0; t < NW; t++) nw.w[t] = acc.w[t] & ~vis.w[t];
+      bool take = false;
+      if (lane == 0) {
+        words++;
+        if (any_bits(nw)) {
+          Word<NW> nv;
+#pragma unroll
+          for (int t = 0; t < NW; t++) nv.w[t] = vis.w[t] | nw.w[t];
+          store_w<NW>(p.vis + wi, nv);
+          store_w<NW>(FB + wi, nw);
+          take = true;
         }
       }
       warp_append(take, (gq2 << 32) | w, &p.ctl->n_list[nxt], nlist);

@@ -50,6 +50,8 @@ int compile_regex(const char *regex, const char *const *names, uint32_t n_names,
 // out-edges (sorted by label, src, dst) and in-edges (label, dst, src).
 // off[l * (n + 1) + v] is the first edge of row v of label l.
 // ---------------------------------------------------------------------------
+constexpr uint32_t HEAVY_DEGREE = 128;
+
 struct DevGraph {
   uint32_t n = 0;
   uint32_t L = 0;
@@ -59,6 +61,12 @@ struct DevGraph {
   uint32_t *in_off = nullptr;
   uint32_t *in_col = nullptr;
   uint8_t *vlabel = nullptr;
+  // High-degree vertices (total degree over all labels >= HEAVY_DEGREE), per
+  // direction: a bit per vertex and the sorted list.  Bottom-up levels give
+  // each of them a whole warp instead of one thread.
+  uint32_t *heavy_in_bits = nullptr, *heavy_in_list = nullptr;
+  uint32_t *heavy_out_bits = nullptr, *heavy_out_list = nullptr;
+  uint32_t n_heavy_in = 0, n_heavy_out = 0;
   std::vector<uint8_t> vlabel_host;   // vertex labels (host copy), empty if none
   std::vector<uint64_t> label_edges;  // edges per label (host copy)
 };
@@ -97,6 +105,9 @@ struct BfsParams {
   const uint32_t *out_col;
   const uint32_t *in_off;
   const uint32_t *in_col;
+  const uint32_t *heavy_bits;  // high in-degree vertices (for in_off / in_col)
+  const uint32_t *heavy_list;
+  uint32_t n_heavy;
   uint32_t n;
   uint32_t L;             // edge labels of the graph
   // lane groups

@@ -172,6 +172,28 @@ def test_edge_cases(ctx):
         check(ctx, g1, og1, regex)
 
 
+def test_heavy_vertices(ctx):
+    """Hubs far above the high-degree threshold in both directions: vertex 0
+    has in-degree 3,000 (label a), vertex 1 out-degree 2,500 (label b)."""
+    n = 4000
+    rs, rd, rl = synth.random_graph(n, 6000, 3, seed=77)
+    src = np.concatenate([np.arange(1, 3001), np.ones(2500), rs]).astype(np.uint32)
+    dst = np.concatenate([np.zeros(3000), np.arange(1500, 4000), rd]).astype(np.uint32)
+    lab = np.concatenate([np.zeros(3000), np.ones(2500), rl]).astype(np.uint16)
+    g = rpq.load_graph(ctx, n, 3, src, dst, lab)
+    og = oracle.Graph(n, 3, src, dst, lab)
+    sample = np.arange(0, n, 7, dtype=np.uint32)
+    for regex in ("a.b", "(a|b)*", "a*.b.c*", "(a.b)+"):
+        want = oracle.rpq(og, regex, sources=sample)
+        for mode in MODES.values():
+            check(ctx, g, og, regex, sources=sample, mode=mode, want=want)
+        wrev = rpq.fetch_pairs(rpq.run_rpq(ctx, g, rpq.compile_rpq(ctx, regex), np.array([0, 1, 2000], np.uint32),
+                                           flags=rpq.RPQ_MATERIALIZE | rpq.RPQ_REVERSE | rpq.RPQ_FORCE_PULL))
+        full = oracle.rpq(og, regex).rows
+        want_rev = sorted((int(d), int(s)) for s, d in full.tolist() if d in (0, 1, 2000))
+        assert [tuple(r) for r in wrev.tolist()] == want_rev
+
+
 def test_invalid_arguments(ctx):
     with pytest.raises(rpq.RPQError) as e:
         rpq.load_graph(ctx, 4, 1, [0], [9], [0])
