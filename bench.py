@@ -122,15 +122,15 @@ class ClockSampler:
 
 
 def algorithmic_bytes(st: dict) -> float:
-    """Bytes the traversal must move for the work it did (per launch sums):
-    per top-down edge relaxation a 4-byte column id and the target's visited
-    word (8 * NW bytes); per adjacency row opened the two 4-byte offsets; per
-    lane-group product vertex discovered its 8-byte list entry; per bottom-up
-    in-edge a column id and one gathered frontier word; per bottom-up
-    (vertex, state) word examined its visited word."""
-    nw = st["lane_words"]
-    return ((4 + 8 * nw) * st["group_edges"] + 8 * st["group_rows"] + 8 * st["group_vertices"]
-            + (4 + 8 * nw) * st["pull_edges"] + 8 * nw * st["pull_vertices"])
+    """Bytes the traversal kernel must move for the work it did, counted by the
+    kernel itself (rpq_stats.alg_bytes): per top-down relaxation a 4-byte
+    column id and the target's visited word (8 * NW bytes); per adjacency row
+    its two offsets; per frontier entry the 8-byte entry and its frontier word;
+    per bottom-up (state, vertex) examined the visited words of all G groups;
+    per bottom-up in-edge a column id and the G frontier words of each active
+    source state; per new entry its entry, new frontier word and visited word
+    read and written; per old entry its entry and cleared frontier word."""
+    return float(st["alg_bytes"])
 
 
 def cpu_oracle_sample(n, src, dst, lab, seconds: float, batch0: int):
@@ -228,13 +228,14 @@ def ours(args, rank: int, world: int, local_rank: int):
             acc["bfs_launches"] += st["bfs_launches"]
             acc["launches"] += st["launches"]
             acc["alg_bytes"] += algorithmic_bytes(st)
+            acc["emit_ms"] += st["emit_ms"]
             for k in ("push_levels", "pull_levels", "levels"):
                 acc[k] += st[k]
             r.free()
 
     def new_acc():
-        return dict(W=0, pairs=0, bfs_ms=0.0, bfs_launches=0, launches=0, alg_bytes=0.0, push_levels=0,
-                    pull_levels=0, levels=0)
+        return dict(W=0, pairs=0, bfs_ms=0.0, emit_ms=0.0, bfs_launches=0, launches=0, alg_bytes=0.0,
+                    push_levels=0, pull_levels=0, levels=0)
 
     for i in range(args.warmup):
         run_step(i, new_acc())
@@ -333,7 +334,8 @@ def ours(args, rank: int, world: int, local_rank: int):
             "levels": {"push": acc["push_levels"], "pull": acc["pull_levels"]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": "msbfs_kernel<4>",
-                         "peak_kind": peak_kind, "bfs_ms": acc["bfs_ms"], "bfs_launches": acc["bfs_launches"]},
+                         "peak_kind": peak_kind, "bfs_ms": acc["bfs_ms"], "bfs_launches": acc["bfs_launches"],
+                         "emit_ms": acc["emit_ms"]},
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clocks,

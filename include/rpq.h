@@ -170,6 +170,29 @@ int run_rpq(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, const uint32_t
 int run_rpq_range(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, uint32_t src_begin, uint32_t src_end,
                   uint32_t flags, rpq_result **out);
 
+/* ---- batched single-source RPQs (many expressions, one launch) ----------- */
+
+/* Evaluates n_queries single-source RPQs together: query i is the compiled
+ * expression queries[i] (different queries may use different expressions)
+ * from the start vertex sources[i] (host arrays).  All queries advance level
+ * by level in one persistent traversal launch (several launches when they
+ * do not fit the device together).  Rows are (i, y) for every y with
+ * sources[i] -rho_i-> y, sorted by i then y; arity 2.  The digest of
+ * result_info is taken over these (i, y) rows.  flags: RPQ_MATERIALIZE or
+ * RPQ_COUNT_ONLY.  Block size and queries per launch come from the last
+ * rpq_autotune_batch on the context (defaults otherwise).
+ * Errors: INVALID_ARG, OUT_OF_BUDGET, CUDA, TIMEOUT. */
+int run_rpq_batch(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_queries, const rpq_query *const *queries,
+                  const uint32_t *sources, uint32_t flags, rpq_result **out);
+
+/* Times run_rpq_batch (count only) on the given batch for each candidate
+ * block size (128, 256, 512 threads) and queries-per-launch (1024, 2048,
+ * 4096, capped by n_queries), keeps the fastest on the context for later
+ * run_rpq_batch calls and reports it (out pointers may be NULL).
+ * Errors: as run_rpq_batch. */
+int rpq_autotune_batch(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_queries, const rpq_query *const *queries,
+                       const uint32_t *sources, uint32_t *threads_out, uint32_t *queries_per_launch_out);
+
 /* ---- RPQ evaluation that allocates no device memory ---------------------- */
 
 /* The paper has no counterpart to this entry point.  It serves callers that
@@ -257,6 +280,9 @@ typedef struct {
   double emit_ms;            /* device time of the emission kernels           */
   uint64_t bfs_launches;     /* traversal kernel launches                     */
   uint64_t launches;         /* all kernel launches of the evaluation         */
+  uint64_t alg_bytes;        /* bytes the traversal kernels must move for the
+                                work they did (column ids, offsets, visited and
+                                frontier words, list entries)                 */
 } rpq_stats;
 
 int result_stats(const rpq_result *r, rpq_stats *out);

@@ -2,11 +2,15 @@
 // budget, graph loading, query compilation, batched evaluation driving the
 // traversal and emission kernels, results and fetch.
 #include <algorithm>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
+#include <chrono>
+
+#include "batch.h"
 #include "crpq.h"
 #include "device_common.cuh"
 #include "rpq_internal.h"
@@ -28,6 +32,7 @@ struct Workspace {
   u32 *claim = nullptr;
   u32 *lanesrc = nullptr;
   u64 *empty = nullptr;
+  u64 *spill = nullptr;  // SPILL_CAP chunk records of 6 words
 };
 
 }  // namespace
@@ -48,6 +53,8 @@ struct rpq_ctx {
   float alpha = 4.0f;
   uint64_t time_limit_ns = 20ull * 1000 * 1000 * 1000;
   uint32_t max_groups = 16;
+  bool trace = false;    // print per-level timings of each traversal (RPQ_TRACE=1)
+  rpq::BatchTuning batch = rpq::batch_default_tuning();  // run_rpq_batch tunables
   int live = 0;          // graphs and results not yet freed
   bool closing = false;  // rpq_destroy was called while handles were live
 };
@@ -157,6 +164,7 @@ void free_workspace(rpq_ctx *ctx) {
   dfree(ctx, w.claim, w.claim_cap);
   dfree(ctx, w.lanesrc, w.lane_cap);
   dfree(ctx, w.empty, w.lane_cap / 64);
+  dfree(ctx, w.spill, SPILL_CAP * 6);
   w = Workspace();
 }
 
@@ -179,7 +187,7 @@ int ensure_workspace(rpq_ctx *ctx, uint64_t words, uint64_t lists, uint64_t clai
   if ((rc = dalloc(ctx, &w.vis, words)) || (rc = dalloc(ctx, &w.fr0, words)) || (rc = dalloc(ctx, &w.fr1, words)) ||
       (rc = dalloc(ctx, &w.list0, lists)) || (rc = dalloc(ctx, &w.list1, lists)) ||
       (rc = dalloc(ctx, &w.claim, claims ? claims : 1)) || (rc = dalloc(ctx, &w.lanesrc, lanes)) ||
-      (rc = dalloc(ctx, &w.empty, lanes / 64 + 1))) {
+      (rc = dalloc(ctx, &w.empty, lanes / 64 + 1)) || (rc = dalloc(ctx, &w.spill, SPILL_CAP * 6))) {
     free_workspace(ctx);
     return rc;
   }
@@ -234,17 +242,6 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
   }
   Workspace &w = ctx->ws;
 
-  // bottom-up cost per level, in bytes, for the direction choice
-  double pull_fixed = 0;
-  for (uint32_t q2 = 0; q2 < Q; q2++) {
-    if (qd.in_begin[q2] == qd.in_begin[q2 + 1]) continue;
-    pull_fixed += (double)n * 8.0 * nw;
-    for (uint32_t j = qd.in_begin[q2]; j < qd.in_begin[q2 + 1]; j++) {
-      uint32_t l = qd.in_label[j];
-      double el = l < g.L ? (double)g.label_edges[l] : 0.0;
-      pull_fixed += (double)n * 8.0 + el * (4.0 + 8.0 * nw * __builtin_popcount(qd.in_from[j]));
-    }
-  }
 
   const int force = (flags & RPQ_FORCE_PUSH) ? 1 : (flags & RPQ_FORCE_PULL) ? 2 : 0;
   const int blocks = ctx->sms * ctx->bpsm[nw == 1 ? 0 : 1];
@@ -273,9 +270,13 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
     p.out_col = reverse ? g.in_col : g.out_col;
     p.in_off = reverse ? g.out_off : g.in_off;
     p.in_col = reverse ? g.out_col : g.in_col;
-    p.heavy_bits = reverse ? g.heavy_out_bits : g.heavy_in_bits;
-    p.heavy_list = reverse ? g.heavy_out_list : g.heavy_in_list;
-    p.n_heavy = reverse ? g.n_heavy_out : g.n_heavy_in;
+    // bottom-up levels read the in-direction of the traversal
+    p.hchunk = reverse ? g.hchunk_out : g.hchunk_in;
+    {
+      const std::vector<uint32_t> &ho = reverse ? g.hchunk_out_off : g.hchunk_in_off;
+      for (uint32_t l = 0; l <= g.L && l < ho.size(); l++) p.hchunk_off[l] = ho[l];
+      for (uint32_t l = 0; l < g.L; l++) p.label_edges[l] = g.label_edges[l];
+    }
     p.n = n;
     p.L = g.L;
     p.G = Gb;
@@ -285,6 +286,7 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
     p.fr0 = w.fr0;
     p.fr1 = w.fr1;
     p.claim = w.claim;
+    p.spill = w.spill;
     p.list0 = w.list0;
     p.list1 = w.list1;
     p.ctl = ctx->ctl;
@@ -292,7 +294,6 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
     p.nblocks = (unsigned)blocks;
     p.force = force;
     p.alpha = ctx->alpha;
-    p.pull_cost_fixed = pull_fixed * Gb;
     p.time_limit_ns = ctx->time_limit_ns;
     p.q = qd;
 
@@ -362,7 +363,17 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
     s.group_vertices += hctl.stats[ST_GROUP_VERTICES];
     s.pull_edges += hctl.stats[ST_PULL_EDGES];
     s.pull_vertices += hctl.stats[ST_PULL_VERTICES];
+    s.alg_bytes += hctl.stats[ST_ALG_BYTES];
     s.lane_groups += Gb;
+    if (ctx->trace) {
+      uint32_t nl = (uint32_t)std::min<uint64_t>(hctl.levels, TRACE_LEVELS);
+      std::fprintf(stderr, "[rpq trace] G=%u Q=%u levels=%llu W=%llu\n", Gb, Q, (unsigned long long)hctl.levels,
+                   (unsigned long long)hctl.stats[ST_W]);
+      for (uint32_t l = 0; l < nl; l++)
+        std::fprintf(stderr, "[rpq trace]   level %2u %s n=%10llu mf=%12llu %9.3f ms\n", l,
+                     hctl.trace_mode[l] == 1 ? "push" : "pull", (unsigned long long)hctl.trace_n[l],
+                     (unsigned long long)hctl.trace_mf[l], (hctl.trace_t[l + 1] - hctl.trace_t[l]) * 1e-6);
+    }
     ctx->stamp += (uint32_t)hctl.levels + 2;
 
     if (materialize) {
@@ -463,7 +474,10 @@ int rpq_create(rpq_ctx **out, int device, uint64_t mem_budget_bytes, void *cuda_
     return RPQ_ERR_CUDA;
   }
   if (const char *a = std::getenv("RPQ_ALPHA")) c->alpha = (float)std::atof(a);
-  if (const char *m = std::getenv("RPQ_MAX_GROUPS")) c->max_groups = (uint32_t)std::max(1, std::atoi(m));
+  if (const char *m = std::getenv("RPQ_MAX_GROUPS")) c->max_groups = (uint32_t)std::min(16, std::max(1, std::atoi(m)));
+  if (const char *t = std::getenv("RPQ_TRACE")) c->trace = std::atoi(t) != 0;
+  if (const char *b = std::getenv("RPQ_BATCH_LIST_CAP"))
+    c->batch.list_cap = (uint64_t)std::max(1024ll, std::atoll(b));
   if (dalloc(c, &c->ctl, 1) || dalloc(c, &c->small, 8)) {
     g_create_error = c->err;
     rpq_destroy(c);
@@ -574,8 +588,8 @@ int load_graph(rpq_ctx *ctx, uint32_t n_vertices, uint32_t n_labels, uint64_t n_
   {
     // the graph arrays were allocated inside build_graph outside the budget
     // accounting; account for them now
-    uint64_t b = rows * 8 + gr->g.m * 8 + 2 * (((uint64_t)n_vertices + 31) / 32 * 4) +
-                 ((uint64_t)gr->g.n_heavy_in + gr->g.n_heavy_out) * 4;
+    uint64_t b = rows * 8 + gr->g.m * 8 +
+                 12ull * ((uint64_t)gr->g.hchunk_in_off.back() + gr->g.hchunk_out_off.back());
     ctx->used += b;
     gr->bytes = b;
   }
@@ -600,10 +614,8 @@ fail:
   if (gr->g.in_off) cudaFreeAsync(gr->g.in_off, st);
   if (gr->g.out_col) cudaFreeAsync(gr->g.out_col, st);
   if (gr->g.in_col) cudaFreeAsync(gr->g.in_col, st);
-  if (gr->g.heavy_in_bits) cudaFreeAsync(gr->g.heavy_in_bits, st);
-  if (gr->g.heavy_in_list) cudaFreeAsync(gr->g.heavy_in_list, st);
-  if (gr->g.heavy_out_bits) cudaFreeAsync(gr->g.heavy_out_bits, st);
-  if (gr->g.heavy_out_list) cudaFreeAsync(gr->g.heavy_out_list, st);
+  if (gr->g.hchunk_in) cudaFreeAsync(gr->g.hchunk_in, st);
+  if (gr->g.hchunk_out) cudaFreeAsync(gr->g.hchunk_out, st);
   if (gr->g.vlabel) dfree(ctx, gr->g.vlabel, n_vertices);
   delete gr;
   release_handle(ctx);
@@ -627,10 +639,8 @@ void free_graph(rpq_graph *g) {
   cudaFreeAsync(g->g.in_off, st);
   cudaFreeAsync(g->g.out_col, st);
   cudaFreeAsync(g->g.in_col, st);
-  cudaFreeAsync(g->g.heavy_in_bits, st);
-  cudaFreeAsync(g->g.heavy_in_list, st);
-  cudaFreeAsync(g->g.heavy_out_bits, st);
-  cudaFreeAsync(g->g.heavy_out_list, st);
+  cudaFreeAsync(g->g.hchunk_in, st);
+  cudaFreeAsync(g->g.hchunk_out, st);
   ctx->used -= std::min(ctx->used, g->bytes);
   if (g->g.vlabel) dfree(ctx, g->g.vlabel, g->g.n);
   delete g;
@@ -707,6 +717,86 @@ int run_crpq(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_vars, const int32_t *v
   int rc = check_rpq_flags(ctx, flags);
   if (rc) return rc;
   return crpq_eval(ctx, g, n_vars, var_label, atoms, n_atoms, restrict0, n_restrict0, flags, out);
+}
+
+int run_rpq_batch(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_queries, const rpq_query *const *queries,
+                  const uint32_t *sources, uint32_t flags, rpq_result **out) {
+  if (!ctx || !g || !out || (n_queries && (!queries || !sources)))
+    return set_err(ctx, RPQ_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (!usable(ctx)) return RPQ_ERR_NO_DEVICE;
+  uint32_t mode = flags & (RPQ_MATERIALIZE | RPQ_COUNT_ONLY);
+  if ((mode != RPQ_MATERIALIZE && mode != RPQ_COUNT_ONLY) || (flags & ~(RPQ_MATERIALIZE | RPQ_COUNT_ONLY)))
+    return set_err(ctx, RPQ_ERR_INVALID_ARG, "run_rpq_batch takes RPQ_MATERIALIZE or RPQ_COUNT_ONLY only");
+  for (uint32_t i = 0; i < n_queries; i++) {
+    if (!queries[i]) return set_err(ctx, RPQ_ERR_INVALID_ARG, "null query");
+    if (sources[i] >= g->g.n) return set_err(ctx, RPQ_ERR_INVALID_ARG, "source id out of range");
+  }
+  const bool materialize = mode == RPQ_MATERIALIZE;
+  BatchOut bo;
+  int rc = n_queries ? batch_run(ctx, g, n_queries, queries, sources, materialize, ctx->batch, &bo) : RPQ_OK;
+  auto drop = [&]() {
+    for (auto &c : bo.chunks) dev_free(ctx, c.first, c.second * 8);
+    bo.chunks.clear();
+  };
+  if (rc) {
+    drop();
+    return rc;
+  }
+  u32 *tuples = nullptr;
+  if (materialize && bo.count) {
+    if (bo.chunks.size() == 1) {
+      tuples = bo.chunks[0].first;
+      bo.chunks.clear();
+    } else {
+      if ((rc = dev_alloc(ctx, (void **)&tuples, bo.count * 8))) {
+        drop();
+        return rc;
+      }
+      uint64_t o = 0;
+      for (auto &c : bo.chunks) {
+        cudaMemcpyAsync(tuples + 2 * o, c.first, c.second * 8, cudaMemcpyDeviceToDevice, ctx->stream);
+        o += c.second;
+      }
+      drop();
+    }
+  }
+  bo.stats.lane_words = 0;
+  return make_tuple_result(ctx, 2, tuples, bo.count, bo.dsum, bo.dxor, materialize, bo.stats, out);
+}
+
+int rpq_autotune_batch(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_queries, const rpq_query *const *queries,
+                       const uint32_t *sources, uint32_t *threads_out, uint32_t *queries_per_launch_out) {
+  if (!ctx || !g || (n_queries && (!queries || !sources))) return set_err(ctx, RPQ_ERR_INVALID_ARG, "null argument");
+  if (!usable(ctx)) return RPQ_ERR_NO_DEVICE;
+  for (uint32_t i = 0; i < n_queries; i++)
+    if (!queries[i] || sources[i] >= g->g.n) return set_err(ctx, RPQ_ERR_INVALID_ARG, "bad query or source");
+  BatchTuning best = ctx->batch;
+  double best_s = -1;
+  const int threads[] = {128, 256, 512};
+  const uint32_t qpls[] = {1024, 2048, 4096};
+  for (int t : threads)
+    for (uint32_t qpl : qpls) {
+      if (qpl > n_queries && qpl != qpls[0] && n_queries) continue;
+      BatchTuning cand = ctx->batch;
+      cand.threads = t;
+      cand.queries_per_launch = qpl;
+      BatchOut bo;
+      cudaStreamSynchronize(ctx->stream);
+      auto t0 = std::chrono::steady_clock::now();
+      int rc = n_queries ? batch_run(ctx, g, n_queries, queries, sources, false, cand, &bo) : RPQ_OK;
+      cudaStreamSynchronize(ctx->stream);
+      double s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (rc) return rc;
+      if (best_s < 0 || s < best_s) {
+        best_s = s;
+        best = cand;
+      }
+    }
+  ctx->batch = best;
+  if (threads_out) *threads_out = (uint32_t)best.threads;
+  if (queries_per_launch_out) *queries_per_launch_out = best.queries_per_launch;
+  return RPQ_OK;
 }
 
 int result_info(const rpq_result *r, uint64_t *count, uint32_t *arity, uint64_t *digest_sum, uint64_t *digest_xor) {
@@ -814,6 +904,7 @@ int rpq_rows_for_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, s
     stats->group_vertices += r.stats.group_vertices;
     stats->pull_edges += r.stats.pull_edges;
     stats->pull_vertices += r.stats.pull_vertices;
+    stats->alg_bytes += r.stats.alg_bytes;
     stats->lane_groups += r.stats.lane_groups;
     stats->bfs_ms += r.stats.bfs_ms;
     stats->emit_ms += r.stats.emit_ms;

@@ -1,0 +1,545 @@
+// Many single-source RPQs with different expressions in one persistent
+// launch (the batched form of Definition 1 with one start vertex per query).
+//
+// The paper evaluates each traversal group in a thread block and notes that
+// with few start vertices the GPU is poorly used (small-batch experiments,
+// Section 7.3).  Here every query keeps a dense visited bitmap over its own
+// (DFA state, vertex) pairs -- one bit each, Q_i * |V| bits -- and all
+// queries advance together, level by level, in one cooperative kernel over a
+// shared frontier list of (query, state, vertex) entries.  A level is
+// expanded top-down: a warp takes 32 entries, spreads the out-edges of their
+// transition rows evenly over its lanes, and test-and-sets the target bits
+// (a plain read first, the atomic only when the bit is clear); rows longer
+// than SPILL_EDGES are cut into chunks shared by all warps.  Results are the
+// accepting states' bitmaps, emitted as (query index, vertex) rows.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "batch.h"
+#include "crpq.h"
+#include "device_common.cuh"
+#include "rpq_internal.h"
+
+namespace rpq {
+
+namespace {
+
+constexpr int BATCH_THREADS = 256;  // default block size (the autotuner may pick another)
+constexpr int BATCH_MAX_THREADS = 512;
+constexpr unsigned ERR_LIST_FULL = 100;  // frontier list capacity exceeded
+
+struct BatchParams {
+  const uint32_t *out_off;
+  const uint32_t *out_col;
+  uint32_t n;
+  uint32_t L;
+  uint32_t nq;
+  const QueryDesc *qd;
+  const u64 *vis_off;  // first word of query i's bitmaps
+  const u32 *srcs;
+  u64 *vis;
+  u64 wps;             // words per state bitmap
+  u64 *list0, *list1;
+  u64 list_cap;
+  u64 *spill;
+  BfsCtl *ctl;
+  unsigned nblocks;
+  u64 time_limit_ns;
+};
+
+__device__ __forceinline__ u64 bentry(u32 i, u32 q, u32 v) { return ((u64)i << 37) | ((u64)q << 32) | v; }
+
+__device__ bool bbarrier(BfsCtl *c, unsigned nblocks, u64 limit_ns) {
+  __shared__ unsigned stop;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = &c->bar_gen;
+    unsigned g0 = *gen;
+    __threadfence();
+    unsigned arrived = atomicAdd(&c->bar_count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(&c->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&c->bar_gen, 1u);
+    } else {
+      u64 t0 = globaltimer_ns();
+      unsigned spins = 0;
+      while (*gen == g0) {
+        __nanosleep(100);
+        if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > limit_ns) {
+          atomicCAS(&c->err, 0u, (unsigned)(-RPQ_ERR_TIMEOUT));
+          break;
+        }
+        if (*(volatile unsigned *)&c->err) break;
+      }
+    }
+    __threadfence();
+    stop = *(volatile unsigned *)&c->err;
+  }
+  __syncthreads();
+  return stop == 0;
+}
+
+__device__ __forceinline__ u32 bdegsum(const BatchParams &p, const QueryDesc &qd, u32 q, u32 v) {
+  u32 s = 0;
+  for (u32 t = qd.out_begin[q]; t < qd.out_begin[q + 1]; t++) {
+    u32 l = qd.out_label[t];
+    if (l >= p.L) continue;
+    const u32 *off = p.out_off + (u64)l * (p.n + 1) + v;
+    s += __ldg(off + 1) - __ldg(off);
+  }
+  return s;
+}
+
+// Appends with a capacity check; a full list stops the search with an error
+// the host answers by splitting the batch.
+__device__ __forceinline__ void bappend(const BatchParams &p, bool take, u64 entry, unsigned long long *count,
+                                        u64 *list) {
+  u32 b = __ballot_sync(FULL_MASK, take);
+  if (!b) return;
+  u64 base = 0;
+  if (lane_id() == __ffs(b) - 1) base = atomicAdd(count, (unsigned long long)__popc(b));
+  base = __shfl_sync(FULL_MASK, base, __ffs(b) - 1);
+  u64 at = base + __popc(b & lanemask_lt());
+  if (take) {
+    if (at < p.list_cap)
+      list[at] = entry;
+    else
+      atomicCAS(&p.ctl->err, 0u, ERR_LIST_FULL);
+  }
+}
+
+// Test-and-set of (query i, state q2, vertex w); true when this thread set it.
+__device__ __forceinline__ bool bvisit(const BatchParams &p, u32 i, u32 q2, u32 w) {
+  u64 *word = p.vis + p.vis_off[i] + (u64)q2 * p.wps + (w >> 6);
+  const u64 bit = 1ull << (w & 63);
+  if (__ldcg(word) & bit) return false;
+  return !(atomicOr((unsigned long long *)word, bit) & bit);
+}
+
+__device__ void bseed(const BatchParams &p, u64 *W, u64 *N) {
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  for (u64 base = (u64)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < p.nq; base += stride) {
+    u64 i = base + lane_id();
+    bool take = false;
+    u32 s = 0;
+    if (i < p.nq && p.qd[i].n_states > 0) {
+      s = p.srcs[i];
+      take = bvisit(p, (u32)i, 0, s);
+      if (take) {
+        *W += bdegsum(p, p.qd[i], 0, s);
+        *N += 1;
+      }
+    }
+    bappend(p, take, bentry((u32)i, 0, s), &p.ctl->n_list[0], p.list0);
+  }
+}
+
+__device__ void bpush(const BatchParams &p, int lp, u32 cur, u32 nxt, u64 n_cur, u64 *edges) {
+  const u64 *list = lp ? p.list1 : p.list0;
+  u64 *nlist = lp ? p.list0 : p.list1;
+  const u32 lane = lane_id();
+  for (;;) {
+    u64 base = 0;
+    if (lane == 0) base = atomicAdd(&p.ctl->cursor[cur], 32ull);
+    base = __shfl_sync(FULL_MASK, base, 0);
+    if (base >= n_cur) break;
+    const u64 idx = base + lane;
+    const bool valid = idx < n_cur;
+    const u64 e = valid ? __ldcg(&list[idx]) : 0;
+    const u32 i = (u32)(e >> 37), q = (u32)(e >> 32) & 31u, v = (u32)e;
+    const QueryDesc *qd = p.qd + i;
+    const u32 t_beg = valid ? qd->out_begin[q] : 0;
+    const u32 nt = valid ? qd->out_begin[q + 1] - t_beg : 0;
+    const u32 max_nt = __reduce_max_sync(FULL_MASK, nt);
+    for (u32 j = 0; j < max_nt; j++) {
+      u32 rbeg = 0, rlen = 0, q2 = 0;
+      if (j < nt) {
+        const u32 t = t_beg + j;
+        const u32 l = qd->out_label[t];
+        q2 = qd->out_to[t];
+        if (l < p.L) {
+          const u32 *off = p.out_off + (u64)l * (p.n + 1) + v;
+          rbeg = __ldg(off);
+          rlen = __ldg(off + 1) - rbeg;
+        }
+      }
+      if (rlen > SPILL_EDGES) {
+        const u32 chunks = (rlen + SPILL_EDGES - 1) / SPILL_EDGES;
+        const u64 at = atomicAdd(&p.ctl->spill_count[cur], (unsigned long long)chunks);
+        if (at + chunks <= SPILL_CAP) {
+          for (u32 c = 0; c < chunks; c++) {
+            u64 *rec = p.spill + (at + c) * 2;
+            rec[0] = bentry(i, q2, 0) | (rbeg + c * SPILL_EDGES);
+            rec[1] = min(SPILL_EDGES, rlen - c * SPILL_EDGES);
+          }
+          rlen = 0;
+        }
+      }
+      u32 pre = rlen;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        u32 t = __shfl_up_sync(FULL_MASK, pre, o);
+        if (lane >= (u32)o) pre += t;
+      }
+      const u32 total = __shfl_sync(FULL_MASK, pre, 31);
+      pre -= rlen;
+      *edges += (lane == 0) ? total : 0;
+      for (u32 k0 = 0; k0 < total; k0 += 32) {
+        const u32 k = k0 + lane;
+        u32 o = 0;
+#pragma unroll
+        for (u32 step = 16; step > 0; step >>= 1) {
+          u32 pv = __shfl_sync(FULL_MASK, pre, o + step);
+          if (pv <= k) o += step;
+        }
+        const u32 o_beg = __shfl_sync(FULL_MASK, rbeg, o);
+        const u32 o_pre = __shfl_sync(FULL_MASK, pre, o);
+        const u32 o_q2 = __shfl_sync(FULL_MASK, q2, o);
+        const u32 o_i = __shfl_sync(FULL_MASK, i, o);
+        bool take = false;
+        u32 w = 0;
+        if (k < total) {
+          w = __ldg(p.out_col + o_beg + (k - o_pre));
+          take = bvisit(p, o_i, o_q2, w);
+        }
+        bappend(p, take, bentry(o_i, o_q2, w), &p.ctl->n_list[nxt], nlist);
+      }
+    }
+  }
+}
+
+__device__ void bspill(const BatchParams &p, int lp, u32 cur, u32 nxt, u64 *edges) {
+  u64 *nlist = lp ? p.list0 : p.list1;
+  const u32 lane = lane_id();
+  u64 count = *(volatile unsigned long long *)&p.ctl->spill_count[cur];
+  if (count > SPILL_CAP) count = SPILL_CAP;
+  for (;;) {
+    u64 r = 0;
+    if (lane == 0) r = atomicAdd(&p.ctl->spill_cursor[cur], 1ull);
+    r = __shfl_sync(FULL_MASK, r, 0);
+    if (r >= count) break;
+    const u64 h = __ldcg(p.spill + 2 * r);
+    const u32 len = (u32)__ldcg(p.spill + 2 * r + 1);
+    const u32 i = (u32)(h >> 37), q2 = (u32)(h >> 32) & 31u, b = (u32)h;
+    *edges += (lane == 0) ? len : 0;
+    for (u32 k0 = 0; k0 < len; k0 += 32) {
+      const u32 k = k0 + lane;
+      bool take = false;
+      u32 w = 0;
+      if (k < len) {
+        w = __ldg(p.out_col + b + k);
+        take = bvisit(p, i, q2, w);
+      }
+      bappend(p, take, bentry(i, q2, w), &p.ctl->n_list[nxt], nlist);
+    }
+  }
+}
+
+__device__ void bcommit(const BatchParams &p, int lp, u32 nxt, u64 *W, u64 *N) {
+  const u64 *nlist = lp ? p.list0 : p.list1;
+  u64 n_next = *(volatile unsigned long long *)&p.ctl->n_list[nxt];
+  if (n_next > p.list_cap) n_next = p.list_cap;
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  for (u64 j = (u64)blockIdx.x * blockDim.x + threadIdx.x; j < n_next; j += stride) {
+    const u64 e = __ldcg(&nlist[j]);
+    const u32 i = (u32)(e >> 37), q = (u32)(e >> 32) & 31u, v = (u32)e;
+    *W += bdegsum(p, p.qd[i], q, v);
+    *N += 1;
+  }
+}
+
+__global__ void __launch_bounds__(BATCH_MAX_THREADS) batch_kernel(const __grid_constant__ BatchParams p) {
+  BfsCtl *c = p.ctl;
+  u64 W = 0, N = 0, edges = 0, push_levels = 0;
+  bseed(p, &W, &N);
+  if (!bbarrier(c, p.nblocks, p.time_limit_ns)) return;
+  u32 level = 0;
+  for (;; level++) {
+    const u32 cur = level % 3, nxt = (level + 1) % 3, old = (level + 2) % 3;
+    const int lp = level & 1;
+    u64 n_cur = *(volatile unsigned long long *)&c->n_list[cur];
+    if (n_cur > p.list_cap) n_cur = p.list_cap;
+    if (n_cur == 0) break;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      c->n_list[old] = 0;
+      c->cursor[old] = 0;
+      c->spill_count[old] = 0;
+      c->spill_cursor[old] = 0;
+      if (level < (u32)TRACE_LEVELS) {
+        c->trace_t[level] = globaltimer_ns();
+        c->trace_n[level] = n_cur;
+        c->trace_mode[level] = 1u;
+      }
+      push_levels++;
+    }
+    bpush(p, lp, cur, nxt, n_cur, &edges);
+    if (!bbarrier(c, p.nblocks, p.time_limit_ns)) return;
+    if (*(volatile unsigned long long *)&c->spill_count[cur] != 0) {
+      bspill(p, lp, cur, nxt, &edges);
+      if (!bbarrier(c, p.nblocks, p.time_limit_ns)) return;
+    }
+    bcommit(p, lp, nxt, &W, &N);
+    if (!bbarrier(c, p.nblocks, p.time_limit_ns)) return;
+  }
+  W = warp_sum(W);
+  N = warp_sum(N);
+  edges = warp_sum(edges);
+  if (lane_id() == 0) {
+    if (W) atomicAdd(&c->stats[ST_W], W);
+    if (N) atomicAdd(&c->stats[ST_N], N);
+    if (edges) atomicAdd(&c->stats[ST_GROUP_EDGES], edges);
+    if (N) atomicAdd(&c->stats[ST_GROUP_VERTICES], N);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c->levels = level;
+    c->stats[ST_PUSH_LEVELS] += push_levels;
+    c->trace_t[level < (u32)TRACE_LEVELS ? level : TRACE_LEVELS] = globaltimer_ns();
+  }
+}
+
+// Emission: chunk c (BEMIT_WORDS words = BEMIT_WORDS * 64 vertices) of query
+// i's result bitmap (OR of its accepting states' bitmaps).
+constexpr int BEMIT_WORDS = 256;
+
+struct BEmitParams {
+  const u64 *vis;
+  const u64 *vis_off;
+  const QueryDesc *qd;
+  u64 wps;
+  u32 chunks;
+  u32 *cnt;
+  const u64 *off;
+  u32 *rows;  // (query, vertex) pairs
+  u64 *digest;
+  u32 qbase;  // index of this launch's first query in the caller's arrays
+};
+
+template <bool WRITE>
+__global__ void __launch_bounds__(BEMIT_WORDS) batch_emit(const BEmitParams p) {
+  const u32 c = blockIdx.x, i = blockIdx.y;
+  const u64 k = (u64)c * BEMIT_WORDS + threadIdx.x;
+  u64 r = 0;
+  const u32 fm_all = p.qd[i].final_mask;
+  if (k < p.wps)
+    for (u32 fm = fm_all; fm; fm &= fm - 1) r |= __ldcg(p.vis + p.vis_off[i] + (u64)(__ffs(fm) - 1) * p.wps + k);
+  const u32 pc = __popcll(r);
+  __shared__ u32 warp_tot[BEMIT_WORDS / 32];
+  u32 inc = pc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    u32 t = __shfl_up_sync(FULL_MASK, inc, o);
+    if (lane_id() >= (u32)o) inc += t;
+  }
+  if (lane_id() == 31) warp_tot[threadIdx.x >> 5] = inc;
+  __syncthreads();
+  u32 before = 0, block_tot = 0;
+  for (u32 wv = 0; wv < BEMIT_WORDS / 32; wv++) {
+    if (wv < (threadIdx.x >> 5)) before += warp_tot[wv];
+    block_tot += warp_tot[wv];
+  }
+  if (!WRITE) {
+    u64 hs = 0, hx = 0;
+    for (u64 b = r; b; b &= b - 1) {
+      u64 h = splitmix64(((u64)(p.qbase + i) << 32) | (k * 64 + __ffsll(b) - 1));
+      hs += h;
+      hx ^= h;
+    }
+    hs = warp_sum(hs);
+    hx = warp_xor(hx);
+    if (lane_id() == 0 && (hs | hx)) {
+      atomicAdd(&p.digest[0], hs);
+      atomicXor(&p.digest[1], hx);
+    }
+    if (threadIdx.x == 0) p.cnt[(u64)i * p.chunks + c] = block_tot;
+  } else {
+    u64 pos = p.off[(u64)i * p.chunks + c] + before + inc - pc;
+    for (u64 b = r; b; b &= b - 1) {
+      p.rows[2 * pos] = p.qbase + i;
+      p.rows[2 * pos + 1] = (u32)(k * 64 + __ffsll(b) - 1);
+      pos++;
+    }
+  }
+}
+
+int berr(rpq_ctx *ctx, cudaError_t e, const char *what) {
+  return ctx_error(ctx, RPQ_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T>
+struct DBuf {
+  rpq_ctx *ctx = nullptr;
+  T *p = nullptr;
+  uint64_t n = 0;
+  int alloc(rpq_ctx *c, uint64_t count) {
+    ctx = c;
+    n = std::max<uint64_t>(count, 1);
+    return ctx_alloc(c, (void **)&p, n * sizeof(T));
+  }
+  T *release_ownership() {
+    T *q = p;
+    p = nullptr;
+    return q;
+  }
+  ~DBuf() {
+    if (p) ctx_free(ctx, p, n * sizeof(T));
+  }
+};
+
+}  // namespace
+
+BatchTuning batch_default_tuning() { return BatchTuning{BATCH_THREADS, 4096, 1ull << 28}; }
+
+// One launch over queries [0, nq) of the arrays; appends rows to `out`.
+static int batch_launch(rpq_ctx *ctx, const rpq_graph *g, uint32_t qbase, uint32_t nq,
+                        const rpq_query *const *queries, const uint32_t *sources, bool materialize,
+                        const BatchTuning &tun, BatchOut *out) {
+  const DevGraph &dg = graph_dev(g);
+  cudaStream_t st = ctx_stream(ctx);
+  const u64 wps = ((u64)dg.n + 63) / 64;
+  std::vector<QueryDesc> descs(nq);
+  std::vector<u64> voff(nq + 1, 0);
+  for (uint32_t i = 0; i < nq; i++) {
+    descs[i] = query_host(queries[i]).d;
+    voff[i + 1] = voff[i] + (u64)descs[i].n_states * wps;
+  }
+  const u64 vis_words = std::max<u64>(voff[nq], 1);
+  DBuf<QueryDesc> d_qd;
+  DBuf<u64> d_voff, d_vis, d_l0, d_l1, d_spill, d_small, d_off, d_tmp;
+  DBuf<u32> d_src, d_cnt;
+  DBuf<BfsCtl> d_ctl;
+  int rc;
+  if ((rc = d_qd.alloc(ctx, nq)) || (rc = d_voff.alloc(ctx, nq + 1)) || (rc = d_src.alloc(ctx, nq)) ||
+      (rc = d_vis.alloc(ctx, vis_words)) || (rc = d_l0.alloc(ctx, tun.list_cap)) ||
+      (rc = d_l1.alloc(ctx, tun.list_cap)) || (rc = d_spill.alloc(ctx, SPILL_CAP * 2)) ||
+      (rc = d_ctl.alloc(ctx, 1)) || (rc = d_small.alloc(ctx, 4)))
+    return rc;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(d_qd.p, descs.data(), nq * sizeof(QueryDesc), cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemcpyAsync(d_voff.p, voff.data(), (nq + 1) * 8, cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemcpyAsync(d_src.p, sources, nq * 4, cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemsetAsync(d_vis.p, 0, vis_words * 8, st)) || (e = cudaMemsetAsync(d_ctl.p, 0, sizeof(BfsCtl), st)) ||
+      (e = cudaMemsetAsync(d_small.p, 0, 32, st)))
+    return berr(ctx, e, "batch upload");
+
+  BatchParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.out_off = dg.out_off;
+  p.out_col = dg.out_col;
+  p.n = dg.n;
+  p.L = dg.L;
+  p.nq = nq;
+  p.qd = d_qd.p;
+  p.vis_off = d_voff.p;
+  p.srcs = d_src.p;
+  p.vis = d_vis.p;
+  p.wps = wps;
+  p.list0 = d_l0.p;
+  p.list1 = d_l1.p;
+  p.list_cap = tun.list_cap;
+  p.spill = d_spill.p;
+  p.ctl = d_ctl.p;
+  p.time_limit_ns = ctx_time_limit_ns(ctx);
+  int bpsm = 0, sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, batch_kernel, tun.threads, 0)) != cudaSuccess)
+    return berr(ctx, e, "occupancy");
+  const int blocks = sms * bpsm;
+  p.nblocks = (unsigned)blocks;
+  void *args[] = {(void *)&p};
+  cudaEvent_t ev0, ev1;
+  cudaEventCreate(&ev0);
+  cudaEventCreate(&ev1);
+  cudaEventRecord(ev0, st);
+  e = cudaLaunchCooperativeKernel((void *)batch_kernel, blocks, tun.threads, args, 0, st);
+  cudaEventRecord(ev1, st);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    return berr(ctx, e, "batch_kernel");
+  }
+  out->stats.launches += 1;
+  out->stats.bfs_launches += 1;
+
+  // emission pass 1: counts and digest
+  const u32 chunks = (u32)((wps + BEMIT_WORDS - 1) / BEMIT_WORDS);
+  const u64 ncnt = (u64)nq * chunks;
+  if ((rc = d_cnt.alloc(ctx, ncnt)) || (rc = d_off.alloc(ctx, ncnt)) || (rc = d_tmp.alloc(ctx, scan_tmp_words(ncnt))))
+    return rc;
+  BEmitParams ep;
+  ep.vis = d_vis.p;
+  ep.vis_off = d_voff.p;
+  ep.qd = d_qd.p;
+  ep.wps = wps;
+  ep.chunks = chunks;
+  ep.cnt = d_cnt.p;
+  ep.off = d_off.p;
+  ep.rows = nullptr;
+  ep.digest = d_small.p;
+  ep.qbase = qbase;
+  dim3 grid(chunks, nq);
+  batch_emit<false><<<grid, BEMIT_WORDS, 0, st>>>(ep);
+  if ((e = cudaGetLastError()) != cudaSuccess) return berr(ctx, e, "batch_emit");
+  if ((e = exclusive_scan_u32_to_u64(d_cnt.p, d_off.p, ncnt, d_small.p + 2, d_tmp.p, st)) != cudaSuccess)
+    return berr(ctx, e, "scan");
+  out->stats.launches += 2;
+  BfsCtl hctl;
+  u64 hsmall[3];
+  if ((e = cudaMemcpyAsync(&hctl, d_ctl.p, sizeof(BfsCtl), cudaMemcpyDeviceToHost, st)) ||
+      (e = cudaMemcpyAsync(hsmall, d_small.p, 24, cudaMemcpyDeviceToHost, st)) || (e = cudaStreamSynchronize(st))) {
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    return berr(ctx, e, "batch readback");
+  }
+  float ms = 0;
+  cudaEventElapsedTime(&ms, ev0, ev1);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  if (hctl.err == ERR_LIST_FULL) return RPQ_BATCH_SPLIT;
+  if (hctl.err) return ctx_error(ctx, RPQ_ERR_TIMEOUT, "batch traversal grid barrier wait ran out of time");
+  out->stats.bfs_ms += ms;
+  out->stats.product_edges += hctl.stats[ST_W];
+  out->stats.product_vertices += hctl.stats[ST_N];
+  out->stats.levels += hctl.levels;
+  out->stats.push_levels += hctl.stats[ST_PUSH_LEVELS];
+  out->stats.group_edges += hctl.stats[ST_GROUP_EDGES];
+  out->stats.group_vertices += hctl.stats[ST_GROUP_VERTICES];
+  out->stats.lane_groups += 1;
+  const u64 total = hsmall[2];
+  out->count += total;
+  out->dsum += hsmall[0];
+  out->dxor ^= hsmall[1];
+  if (materialize && total) {
+    u32 *rows = nullptr;
+    if ((rc = ctx_alloc(ctx, (void **)&rows, total * 8))) return rc;
+    ep.rows = rows;
+    batch_emit<true><<<grid, BEMIT_WORDS, 0, st>>>(ep);
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+      ctx_free(ctx, rows, total * 8);
+      return berr(ctx, e, "batch_emit");
+    }
+    out->stats.launches += 1;
+    out->chunks.push_back({rows, total});
+  }
+  return RPQ_OK;
+}
+
+int batch_run(rpq_ctx *ctx, const rpq_graph *g, uint32_t nq, const rpq_query *const *queries,
+              const uint32_t *sources, bool materialize, const BatchTuning &tun, BatchOut *out) {
+  for (uint32_t b0 = 0; b0 < nq;) {
+    uint32_t k = std::min<uint32_t>(tun.queries_per_launch, nq - b0);
+    for (;;) {
+      int rc = batch_launch(ctx, g, b0, k, queries + b0, sources + b0, materialize, tun, out);
+      if (rc == RPQ_OK) break;
+      if (rc != RPQ_BATCH_SPLIT) return rc;
+      if (k == 1) return ctx_error(ctx, RPQ_ERR_OUT_OF_BUDGET, "one query's frontier exceeds the list capacity");
+      k = (k + 1) / 2;  // frontier list too small for this many queries at once: halve
+    }
+    b0 += k;
+  }
+  return RPQ_OK;
+}
+
+}  // namespace rpq

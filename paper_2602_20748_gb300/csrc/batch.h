@@ -1,0 +1,33 @@
+// Interface of the batched single-source engine (batch.cu).
+#pragma once
+
+#include <utility>
+#include <vector>
+
+#include "device_common.cuh"
+#include "rpq_internal.h"
+
+namespace rpq {
+
+constexpr int RPQ_BATCH_SPLIT = 1;  // internal: the launch must be retried with fewer queries
+
+// Tunables of the batched engine (chosen by rpq_autotune_batch).
+struct BatchTuning {
+  int threads;                  // block size of the persistent kernel
+  uint32_t queries_per_launch;  // queries sharing one launch
+  uint64_t list_cap;            // frontier list capacity (entries)
+};
+
+struct BatchOut {
+  uint64_t count = 0, dsum = 0, dxor = 0;
+  rpq_stats stats{};
+  std::vector<std::pair<u32 *, uint64_t>> chunks;  // row-major (query, vertex) rows, in order
+};
+
+BatchTuning batch_default_tuning();
+
+// Evaluates queries[i] from sources[i] for i < nq; rows (i, y) sorted.
+int batch_run(rpq_ctx *ctx, const rpq_graph *g, uint32_t nq, const rpq_query *const *queries,
+              const uint32_t *sources, bool materialize, const BatchTuning &tun, BatchOut *out);
+
+}  // namespace rpq

@@ -37,7 +37,7 @@ __global__ void emit_kernel(const EmitParams p) {
     if (w < p.n) {
       for (u32 fm = p.final_mask; fm; fm &= fm - 1) {
         u32 q = __ffs(fm) - 1;
-        u64 word = (((u64)g * p.Q + q) * p.n + w) * NW;
+        u64 word = (((u64)q * p.n + w) * p.G + g) * NW;
         x |= __ldcg(vis32 + word * 2 + col);
       }
     }
@@ -110,7 +110,7 @@ __global__ void emit_pairs_kernel(const EmitParams p, u32 *__restrict__ out) {
     if (w < p.n) {
       for (u32 fm = p.final_mask; fm; fm &= fm - 1) {
         u32 q = __ffs(fm) - 1;
-        u64 word = (((u64)g * p.Q + q) * p.n + w) * NW;
+        u64 word = (((u64)q * p.n + w) * p.G + g) * NW;
         x |= __ldcg(vis32 + word * 2 + col);
       }
     }

@@ -7,6 +7,7 @@
 // radix sort, drop adjacent duplicates (identical triples count once), then
 // locate the row boundaries by binary search; the in-edge CSR repeats this with
 // (label | dst | src) keys.
+#include <algorithm>
 #include <string>
 
 #include "device_common.cuh"
@@ -128,28 +129,29 @@ __global__ void label_bounds(const uint32_t *__restrict__ off, uint32_t n, uint3
   }
 }
 
-// flag[v] = total degree of v over all labels >= thresh; bits[v / 32] holds
-// the same flags packed (n rounded up to a whole warp).
-__global__ void mark_heavy(const uint32_t *__restrict__ off, uint32_t n, uint32_t L, uint32_t thresh,
-                           u32 *__restrict__ flag, u32 *__restrict__ bits) {
-  const u64 n_pad = ((u64)n + 31) & ~31ull;
-  for (u64 v = (u64)blockIdx.x * blockDim.x + threadIdx.x; v < n_pad; v += (u64)gridDim.x * blockDim.x) {
-    bool heavy = false;
-    if (v < n) {
-      u64 d = 0;
-      for (uint32_t l = 0; l < L; l++) d += off[(u64)l * (n + 1) + v + 1] - off[(u64)l * (n + 1) + v];
-      heavy = d >= thresh;
-      flag[v] = heavy ? 1u : 0u;
-    }
-    u32 b = __ballot_sync(FULL_MASK, heavy);
-    if ((threadIdx.x & 31) == 0) bits[v / 32] = b;
+// Chunks of long rows: cnt[v] = number of HCHUNK-edge chunks of row v of one
+// label's CSR when the row has at least HEAVY_ROW edges, else 0.
+__global__ void count_chunks(const uint32_t *__restrict__ off, uint32_t n, u32 *__restrict__ cnt) {
+  for (u64 v = (u64)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (u64)gridDim.x * blockDim.x) {
+    uint32_t len = off[v + 1] - off[v];
+    cnt[v] = len >= HEAVY_ROW ? (len + HCHUNK - 1) / HCHUNK : 0u;
   }
 }
 
-__global__ void list_heavy(const u32 *__restrict__ flag, const u64 *__restrict__ pos, uint32_t n,
-                           uint32_t *__restrict__ list) {
-  for (u64 v = (u64)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (u64)gridDim.x * blockDim.x)
-    if (flag[v]) list[pos[v]] = (uint32_t)v;
+// Chunk records (vertex, first edge, end edge) at out[3 * (base + pos[v] + c)].
+__global__ void write_chunks(const uint32_t *__restrict__ off, uint32_t n, const u64 *__restrict__ pos, u64 base,
+                             uint32_t *__restrict__ out) {
+  for (u64 v = (u64)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (u64)gridDim.x * blockDim.x) {
+    uint32_t b = off[v], len = off[v + 1] - b;
+    if (len < HEAVY_ROW) continue;
+    uint32_t k = (len + HCHUNK - 1) / HCHUNK;
+    for (uint32_t c = 0; c < k; c++) {
+      u64 r = 3 * (base + pos[v] + c);
+      out[r] = (uint32_t)v;
+      out[r + 1] = b + c * HCHUNK;
+      out[r + 2] = min(b + (c + 1) * HCHUNK, b + len);
+    }
+  }
 }
 
 // (label | src | dst) -> (label | dst | src)
@@ -250,36 +252,43 @@ static int bits_for(uint64_t n) {
   return b;
 }
 
-// Flags, packed bits and sorted list of the vertices whose total degree in
-// the CSR `off` reaches HEAVY_DEGREE.
-static cudaError_t build_heavy(const uint32_t *off, uint32_t n, uint32_t L, uint32_t **bits, uint32_t **list,
-                               uint32_t *count, cudaStream_t st) {
-  u32 *flag = nullptr;
-  u64 *pos = nullptr, *tmp = nullptr, *dcount = nullptr;
-  u64 hcount = 0;
-  const u64 words = ((u64)n + 31) / 32;
-  cudaError_t e = cudaMallocAsync(&flag, (u64)n * 4, st);
+// Chunk records of the long rows of every label of the CSR `off`; offs gets
+// the L + 1 per-label chunk offsets.
+static cudaError_t build_chunks(const uint32_t *off, uint32_t n, uint32_t L, uint32_t **chunks,
+                                std::vector<uint32_t> *offs, cudaStream_t st) {
+  u32 *cnt = nullptr;
+  u64 *pos = nullptr, *tmp = nullptr, *dtot = nullptr;
+  offs->assign(L + 1, 0);
+  cudaError_t e = cudaMallocAsync(&cnt, (u64)n * 4, st);
   if (e == cudaSuccess) e = cudaMallocAsync(&pos, (u64)n * 8, st);
   if (e == cudaSuccess) e = cudaMallocAsync(&tmp, scan_tmp_words(n) * 8, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&dcount, 8, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(bits, words * 4, st);
-  if (e == cudaSuccess) {
-    mark_heavy<<<grid_for(words * 32, 256), 256, 0, st>>>(off, n, L, HEAVY_DEGREE, flag, *bits);
-    e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMallocAsync(&dtot, 8, st);
+  for (int pass = 0; pass < 2 && e == cudaSuccess; pass++) {
+    if (pass == 1) {
+      for (uint32_t l = 0; l < L; l++) (*offs)[l + 1] += (*offs)[l];
+      e = cudaMallocAsync(chunks, 3 * (u64)std::max(1u, (*offs)[L]) * 4, st);
+    }
+    for (uint32_t l = 0; l < L && e == cudaSuccess; l++) {
+      const uint32_t *row = off + (u64)l * (n + 1);
+      count_chunks<<<grid_for(n, 256), 256, 0, st>>>(row, n, cnt);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = exclusive_scan_u32_to_u64(cnt, pos, n, dtot, tmp, st);
+      if (e != cudaSuccess) break;
+      if (pass == 0) {
+        u64 t = 0;
+        e = cudaMemcpyAsync(&t, dtot, 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        (*offs)[l + 1] = (uint32_t)t;
+      } else {
+        write_chunks<<<grid_for(n, 256), 256, 0, st>>>(row, n, pos, (*offs)[l], *chunks);
+        e = cudaGetLastError();
+      }
+    }
   }
-  if (e == cudaSuccess) e = exclusive_scan_u32_to_u64(flag, pos, n, dcount, tmp, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&hcount, dcount, 8, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e == cudaSuccess) e = cudaMallocAsync(list, (hcount ? hcount : 1) * 4, st);
-  if (e == cudaSuccess) {
-    list_heavy<<<grid_for(n, 256), 256, 0, st>>>(flag, pos, n, *list);
-    e = cudaGetLastError();
-  }
-  *count = (uint32_t)hcount;
-  if (flag) cudaFreeAsync(flag, st);
+  if (cnt) cudaFreeAsync(cnt, st);
   if (pos) cudaFreeAsync(pos, st);
   if (tmp) cudaFreeAsync(tmp, st);
-  if (dcount) cudaFreeAsync(dcount, st);
+  if (dtot) cudaFreeAsync(dtot, st);
   return e;
 }
 
@@ -373,8 +382,8 @@ int build_graph(DevGraph *g, uint32_t n, uint32_t L, uint64_t m, const uint32_t 
     g->label_edges.assign(L, 0);
     for (uint32_t l = 0; l < L; l++) g->label_edges[l] = (uint64_t)ends[2 * l + 1] - ends[2 * l];
   }
-  RPQ_TRY(build_heavy(g->in_off, n, L, &g->heavy_in_bits, &g->heavy_in_list, &g->n_heavy_in, st));
-  RPQ_TRY(build_heavy(g->out_off, n, L, &g->heavy_out_bits, &g->heavy_out_list, &g->n_heavy_out, st));
+  RPQ_TRY(build_chunks(g->in_off, n, L, &g->hchunk_in, &g->hchunk_in_off, st));
+  RPQ_TRY(build_chunks(g->out_off, n, L, &g->hchunk_out, &g->hchunk_out_off, st));
 done:
   if (ka) cudaFreeAsync(ka, st);
   if (kb) cudaFreeAsync(kb, st);

@@ -10,17 +10,25 @@
 //
 // How (design of this engine, not the paper's hop-limited DFS / segment
 // pooling): start vertices are packed as bit lanes, K = 64 * NW of them per
-// lane group.  For every (group, state, vertex) there is one K-bit word in
-// each of three arrays: VIS (visited), and two frontier words used in
-// ping-pong.  One word operation therefore advances K searches.  A level is
-// expanded either
-//   * top-down ("push"): the sparse list of frontier entries is scanned, each
-//     entry's out-edges on the labels of its state's transitions are read and
-//     the new lanes are OR-ed into the next frontier word with atomics, or
-//   * bottom-up ("pull"): every (vertex, target state) word gathers the
-//     frontier words of its in-neighbours on the transition labels, with no
-//     atomics and an early exit once all lanes are visited,
-// chosen per level from the byte cost of each.  The whole search is one
+// lane group, G groups per launch.  For every (state, vertex, group) there is
+// one K-bit word in each of three arrays: VIS (visited) and two frontier
+// words used in ping-pong, laid out [state][vertex][group][word] so that the
+// G words of one (state, vertex) are contiguous (G * 8 * NW bytes, 512 for
+// 16 groups of 256 lanes).  A level is expanded either
+//   * top-down ("push"): the sparse list of (group, state, vertex) frontier
+//     entries is scanned, the out-edges on the labels of the state's
+//     transitions are spread evenly over the lanes of a warp, and the new
+//     lanes are OR-ed into the next frontier word with atomics; rows longer
+//     than SPILL_EDGES are cut into chunks shared by all warps; or
+//   * bottom-up ("pull"): a warp takes one vertex and all groups at once: for
+//     each in-edge on an incoming transition from a state that is present in
+//     the frontier, it gathers the neighbour's G frontier words (one
+//     coalesced 512-byte read) and ORs them into per-lane accumulators; rows
+//     with at least HEAVY_ROW in-edges are cut (at graph load) into chunks
+//     shared by all warps,
+// chosen per level from the byte cost of each given the DFA states present
+// in the frontier.  New lanes land in the next frontier word; a commit phase
+// folds them into VIS and clears the old frontier.  The whole search is one
 // persistent cooperative launch; levels are separated by a grid barrier whose
 // waits are bounded by a time limit (on expiry the kernel records
 // RPQ_ERR_TIMEOUT and returns).
@@ -73,19 +81,17 @@ __device__ __forceinline__ bool any_bits(const Word<NW> &x) {
 }
 
 template <int NW>
-__device__ __forceinline__ bool all_bits(const Word<NW> &x) {
-  u64 a = ~0ull;
-#pragma unroll
-  for (int i = 0; i < NW; i++) a &= x.w[i];
-  return a == ~0ull;
-}
-
-template <int NW>
 __device__ __forceinline__ u32 popc_w(const Word<NW> &x) {
   u32 c = 0;
 #pragma unroll
   for (int i = 0; i < NW; i++) c += __popcll(x.w[i]);
   return c;
+}
+
+// First u64 of the word of (group g, state q, vertex v).
+template <int NW>
+__device__ __forceinline__ u64 widx(const BfsParams &p, u32 g, u32 q, u32 v) {
+  return (((u64)q * p.n + v) * p.G + g) * NW;
 }
 
 // Grid-wide barrier for a cooperative launch.  Waits are bounded by the
@@ -161,11 +167,10 @@ __device__ void seed_phase(const BfsParams &p, u64 *stat) {
       u32 s = p.lanesrc[i];
       if (s != NO_SOURCE) {
         u32 g = (u32)(i / K), lane = (u32)(i % K);
-        u64 gq = (u64)g * p.Q;  // start state 0
-        u64 wi = (gq * p.n + s) * NW;
+        u64 wi = widx<NW>(p, g, 0, s);  // start state 0
         p.vis[wi + lane / 64] |= 1ull << (lane % 64);
         p.fr0[wi + lane / 64] = 1ull << (lane % 64);
-        entry = (gq << 32) | s;
+        entry = ((u64)g * p.Q << 32) | s;
         take = true;
         u32 d = degsum(p, 0, s);
         W += d;
@@ -184,18 +189,46 @@ __device__ void seed_phase(const BfsParams &p, u64 *stat) {
     stat[ST_GROUP_VERTICES] += N;
     if (mf) atomicAdd(&p.ctl->mf[0], mf);
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&p.ctl->smask[0], 1u);
 }
 
-// Top-down expansion of the entries of the current list.
+// One top-down relaxation of edge (tgq, w) with source lanes fm: the lanes
+// not yet visited at (tgq, w) are OR-ed into the next frontier word; returns
+// whether this thread must list (tgq, w) in the next frontier.
+template <int NW>
+__device__ __forceinline__ bool relax(const BfsParams &p, u64 *FB, u32 tgq, u32 w, const Word<NW> &fm, u32 stamp) {
+  const u32 g = tgq / p.Q, q2 = tgq - g * p.Q;
+  const u64 wi = widx<NW>(p, g, q2, w);
+  Word<NW> vis = load_cg<NW>(p.vis + wi);
+  Word<NW> m;
+#pragma unroll
+  for (int i = 0; i < NW; i++) m.w[i] = fm.w[i] & ~vis.w[i];
+  if (!any_bits(m)) return false;
+  if constexpr (NW == 1) {
+    u64 old = atomicOr((unsigned long long *)(FB + wi), m.w[0]);
+    return old == 0;
+  } else {
+#pragma unroll
+    for (int i = 0; i < NW; i++)
+      if (m.w[i]) atomicOr((unsigned long long *)(FB + wi + i), m.w[i]);
+    u32 old = atomicMax(p.claim + (((u64)q2 * p.n + w) * p.G + g), stamp);
+    return old < stamp;
+  }
+}
+
+// Top-down expansion of the entries of the current list.  A warp takes 32
+// entries at a time and spreads the edges of their rows evenly over its lanes
+// (prefix sum of row lengths, owner found by binary search); rows longer than
+// SPILL_EDGES are queued in chunks for the spill sub-phase.
 template <int NW>
 __device__ void push_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u64 n_cur, u32 stamp, u64 *stat) {
   const u64 *list = lp ? p.list1 : p.list0;
   u64 *nlist = lp ? p.list0 : p.list1;
   const u64 *F = lp ? p.fr1 : p.fr0;
   u64 *FB = lp ? p.fr0 : p.fr1;
-  const u32 n = p.n, Q = p.Q, n1 = p.n + 1;
+  const u32 Q = p.Q, n1 = p.n + 1;
   const u32 lane = lane_id();
-  u64 edges = 0, rows = 0;
+  u64 edges = 0, rows = 0, entries = 0;
   for (;;) {
     u64 base = 0;
     if (lane == 0) base = atomicAdd(&p.ctl->cursor[cur], 32ull);
@@ -209,7 +242,8 @@ __device__ void push_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u64 n_c
     Word<NW> fm;
 #pragma unroll
     for (int i = 0; i < NW; i++) fm.w[i] = 0;
-    if (valid) fm = load_cg<NW>(F + ((u64)gq * n + v) * NW);
+    if (valid) fm = load_cg<NW>(F + widx<NW>(p, g, q, v));
+    entries += valid;
     u32 t_beg = valid ? p.q.out_begin[q] : 0;
     u32 nt = valid ? p.q.out_begin[q + 1] - t_beg : 0;
     u32 max_nt = __reduce_max_sync(FULL_MASK, nt);
@@ -224,6 +258,20 @@ __device__ void push_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u64 n_c
           rbeg = __ldg(off);
           rlen = __ldg(off + 1) - rbeg;
           rows++;
+        }
+      }
+      if (p.spill && rlen > SPILL_EDGES) {
+        const u32 chunks = (rlen + SPILL_EDGES - 1) / SPILL_EDGES;
+        const u64 at = atomicAdd(&p.ctl->spill_count[cur], (unsigned long long)chunks);
+        if (at + chunks <= SPILL_CAP) {
+          for (u32 c = 0; c < chunks; c++) {
+            u64 *rec = p.spill + (at + c) * (2 + NW);
+            rec[0] = ((u64)tgq << 32) | (rbeg + c * SPILL_EDGES);
+            rec[1] = min(SPILL_EDGES, rlen - c * SPILL_EDGES);
+#pragma unroll
+            for (int t = 0; t < NW; t++) rec[2 + t] = fm.w[t];
+          }
+          rlen = 0;
         }
       }
       // exclusive prefix of row lengths across the warp
@@ -255,221 +303,327 @@ __device__ void push_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u64 n_c
         u32 w = 0;
         if (k < total) {
           w = __ldg(p.out_col + o_beg + (k - o_pre));
-          u64 wi = ((u64)o_gq * n + w) * NW;
-          Word<NW> vis = load_cg<NW>(p.vis + wi);
-          Word<NW> m;
-#pragma unroll
-          for (int i = 0; i < NW; i++) m.w[i] = ofm.w[i] & ~vis.w[i];
-          if (any_bits(m)) {
-            if constexpr (NW == 1) {
-              u64 old = atomicOr((unsigned long long *)(FB + wi), m.w[0]);
-              take = (old == 0);
-            } else {
-#pragma unroll
-              for (int i = 0; i < NW; i++)
-                if (m.w[i]) atomicOr((unsigned long long *)(FB + wi + i), m.w[i]);
-              u32 old = atomicMax(p.claim + ((u64)o_gq * n + w), stamp);
-              take = old < stamp;
-            }
-          }
+          take = relax<NW>(p, FB, o_gq, w, ofm, stamp);
         }
         warp_append(take, ((u64)o_gq << 32) | w, &p.ctl->n_list[nxt], nlist);
       }
     }
   }
-  stat[ST_GROUP_EDGES] += warp_sum(edges);
-  stat[ST_GROUP_ROWS] += warp_sum(rows);
+  edges = warp_sum(edges);
+  rows = warp_sum(rows);
+  entries = warp_sum(entries);
+  stat[ST_GROUP_EDGES] += edges;
+  stat[ST_GROUP_ROWS] += rows;
+  // per relaxation a column id and the target's visited word (the spilled
+  // share is counted by the spill phase); per row its two offsets; per entry
+  // the list entry and its frontier word
+  stat[ST_ALG_BYTES] += edges * (4 + 8 * NW) + rows * 8 + entries * (8 + 8 * NW);
 }
 
-// Bottom-up expansion over every (group, vertex).
+// The queued chunks of long rows: a warp per chunk, taken dynamically.
 template <int NW>
-__device__ void pull_level(const BfsParams &p, int lp, u32 nxt, u64 *stat) {
+__device__ void spill_phase(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 stamp, u64 *stat) {
+  u64 *nlist = lp ? p.list0 : p.list1;
+  u64 *FB = lp ? p.fr0 : p.fr1;
+  const u32 lane = lane_id();
+  u64 count = *(volatile unsigned long long *)&p.ctl->spill_count[cur];
+  if (count > SPILL_CAP) count = SPILL_CAP;
+  u64 edges = 0;
+  for (;;) {
+    u64 r = 0;
+    if (lane == 0) r = atomicAdd(&p.ctl->spill_cursor[cur], 1ull);
+    r = __shfl_sync(FULL_MASK, r, 0);
+    if (r >= count) break;
+    const u64 *rec = p.spill + r * (2 + NW);
+    const u64 h = __ldcg(rec);
+    const u32 tgq = (u32)(h >> 32), b = (u32)h;
+    const u32 len = (u32)__ldcg(rec + 1);
+    Word<NW> fm;
+#pragma unroll
+    for (int t = 0; t < NW; t++) fm.w[t] = __ldcg(rec + 2 + t);
+    edges += (lane == 0) ? len : 0;
+    for (u32 k0 = 0; k0 < len; k0 += 32) {
+      u32 k = k0 + lane;
+      bool take = false;
+      u32 w = 0;
+      if (k < len) {
+        w = __ldg(p.out_col + b + k);
+        take = relax<NW>(p, FB, tgq, w, fm, stamp);
+      }
+      warp_append(take, ((u64)tgq << 32) | w, &p.ctl->n_list[nxt], nlist);
+    }
+  }
+  edges = warp_sum(edges);
+  stat[ST_GROUP_EDGES] += edges;
+  stat[ST_ALG_BYTES] += edges * (4 + 8 * NW);
+}
+
+// Bottom-up work for target (q2, w) over in-edges [beg, end) of one
+// transition group with active source states `from`: every lane ORs the
+// gathered frontier words of its PER words into acc.
+template <int NW, int PER>
+__device__ __forceinline__ void gather_row(const BfsParams &p, const u64 *F, u32 from, u32 beg, u32 end,
+                                           u32 lane_off, bool lane_on, u64 (&acc)[PER]) {
+  const u32 n = p.n;
+  const u64 wpv = (u64)p.G * NW;
+  u32 i = beg;
+  // four in-edges per step keep four gathers in flight
+  for (; i + 4 <= end; i += 4) {
+    u32 v0 = __ldg(p.in_col + i), v1 = __ldg(p.in_col + i + 1), v2 = __ldg(p.in_col + i + 2),
+        v3 = __ldg(p.in_col + i + 3);
+    if (!lane_on) continue;
+    for (u32 fb = from; fb; fb &= fb - 1) {
+      const u64 qb = (u64)(__ffs(fb) - 1) * n;
+      const u64 *f0 = F + (qb + v0) * wpv + lane_off, *f1 = F + (qb + v1) * wpv + lane_off;
+      const u64 *f2 = F + (qb + v2) * wpv + lane_off, *f3 = F + (qb + v3) * wpv + lane_off;
+      if constexpr (PER == 2) {
+        ulonglong2 a0 = __ldcg(reinterpret_cast<const ulonglong2 *>(f0));
+        ulonglong2 a1 = __ldcg(reinterpret_cast<const ulonglong2 *>(f1));
+        ulonglong2 a2 = __ldcg(reinterpret_cast<const ulonglong2 *>(f2));
+        ulonglong2 a3 = __ldcg(reinterpret_cast<const ulonglong2 *>(f3));
+        acc[0] |= a0.x | a1.x | a2.x | a3.x;
+        acc[1] |= a0.y | a1.y | a2.y | a3.y;
+      } else {
+        acc[0] |= __ldcg(f0) | __ldcg(f1) | __ldcg(f2) | __ldcg(f3);
+      }
+    }
+  }
+  for (; i < end; i++) {
+    u32 v = __ldg(p.in_col + i);
+    if (!lane_on) continue;
+    for (u32 fb = from; fb; fb &= fb - 1) {
+      const u64 *f = F + ((u64)(__ffs(fb) - 1) * n + v) * wpv + lane_off;
+#pragma unroll
+      for (int k = 0; k < PER; k++) acc[k] |= __ldcg(f + k);
+    }
+  }
+}
+
+// Bottom-up target (q2, w), all groups: new lanes = acc & ~VIS go to the next
+// frontier word (atomically: chunks of long rows of the same vertex may run
+// concurrently); one lane per group claims the list entry.
+template <int NW, int PER>
+__device__ __forceinline__ void pull_finish(const BfsParams &p, u64 *FB, u64 *nlist, u32 nxt, u32 q2, u32 w, u32 stamp,
+                                            u32 lane, bool lane_on, u32 my_g, const u64 (&vis)[PER],
+                                            const u64 (&acc)[PER]) {
+  const u64 base = ((u64)q2 * p.n + w) * p.G * NW + (u64)lane * PER;
+  bool take = false;
+  bool nz = false;
+  u64 nw[PER];
+#pragma unroll
+  for (int k = 0; k < PER; k++) {
+    nw[k] = lane_on ? (acc[k] & ~vis[k]) : 0;
+    nz |= nw[k] != 0;
+  }
+  if constexpr (NW == 1) {
+    if (nz) take = atomicOr((unsigned long long *)(FB + base), nw[0]) == 0;
+  } else {
+#pragma unroll
+    for (int k = 0; k < PER; k++)
+      if (nw[k]) atomicOr((unsigned long long *)(FB + base + k), nw[k]);
+    // NW / PER lanes hold one group's word
+    bool gnz = nz;
+#pragma unroll
+    for (int o = 1; o < NW / PER; o <<= 1) gnz |= __shfl_xor_sync(FULL_MASK, gnz, o);
+    if (gnz && lane_on && (lane % (NW / PER)) == 0)
+      take = atomicMax(p.claim + (((u64)q2 * p.n + w) * p.G + my_g), stamp) < stamp;
+  }
+  warp_append(take, ((u64)(my_g * p.Q + q2) << 32) | w, &p.ctl->n_list[nxt], nlist);
+}
+
+// Bottom-up expansion.  Light rows: a warp per vertex, all groups at once
+// (lane L holds words [L*PER, L*PER+PER) of the vertex's G*NW words).  Long
+// rows: their precomputed chunks, a warp per chunk, taken dynamically over
+// the (target state, transition group) pairs whose source states are active.
+template <int NW>
+__device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 active, u32 stamp, u64 *stat) {
+  constexpr int PER = (NW >= 2) ? 2 : 1;
   const u64 *F = lp ? p.fr1 : p.fr0;
   u64 *FB = lp ? p.fr0 : p.fr1;
   u64 *nlist = lp ? p.list0 : p.list1;
   const u32 n = p.n, Q = p.Q, n1 = p.n + 1;
-  const u64 total = (u64)p.G * n;
-  const u64 stride = (u64)gridDim.x * blockDim.x;
-  u64 edges = 0, words = 0;
-  for (u64 base = (u64)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
-    u64 item = base + lane_id();
-    bool valid = item < total;
-    u32 g = valid ? (u32)(item / n) : 0;
-    u32 w = valid ? (u32)(item - (u64)g * n) : 0;
-    // high in-degree vertices are left to the warp-per-vertex loop below
-    if (valid && p.heavy_bits && (__ldg(p.heavy_bits + (w >> 5)) >> (w & 31) & 1u)) valid = false;
+  const u32 lane = lane_id();
+  const u32 lanes_used = p.G * NW / PER;
+  const bool lane_on = lane < lanes_used;
+  const u32 lane_off = lane * PER;
+  const u32 my_g = lane_on ? lane_off / NW : 0;
+  const u64 wpv = (u64)p.G * NW;
+  const u64 warp = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const u64 n_warps = ((u64)gridDim.x * blockDim.x) >> 5;
+  const bool chunked = p.hchunk != nullptr;
+  const u64 gword = 8ull * NW * p.G;  // bytes of the G words of one (state, vertex)
+  u64 edges = 0, words = 0, bytes = 0;
+
+  for (u64 w64 = warp; w64 < n; w64 += n_warps) {
+    const u32 w = (u32)w64;
     for (u32 q2 = 0; q2 < Q; q2++) {
-      u32 gb = p.q.in_begin[q2], ge = p.q.in_begin[q2 + 1];
-      if (gb == ge) continue;
-      bool take = false;
-      u64 gq2 = (u64)g * Q + q2;
-      bool has_in = false;  // skip vertices with no in-edge on these labels
-      if (valid)
-        for (u32 j = gb; j < ge && !has_in; j++) {
-          u32 l = p.q.in_label[j];
-          if (l >= p.L) continue;
-          const u32 *off = p.in_off + (u64)l * n1 + w;
-          has_in = __ldg(off) != __ldg(off + 1);
-        }
-      if (has_in) {
-        u64 wi = (gq2 * n + w) * NW;
-        Word<NW> vis = load_cg<NW>(p.vis + wi);
-        if (!all_bits(vis)) {
-          words++;
-          Word<NW> acc;
-#pragma unroll
-          for (int i = 0; i < NW; i++) acc.w[i] = 0;
-          bool full = false;
-          for (u32 j = gb; j < ge && !full; j++) {
-            u32 l = p.q.in_label[j];
-            if (l >= p.L) continue;
-            u32 from = p.q.in_from[j];
-            const u32 *off = p.in_off + (u64)l * n1 + w;
-            u32 beg = __ldg(off), end = __ldg(off + 1);
-            for (u32 i = beg; i < end; i++) {
-              u32 v = __ldg(p.in_col + i);
-              edges++;
-              for (u32 fb = from; fb; fb &= fb - 1) {
-                u32 q = __ffs(fb) - 1;
-                Word<NW> f = load_cg<NW>(F + (((u64)g * Q + q) * n + v) * NW);
-#pragma unroll
-                for (int t = 0; t < NW; t++) acc.w[t] |= f.w[t];
-              }
-              Word<NW> cover;
-#pragma unroll
-              for (int t = 0; t < NW; t++) cover.w[t] = acc.w[t] | vis.w[t];
-              if (all_bits(cover)) {
-                full = true;
-                break;
-              }
-            }
-          }
-          Word<NW> nw;
-#pragma unroll
-          for (int t = 0; t < NW; t++) nw.w[t] = acc.w[t] & ~vis.w[t];
-          if (any_bits(nw)) {
-            Word<NW> nv;
-#pragma unroll
-            for (int t = 0; t < NW; t++) nv.w[t] = vis.w[t] | nw.w[t];
-            store_w<NW>(p.vis + wi, nv);
-            store_w<NW>(FB + wi, nw);
-            take = true;
-          }
-        }
+      const u32 gb = p.q.in_begin[q2], ge = p.q.in_begin[q2 + 1];
+      bool any = false;
+      for (u32 j = gb; j < ge && !any; j++) {
+        const u32 l = p.q.in_label[j];
+        if (!(p.q.in_from[j] & active) || l >= p.L) continue;
+        const u32 *off = p.in_off + (u64)l * n1 + w;
+        const u32 len = __ldg(off + 1) - __ldg(off);
+        any = len > 0 && (len < HEAVY_ROW || !chunked);
       }
-      warp_append(take, (gq2 << 32) | w, &p.ctl->n_list[nxt], nlist);
+      if (!any) continue;
+      const u64 base = ((u64)q2 * n + w) * wpv + lane_off;
+      u64 vis[PER];
+      bool full = true;
+#pragma unroll
+      for (int k = 0; k < PER; k++) {
+        vis[k] = lane_on ? __ldcg(p.vis + base + k) : ~0ull;
+        full &= vis[k] == ~0ull;
+      }
+      if (__all_sync(FULL_MASK, full)) continue;
+      u64 acc[PER];
+#pragma unroll
+      for (int k = 0; k < PER; k++) acc[k] = 0;
+      for (u32 j = gb; j < ge; j++) {
+        const u32 l = p.q.in_label[j];
+        const u32 from = p.q.in_from[j] & active;
+        if (!from || l >= p.L) continue;
+        const u32 *off = p.in_off + (u64)l * n1 + w;
+        const u32 beg = __ldg(off), end = __ldg(off + 1);
+        if (end - beg >= HEAVY_ROW && chunked) continue;
+        edges += (lane == 0) ? (end - beg) : 0;
+        bytes += (lane == 0) ? 8 + (u64)(end - beg) * (4 + gword * __popc(from)) : 0;
+        gather_row<NW, PER>(p, F, from, beg, end, lane_off, lane_on, acc);
+      }
+      words += (lane == 0);
+      bytes += (lane == 0) ? gword : 0;
+      pull_finish<NW, PER>(p, FB, nlist, nxt, q2, w, stamp, lane, lane_on, my_g, vis, acc);
     }
   }
-  // High in-degree vertices: a warp per (group, vertex); lanes stride over
-  // the in-edges and the partial words are OR-reduced across the warp.
-  const u64 n_hv = (u64)p.G * p.n_heavy;
-  const u32 lane = lane_id();
-  for (u64 it = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n_hv; it += stride >> 5) {
-    const u32 g = (u32)(it / p.n_heavy);
-    const u32 w = __ldg(p.heavy_list + (it - (u64)g * p.n_heavy));
-    for (u32 q2 = 0; q2 < Q; q2++) {
-      u32 gb = p.q.in_begin[q2], ge = p.q.in_begin[q2 + 1];
-      if (gb == ge) continue;
-      const u64 gq2 = (u64)g * Q + q2;
-      const u64 wi = (gq2 * n + w) * NW;
-      Word<NW> vis = load_cg<NW>(p.vis + wi);
-      if (all_bits(vis)) continue;
-      Word<NW> acc;
-#pragma unroll
-      for (int t = 0; t < NW; t++) acc.w[t] = 0;
-      for (u32 j = gb; j < ge; j++) {
-        u32 l = p.q.in_label[j];
-        if (l >= p.L) continue;
-        u32 from = p.q.in_from[j];
-        const u32 *off = p.in_off + (u64)l * n1 + w;
-        u32 beg = __ldg(off), end = __ldg(off + 1);
-        for (u32 i = beg + lane; i < end; i += 32) {
-          u32 v = __ldg(p.in_col + i);
-          edges++;
-          for (u32 fb = from; fb; fb &= fb - 1) {
-            u32 q = __ffs(fb) - 1;
-            Word<NW> f = load_cg<NW>(F + (((u64)g * Q + q) * n + v) * NW);
-#pragma unroll
-            for (int t = 0; t < NW; t++) acc.w[t] |= f.w[t];
+
+  if (chunked) {
+    for (;;) {
+      u64 it = 0;
+      if (lane == 0) it = atomicAdd(&p.ctl->heavy_cursor[cur], 1ull);
+      it = __shfl_sync(FULL_MASK, it, 0);
+      // map the item number to (target state, transition group, chunk)
+      u64 acc_base = 0, ci = 0;
+      u32 q2s = 0, from = 0;
+      bool found = false;
+      for (u32 q2 = 0; q2 < Q && !found; q2++)
+        for (u32 j = p.q.in_begin[q2]; j < p.q.in_begin[q2 + 1]; j++) {
+          const u32 l = p.q.in_label[j];
+          if (!(p.q.in_from[j] & active) || l >= p.L) continue;
+          const u64 cnt = p.hchunk_off[l + 1] - p.hchunk_off[l];
+          if (it < acc_base + cnt) {
+            found = true;
+            q2s = q2;
+            from = p.q.in_from[j] & active;
+            ci = p.hchunk_off[l] + (it - acc_base);
+            break;
           }
+          acc_base += cnt;
         }
+      if (!found) break;
+      const u32 *rec = p.hchunk + 3 * ci;
+      const u32 w = __ldg(rec), beg = __ldg(rec + 1), end = __ldg(rec + 2);
+      const u64 base = ((u64)q2s * n + w) * wpv + lane_off;
+      u64 vis[PER];
+      bool full = true;
+#pragma unroll
+      for (int k = 0; k < PER; k++) {
+        vis[k] = lane_on ? __ldcg(p.vis + base + k) : ~0ull;
+        full &= vis[k] == ~0ull;
       }
+      if (__all_sync(FULL_MASK, full)) continue;
+      u64 acc[PER];
 #pragma unroll
-      for (int t = 0; t < NW; t++)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc.w[t] |= __shfl_xor_sync(FULL_MASK, acc.w[t], o);
-      Word<NW> nw;
-#pragma unroll
-      for (int t = 0; t < NW; t++) nw.w[t] = acc.w[t] & ~vis.w[t];
-      bool take = false;
-      if (lane == 0) {
-        words++;
-        if (any_bits(nw)) {
-          Word<NW> nv;
-#pragma unroll
-          for (int t = 0; t < NW; t++) nv.w[t] = vis.w[t] | nw.w[t];
-          store_w<NW>(p.vis + wi, nv);
-          store_w<NW>(FB + wi, nw);
-          take = true;
-        }
-      }
-      warp_append(take, (gq2 << 32) | w, &p.ctl->n_list[nxt], nlist);
+      for (int k = 0; k < PER; k++) acc[k] = 0;
+      edges += (lane == 0) ? (end - beg) : 0;
+      bytes += (lane == 0) ? 12 + gword + (u64)(end - beg) * (4 + gword * __popc(from)) : 0;
+      gather_row<NW, PER>(p, F, from, beg, end, lane_off, lane_on, acc);
+      words += (lane == 0);
+      pull_finish<NW, PER>(p, FB, nlist, nxt, q2s, w, stamp, lane, lane_on, my_g, vis, acc);
     }
   }
   stat[ST_PULL_EDGES] += warp_sum(edges);
   stat[ST_PULL_VERTICES] += warp_sum(words);
+  stat[ST_ALG_BYTES] += warp_sum(bytes);
 }
 
-// Commit of a level: fold the new frontier into VIS (top-down levels), count
-// work, clear the old frontier words.
+// Commit of a level: fold the new frontier words into VIS, count work, note
+// the DFA states present in the new frontier, clear the old frontier words.
 template <int NW>
-__device__ void commit_phase(const BfsParams &p, int lp, u32 nxt, u64 n_cur, bool was_push, u64 *stat) {
+__device__ void commit_phase(const BfsParams &p, int lp, u32 nxt, u64 n_cur, u64 *stat) {
   const u64 *list = lp ? p.list1 : p.list0;
   const u64 *nlist = lp ? p.list0 : p.list1;
   u64 *F = lp ? p.fr1 : p.fr0;
   const u64 *FB = lp ? p.fr0 : p.fr1;
-  const u32 n = p.n, Q = p.Q;
+  const u32 Q = p.Q;
   const u64 n_next = *(volatile unsigned long long *)&p.ctl->n_list[nxt];
   const u64 stride = (u64)gridDim.x * blockDim.x;
   const u64 tid = (u64)blockIdx.x * blockDim.x + threadIdx.x;
   u64 W = 0, N = 0, mf = 0, gv = 0;
+  u32 states = 0;
   for (u64 j = tid; j < n_next; j += stride) {
     u64 e = __ldcg(&nlist[j]);
     u32 gq = (u32)(e >> 32), w = (u32)e;
-    u32 q = gq % Q;
-    u64 wi = ((u64)gq * n + w) * NW;
+    u32 g = gq / Q, q = gq - g * Q;
+    u64 wi = widx<NW>(p, g, q, w);
     Word<NW> m = load_cg<NW>(FB + wi);
-    if (was_push) {
-      Word<NW> v = load_cg<NW>(p.vis + wi);
+    Word<NW> v = load_cg<NW>(p.vis + wi);
 #pragma unroll
-      for (int t = 0; t < NW; t++) v.w[t] |= m.w[t];
-      store_w<NW>(p.vis + wi, v);
-    }
+    for (int t = 0; t < NW; t++) v.w[t] |= m.w[t];
+    store_w<NW>(p.vis + wi, v);
     u32 c = popc_w(m);
     u32 d = degsum(p, q, w);
     W += (u64)c * d;
     N += c;
     mf += d;
     gv += 1;
+    states |= 1u << q;
   }
   Word<NW> zero;
 #pragma unroll
   for (int t = 0; t < NW; t++) zero.w[t] = 0;
   for (u64 j = tid; j < n_cur; j += stride) {
     u64 e = __ldcg(&list[j]);
-    u64 wi = ((u64)(u32)(e >> 32) * n + (u32)e) * NW;
-    store_w<NW>(F + wi, zero);
+    u32 gq = (u32)(e >> 32);
+    u32 g = gq / Q;
+    store_w<NW>(F + widx<NW>(p, g, gq - g * Q, (u32)e), zero);
   }
+  if (tid == 0) stat[ST_ALG_BYTES] += n_cur * (8 + 8 * NW);
   W = warp_sum(W);
   N = warp_sum(N);
   mf = warp_sum(mf);
   gv = warp_sum(gv);
+  states = __reduce_or_sync(FULL_MASK, states);
+  // per new entry: the entry, its new frontier word, its visited word read and
+  // written; per old entry: the entry and its frontier word cleared
+  if (lane_id() == 0) stat[ST_ALG_BYTES] += gv * (8 + 24 * NW);
   if (lane_id() == 0) {
     stat[ST_W] += W;
     stat[ST_N] += N;
     stat[ST_GROUP_VERTICES] += gv;
     if (mf) atomicAdd(&p.ctl->mf[nxt], mf);
+    if (states) atomicOr(&p.ctl->smask[nxt], states);
   }
+}
+
+// Bytes a bottom-up level moves when the frontier holds the states `active`:
+// per target state with an active incoming transition, its visited words;
+// per such transition group, the row offsets and per in-edge a column id
+// and the gathered frontier words.
+template <int NW>
+__device__ double pull_bytes(const BfsParams &p, u32 active) {
+  double b = 0;
+  const double wv = 8.0 * NW * p.G;
+  for (u32 q2 = 0; q2 < p.Q; q2++) {
+    bool any = false;
+    for (u32 j = p.q.in_begin[q2]; j < p.q.in_begin[q2 + 1]; j++) {
+      const u32 f = p.q.in_from[j] & active, l = p.q.in_label[j];
+      if (!f || l >= p.L) continue;
+      any = true;
+      b += 8.0 * p.n + (double)p.label_edges[l] * (4.0 + wv * __popc(f));
+    }
+    if (any) b += wv * p.n;
+  }
+  return b;
 }
 
 template <int NW>
@@ -479,6 +633,7 @@ __global__ void __launch_bounds__(BFS_THREADS) msbfs_kernel(const __grid_constan
 #pragma unroll
   for (int i = 0; i < ST_COUNT; i++) stat[i] = 0;
   BfsCtl *c = p.ctl;
+  const bool tracer = blockIdx.x == 0 && threadIdx.x == 0;
 
   seed_phase<NW>(p, stat);
   if (!grid_barrier(c, p.nblocks, p.time_limit_ns)) return;
@@ -490,21 +645,42 @@ __global__ void __launch_bounds__(BFS_THREADS) msbfs_kernel(const __grid_constan
     const u64 n_cur = *(volatile unsigned long long *)&c->n_list[cur];
     if (n_cur == 0) break;
     const u64 mf = *(volatile unsigned long long *)&c->mf[cur];
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const u32 active = *(volatile unsigned *)&c->smask[cur];
+    const double push_cost = (double)mf * (4.0 + 8.0 * NW) + (double)n_cur * (16.0 + 8.0 * NW);
+    const bool push = p.force == 1 || (p.force != 2 && (double)p.alpha * push_cost < pull_bytes<NW>(p, active));
+    if (tracer) {
+      // counters of the level after next start at zero
       c->n_list[old] = 0;
       c->cursor[old] = 0;
       c->mf[old] = 0;
+      c->spill_count[old] = 0;
+      c->spill_cursor[old] = 0;
+      c->heavy_cursor[old] = 0;
+      c->smask[old] = 0;
+      if (level < (u32)TRACE_LEVELS) {
+        c->trace_t[level] = globaltimer_ns();
+        c->trace_n[level] = n_cur;
+        c->trace_mode[level] = push ? 1u : 2u;
+        c->trace_mf[level] = mf;
+      }
+      if (push)
+        stat[ST_PUSH_LEVELS] += 1;
+      else
+        stat[ST_PULL_LEVELS] += 1;
     }
-    const double push_cost = (double)mf * (4.0 + 8.0 * NW) + (double)n_cur * (16.0 + 8.0 * NW);
-    const bool push = p.force == 1 || (p.force != 2 && (double)p.alpha * push_cost < p.pull_cost_fixed);
+    const u32 stamp = p.stamp_base + level + 1;
     if (push) {
-      push_level<NW>(p, lp, cur, nxt, n_cur, p.stamp_base + level + 1, stat);
+      push_level<NW>(p, lp, cur, nxt, n_cur, stamp, stat);
+      if (!grid_barrier(c, p.nblocks, p.time_limit_ns)) return;
+      if (*(volatile unsigned long long *)&c->spill_count[cur] != 0) {
+        spill_phase<NW>(p, lp, cur, nxt, stamp, stat);
+        if (!grid_barrier(c, p.nblocks, p.time_limit_ns)) return;
+      }
     } else {
-      pull_level<NW>(p, lp, nxt, stat);
+      pull_level<NW>(p, lp, cur, nxt, active, stamp, stat);
+      if (!grid_barrier(c, p.nblocks, p.time_limit_ns)) return;
     }
-    if (threadIdx.x == 0 && blockIdx.x == 0) stat[push ? ST_PUSH_LEVELS : ST_PULL_LEVELS] += 1;
-    if (!grid_barrier(c, p.nblocks, p.time_limit_ns)) return;
-    commit_phase<NW>(p, lp, nxt, n_cur, push, stat);
+    commit_phase<NW>(p, lp, nxt, n_cur, stat);
     if (!grid_barrier(c, p.nblocks, p.time_limit_ns)) return;
   }
   if (lane_id() == 0) {
@@ -512,31 +688,31 @@ __global__ void __launch_bounds__(BFS_THREADS) msbfs_kernel(const __grid_constan
     for (int i = 0; i < ST_COUNT; i++)
       if (stat[i]) atomicAdd(&c->stats[i], stat[i]);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) c->levels = level;
+  if (tracer) {
+    c->levels = level;
+    c->trace_t[level < (u32)TRACE_LEVELS ? level : TRACE_LEVELS] = globaltimer_ns();
+  }
 }
 
 // VIS words start as the mask of empty lanes of their group, so empty lanes
 // look visited everywhere (this also lets bottom-up levels stop early).
 template <int NW>
-__global__ void vis_init_kernel(u64 *__restrict__ vis, u64 words_per_group, u32 G,
-                                const u64 *__restrict__ empty) {
-  u64 total = words_per_group * G;
+__global__ void vis_init_kernel(u64 *__restrict__ vis, u64 total, u32 G, const u64 *__restrict__ empty) {
   for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (u64)gridDim.x * blockDim.x) {
-    u32 g = (u32)(i / words_per_group);
+    u32 g = (u32)((i / NW) % G);
     vis[i] = empty[(u64)g * NW + (i % NW)];
   }
 }
 
 cudaError_t launch_vis_init(int nw, const BfsParams &p, const unsigned long long *empty, cudaStream_t st) {
-  u64 wpg = (u64)p.Q * p.n * nw;
-  u64 total = wpg * p.G;
+  u64 total = (u64)p.Q * p.n * p.G * nw;
   u64 blocks = (total + 255) / 256;
   if (blocks > 152ull * 32) blocks = 152ull * 32;
   if (blocks == 0) blocks = 1;
   if (nw == 1)
-    vis_init_kernel<1><<<(unsigned)blocks, 256, 0, st>>>(p.vis, wpg, p.G, empty);
+    vis_init_kernel<1><<<(unsigned)blocks, 256, 0, st>>>(p.vis, total, p.G, empty);
   else
-    vis_init_kernel<4><<<(unsigned)blocks, 256, 0, st>>>(p.vis, wpg, p.G, empty);
+    vis_init_kernel<4><<<(unsigned)blocks, 256, 0, st>>>(p.vis, total, p.G, empty);
   return cudaGetLastError();
 }
 

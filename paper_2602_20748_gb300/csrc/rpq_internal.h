@@ -50,7 +50,11 @@ int compile_regex(const char *regex, const char *const *names, uint32_t n_names,
 // out-edges (sorted by label, src, dst) and in-edges (label, dst, src).
 // off[l * (n + 1) + v] is the first edge of row v of label l.
 // ---------------------------------------------------------------------------
-constexpr uint32_t HEAVY_DEGREE = 128;
+// In-edge rows with at least HEAVY_ROW edges are cut into chunks of HCHUNK
+// edges at graph load; bottom-up levels share the chunks among all warps
+// instead of scanning such a row with one warp.
+constexpr uint32_t HEAVY_ROW = 128;
+constexpr uint32_t HCHUNK = 256;
 
 struct DevGraph {
   uint32_t n = 0;
@@ -61,12 +65,11 @@ struct DevGraph {
   uint32_t *in_off = nullptr;
   uint32_t *in_col = nullptr;
   uint8_t *vlabel = nullptr;
-  // High-degree vertices (total degree over all labels >= HEAVY_DEGREE), per
-  // direction: a bit per vertex and the sorted list.  Bottom-up levels give
-  // each of them a whole warp instead of one thread.
-  uint32_t *heavy_in_bits = nullptr, *heavy_in_list = nullptr;
-  uint32_t *heavy_out_bits = nullptr, *heavy_out_list = nullptr;
-  uint32_t n_heavy_in = 0, n_heavy_out = 0;
+  // Chunks (vertex, first edge, end edge) of the rows with >= HEAVY_ROW
+  // edges, per direction, grouped by label: label l's chunks are
+  // [off[l], off[l+1]) (host copy of the L+1 offsets).
+  uint32_t *hchunk_in = nullptr, *hchunk_out = nullptr;
+  std::vector<uint32_t> hchunk_in_off, hchunk_out_off;
   std::vector<uint8_t> vlabel_host;   // vertex labels (host copy), empty if none
   std::vector<uint64_t> label_edges;  // edges per label (host copy)
 };
@@ -84,8 +87,11 @@ enum StatIdx {
   ST_GROUP_VERTICES, // lane-group product vertices discovered
   ST_PULL_EDGES,     // in-edges read by bottom-up levels
   ST_PULL_VERTICES,  // (vertex, state) words examined bottom-up
+  ST_ALG_BYTES,      // algorithmic bytes of the traversal (see the kernel)
   ST_COUNT
 };
+
+constexpr int TRACE_LEVELS = 64;
 
 struct BfsCtl {
   unsigned int bar_count;
@@ -95,9 +101,24 @@ struct BfsCtl {
   unsigned long long n_list[3];
   unsigned long long cursor[3];
   unsigned long long mf[3];
+  unsigned long long spill_count[3];   // top-down row chunks queued this level
+  unsigned long long spill_cursor[3];
+  unsigned long long heavy_cursor[3];  // bottom-up row chunks taken
+  unsigned int smask[3];               // DFA states present in each frontier
   unsigned long long levels;
   unsigned long long stats[ST_COUNT];
+  // per-level trace (first TRACE_LEVELS levels): start time (ns), frontier
+  // entries, direction (1 top-down, 2 bottom-up)
+  unsigned long long trace_t[TRACE_LEVELS + 1];
+  unsigned long long trace_n[TRACE_LEVELS];
+  unsigned int trace_mode[TRACE_LEVELS];
+  unsigned long long trace_mf[TRACE_LEVELS];  // frontier out-edges (top-down cost)
 };
+
+// A top-down row longer than SPILL_EDGES is cut into chunks of SPILL_EDGES
+// edges that all warps share in a sub-phase of the level.
+constexpr unsigned int SPILL_EDGES = 1024;
+constexpr unsigned long long SPILL_CAP = 1ull << 18;  // chunks per level
 
 struct BfsParams {
   // graph
@@ -105,9 +126,9 @@ struct BfsParams {
   const uint32_t *out_col;
   const uint32_t *in_off;
   const uint32_t *in_col;
-  const uint32_t *heavy_bits;  // high in-degree vertices (for in_off / in_col)
-  const uint32_t *heavy_list;
-  uint32_t n_heavy;
+  const uint32_t *hchunk;       // chunks of long in_off rows (nullptr: none)
+  uint32_t hchunk_off[RPQ_MAX_LABELS + 1];
+  unsigned long long label_edges[RPQ_MAX_LABELS];
   uint32_t n;
   uint32_t L;             // edge labels of the graph
   // lane groups
@@ -115,10 +136,11 @@ struct BfsParams {
   uint32_t Q;             // DFA states
   const uint32_t *lanesrc;  // [G * 64 * NW], 0xFFFFFFFF = empty lane
   // workspace
-  unsigned long long *vis;     // [G][Q][n][NW]
+  unsigned long long *vis;     // [Q][n][G][NW]: groups innermost
   unsigned long long *fr0;     // frontier ping
   unsigned long long *fr1;     // frontier pong
-  unsigned int *claim;         // [G][Q][n] (NW > 1)
+  unsigned int *claim;         // [Q][n][G] level stamps (NW > 1)
+  unsigned long long *spill;   // SPILL_CAP chunk records (nullptr: no spilling)
   unsigned long long *list0;   // entries ((g*Q+q) << 32 | v)
   unsigned long long *list1;
   BfsCtl *ctl;
@@ -126,7 +148,6 @@ struct BfsParams {
   unsigned int nblocks;
   int force;                   // 0 auto, 1 push only, 2 pull only
   float alpha;                 // push if alpha * push_cost < pull_cost
-  double pull_cost_fixed;      // bottom-up bytes per level (all groups)
   unsigned long long time_limit_ns;
   QueryDesc q;
 };

@@ -169,17 +169,8 @@ extern "C" int run_rpq_static(rpq_ctx *ctx, const rpq_graph *g, const rpq_query 
   p.nblocks = (unsigned)blocks;
   p.force = 0;
   p.alpha = ctx_alpha(ctx);
-  double pull_fixed = 0;
-  for (uint32_t q2 = 0; q2 < Q; q2++) {
-    if (qd.in_begin[q2] == qd.in_begin[q2 + 1]) continue;
-    pull_fixed += (double)n * 8.0;
-    for (uint32_t j = qd.in_begin[q2]; j < qd.in_begin[q2 + 1]; j++) {
-      uint32_t l = qd.in_label[j];
-      double el = l < dg.L ? (double)dg.label_edges[l] : 0.0;
-      pull_fixed += (double)n * 8.0 + el * (4.0 + 8.0 * __builtin_popcount(qd.in_from[j]));
-    }
-  }
-  p.pull_cost_fixed = pull_fixed;
+  p.hchunk = nullptr;  // long rows are scanned in place
+  for (uint32_t l = 0; l < dg.L; l++) p.label_edges[l] = dg.label_edges[l];
   p.time_limit_ns = ctx_time_limit_ns(ctx);
   p.q = qd;
   STATIC_CK(launch_vis_init(1, p, empty, st));

@@ -63,7 +63,7 @@ class rpq_stats(ctypes.Structure):
         "product_edges", "product_vertices", "levels", "push_levels", "pull_levels", "group_edges", "group_rows",
         "group_vertices", "pull_edges", "pull_vertices", "lane_words", "lane_groups")] + [
         ("bfs_ms", ctypes.c_double), ("emit_ms", ctypes.c_double), ("bfs_launches", ctypes.c_uint64),
-        ("launches", ctypes.c_uint64)]
+        ("launches", ctypes.c_uint64), ("alg_bytes", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -278,3 +278,34 @@ def run_rpq_static(ctx: Context, g: Graph, q: Query, sources, out_pairs_ptr: int
     n = c_u64()
     ctx.check(_lib.run_rpq_static(ctx.h, g.h, q.h, _ptr(s), len(s), out_pairs_ptr, max_rows, ctypes.byref(n)))
     return n.value
+
+
+_lib.run_rpq_batch.argtypes = [c_void_p, c_void_p, c_u32, c_void_p, c_void_p, c_u32, P(c_void_p)]
+_lib.rpq_autotune_batch.argtypes = [c_void_p, c_void_p, c_u32, c_void_p, c_void_p, P(c_u32), P(c_u32)]
+EXPORTED += ["run_rpq_batch", "rpq_autotune_batch"]
+
+
+def _query_array(queries):
+    return (c_void_p * max(1, len(queries)))(*[q.h.value if isinstance(q.h, c_void_p) else q.h for q in queries])
+
+
+def run_rpq_batch(ctx: Context, g: Graph, queries, sources, flags: int = RPQ_MATERIALIZE) -> Result:
+    """run_rpq_batch: queries[i] (Query) from sources[i]; rows (i, y)."""
+    s = np.ascontiguousarray(sources, dtype=np.uint32)
+    if len(s) != len(queries):
+        raise ValueError("one source per query")
+    arr = _query_array(queries)
+    h = c_void_p()
+    ctx.check(_lib.run_rpq_batch(ctx.h, g.h, len(queries), ctypes.cast(arr, c_void_p), _ptr(s), flags,
+                                 ctypes.byref(h)))
+    return Result(ctx, h)
+
+
+def rpq_autotune_batch(ctx: Context, g: Graph, queries, sources):
+    """Returns the (threads, queries_per_launch) the autotuner kept."""
+    s = np.ascontiguousarray(sources, dtype=np.uint32)
+    arr = _query_array(queries)
+    t, k = c_u32(), c_u32()
+    ctx.check(_lib.rpq_autotune_batch(ctx.h, g.h, len(queries), ctypes.cast(arr, c_void_p), _ptr(s),
+                                      ctypes.byref(t), ctypes.byref(k)))
+    return t.value, k.value

@@ -202,3 +202,35 @@ def random_regex(seed: int, n_labels: int, max_symbols: int = 5, p_star: float =
     elif len(parts) > 1 and r < 0.22:
         text = f"({text})+"
     return text
+
+
+def batch_queries(n_queries: int, n_labels: int, zipf_s: float, src: np.ndarray, n_vertices: int, seed: int):
+    """Single-source query mix: each regex has 1..6 symbols, each a label drawn
+    Zipf(zipf_s); Kleene stars on k in {0, 1, 2} (uniform) distinct symbols; with
+    probability 1/4 two adjacent symbols are grouped as an alternation.  Start
+    vertices are drawn with probability proportional to out-degree (with
+    replacement).  Returns (list of regex strings, uint32 sources)."""
+    st = _Stream(seed)
+    cdf = np.cumsum(zipf_probs(n_labels, zipf_s))
+    cdf[-1] = 1.0
+    regexes = []
+    for _ in range(n_queries):
+        k = 1 + int(st.below(1, 6)[0])
+        syms = [chr(ord("a") + min(int(np.searchsorted(cdf, st.unit(1)[0], side="right")), n_labels - 1))
+                for _ in range(k)]
+        n_star = min(k, int(st.below(1, 3)[0]))
+        starred = set()
+        while len(starred) < n_star:
+            starred.add(int(st.below(1, k)[0]))
+        parts = [s + ("*" if i in starred else "") for i, s in enumerate(syms)]
+        if k >= 2 and st.unit(1)[0] < 0.25:
+            i = int(st.below(1, k - 1)[0])
+            a, b = syms[i], syms[i + 1]
+            star = "*" if (i in starred or i + 1 in starred) else ""
+            parts = parts[:i] + [f"({a}|{b}){star}"] + parts[i + 2:]
+        regexes.append(".".join(parts))
+    deg = np.bincount(np.asarray(src, dtype=np.int64), minlength=n_vertices).astype(np.float64)
+    cum = np.cumsum(deg)
+    u = st.unit(n_queries) * cum[-1]
+    sources = np.minimum(np.searchsorted(cum, u, side="right"), n_vertices - 1).astype(np.uint32)
+    return regexes, sources
