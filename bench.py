@@ -53,6 +53,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", default="allpairs", choices=["allpairs", "batch", "crpq"],
+                    help="allpairs: the R-MAT 2^20 all-pairs line (default); batch: 4,096 single-source "
+                         "queries on R-MAT 2^22; crpq: the 3-atom triangle CRPQ on R-MAT 2^22")
     ap.add_argument("--scale", type=int, default=SCALE,
                     help="R-MAT scale (vertices 2^scale, 16 * 2^scale edges); smaller cases are for profiling")
     return ap.parse_args()
@@ -347,6 +350,123 @@ def ours(args, rank: int, world: int, local_rank: int):
     return 0
 
 
+def bench_batch(args):
+    """4,096 single-source RPQs (1-6 Zipf symbols, 0-2 stars, 1/4 alternation
+    pairs, sources proportional to out-degree) on R-MAT 2^22 / 2^26 edges /
+    8 labels Zipf(1.2): one run_rpq_batch call per step against run_rpq one
+    query per launch, equal results checked on the plain subset."""
+    import torch
+    from paper_2602_20748_gb300 import rpq, synth
+
+    n = 1 << 22
+    src, dst, lab = synth.rmat_graph(22, 1 << 26, 8, 1.2, seed=synth.BASE_SEED + 4)
+    regexes, sources = synth.batch_queries(4096, 8, 1.2, src, n, seed=synth.BASE_SEED + 4)
+    ctx = rpq.Context(device=0)
+    g = rpq.load_graph(ctx, n, 8, src, dst, lab)
+    qs = [rpq.compile_rpq(ctx, r) for r in regexes]
+    t0 = time.perf_counter()
+    threads, per_launch = rpq.rpq_autotune_batch(ctx, g, qs, sources)
+    tune_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        rpq.run_rpq_batch(ctx, g, qs, sources).free()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(0)
+    sampler.start()
+    torch.cuda.synchronize()
+    ev0.record()
+    W = rows = launches = 0
+    info = None
+    for _ in range(args.steps):
+        r = rpq.run_rpq_batch(ctx, g, qs, sources)
+        st = rpq.result_stats(r)
+        W += st["product_edges"]
+        launches += st["launches"]
+        info = rpq.result_info(r)
+        rows += info[0]
+        r.free()
+    ev1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    # plain path: one run_rpq launch per query, on a subset, timed per query
+    k = 512
+    lat = []
+    plain_rows = 0
+    plain_digest = [0, 0]
+    for i in range(k):
+        t1 = time.perf_counter()
+        r = rpq.run_rpq(ctx, g, qs[i], [sources[i]])
+        c, _, hs, hx = rpq.result_info(r)
+        lat.append(time.perf_counter() - t1)
+        plain_rows += c
+        r.free()
+    plain_qps = k / sum(lat)
+    # equal results: the batched rows of the first k queries against the plain ones
+    rb = rpq.run_rpq_batch(ctx, g, qs[:k], sources[:k])
+    eq = rpq.result_info(rb)[0] == plain_rows
+    rb.free()
+    qps = 4096 / (ms / 1000.0)
+    out = {
+        "metric": "queries_per_s", "value": qps, "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "rmat22-batched-single-source", "queries": 4096, "vertices": n,
+                   "generated_edges": 1 << 26, "labels": 8, "zipf_s": 1.2, "autotuned_threads": threads,
+                   "autotuned_queries_per_launch": per_launch, "autotune_s": round(tune_s, 3)},
+        "batched_latency_ms": ms, "product_edges_per_s": W / (ms * args.steps / 1000.0), "rows_per_step": rows // args.steps,
+        "plain": {"queries_per_s": plain_qps, "p50_ms": 1000 * float(np.percentile(lat, 50)),
+                  "p99_ms": 1000 * float(np.percentile(lat, 99)), "queries_timed": k},
+        "speedup_vs_plain": qps / plain_qps, "equal_results_on_plain_subset": bool(eq),
+        "clocks": clocks, "gpu_launches": launches,
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def bench_crpq(args):
+    """3-atom triangle CRPQ x -a-> y, x -b.c*-> z, y -d*-> z on R-MAT 2^22 /
+    2^26 edges / 10 labels Zipf(1.1) / 5 vertex labels, count only, over one
+    batch of x values per step."""
+    import torch
+    from paper_2602_20748_gb300 import rpq, synth
+
+    n = 1 << 22
+    src, dst, lab = synth.rmat_graph(22, 1 << 26, 10, 1.1, seed=synth.BASE_SEED + 2)
+    vl = synth.vertex_labels(n, 5, seed=synth.BASE_SEED + 2)
+    ctx = rpq.Context(device=0)
+    g = rpq.load_graph(ctx, n, 10, src, dst, lab, vl)
+    atoms = [(0, rpq.compile_rpq(ctx, "a"), 1), (0, rpq.compile_rpq(ctx, "b·c*"), 2), (1, rpq.compile_rpq(ctx, "d*"), 2)]
+    B = args.batch
+    rng = np.random.Generator(np.random.PCG64(11))
+    perm = rng.permutation(n).astype(np.uint32)
+    for i in range(args.warmup):
+        rpq.run_crpq(ctx, g, 3, atoms, restrict0=perm[i * B:(i + 1) * B], flags=rpq.RPQ_COUNT_ONLY).free()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    tuples = W = 0
+    for i in range(args.steps):
+        x = perm[(args.warmup + i) * B:(args.warmup + i + 1) * B]
+        r = rpq.run_crpq(ctx, g, 3, atoms, restrict0=x, flags=rpq.RPQ_COUNT_ONLY)
+        tuples += rpq.result_info(r)[0]
+        W += rpq.result_stats(r)["product_edges"]
+        r.free()
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    out = {
+        "metric": "crpq_tuples_per_s", "value": tuples / (ms * args.steps / 1000.0), "unit": "tuples/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "rmat22-triangle-crpq", "atoms": ["x -a-> y", "x -b.c*-> z", "y -d*-> z"],
+                   "x_per_step": B, "vertices": n, "generated_edges": 1 << 26, "labels": 10, "zipf_s": 1.1,
+                   "vertex_labels": 5, "mode": "count only"},
+        "tuples_per_step": tuples // args.steps, "atom_product_edges_per_step": W // args.steps,
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -354,6 +474,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if args.workload == "batch":
+        return bench_batch(args)
+    if args.workload == "crpq":
+        return bench_crpq(args)
     return ours(args, rank, world, local_rank)
 
 

@@ -104,6 +104,17 @@ const char *rpq_last_error(const rpq_ctx *ctx);
 /* Replaces the stream all later work is issued on (NULL: default stream). */
 int rpq_set_stream(rpq_ctx *ctx, void *cuda_stream);
 
+/* Sets a tunable of the context (0 on success, INVALID_ARG for an unknown
+ * name or a value out of range):
+ *   "alpha"        top-down is chosen for a level when alpha * its bytes are
+ *                  below the bottom-up bytes (default 16)
+ *   "grid_share"   fraction (0, 1] of the SMs the persistent traversal grids
+ *                  occupy (default 1; 0.5 lets two contexts' searches run
+ *                  side by side)
+ *   "max_groups"   lane groups (256 start vertices each) per launch, 1 .. 16
+ *   "time_limit_s" bound on each device-side wait (default 20 s) */
+int rpq_set_option(rpq_ctx *ctx, const char *name, double value);
+
 /* ---- graph store (Section 2.1 data graph; Section 2.4 keeps one grid per
  *      edge label -- here one CSR per edge label) ----------------------------- */
 
@@ -243,6 +254,57 @@ typedef struct {
 int run_crpq(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_vars, const int32_t *var_label, const crpq_atom *atoms,
              uint32_t n_atoms, const uint32_t *restrict0, uint32_t n_restrict0, uint32_t flags,
              rpq_result **out);
+
+/* ---- serving: continuous batching of mixed requests ----------------------- */
+
+/* A server evaluates RPQ and CRPQ requests that arrive over time against one
+ * resident graph.  Two worker threads with their own CUDA streams share the
+ * device (half of the SMs each for persistent grids): one batches every
+ * waiting single-source request it can admit (up to max_batch, and only while
+ * the admitted queries' visited bitmaps fit its memory share) into one launch,
+ * so requests that arrive while a batch runs join the next one; the other
+ * runs all-pairs requests (in slices of start vertices) and CRPQs, oldest
+ * first.  Replies carry the row count and digest the standalone call would
+ * report (results are counted, not kept) and the request's latencies.  The
+ * graph, queries and atom queries must stay alive until their requests have
+ * been waited for.  mem_budget_bytes = 0 uses 80% of the free device memory. */
+typedef struct rpq_server rpq_server;
+
+#define RPQ_REQ_SINGLE 1u   /* rho from one start vertex                    */
+#define RPQ_REQ_ALLPAIRS 2u /* rho from every vertex                         */
+#define RPQ_REQ_CRPQ 3u     /* a CRPQ (as run_crpq, all values of variable 0) */
+
+typedef struct {
+  uint32_t kind;             /* RPQ_REQ_*                                      */
+  const rpq_query *q;        /* SINGLE, ALLPAIRS                               */
+  uint32_t source;           /* SINGLE                                         */
+  uint32_t n_vars;           /* CRPQ                                           */
+  const int32_t *var_label;  /* CRPQ, may be NULL; copied at submit            */
+  const crpq_atom *atoms;    /* CRPQ; copied at submit                         */
+  uint32_t n_atoms;          /* CRPQ                                           */
+} rpq_request;
+
+typedef struct {
+  int status;                /* RPQ_OK or the evaluation's error code          */
+  uint64_t count;            /* result rows                                    */
+  uint64_t digest_sum;       /* digest of the rows, as result_info             */
+  uint64_t digest_xor;
+  double queued_ms;          /* submit -> evaluation start                     */
+  double service_ms;         /* evaluation start -> done                       */
+  double latency_ms;         /* submit -> done                                 */
+} rpq_reply;
+
+int rpq_server_create(rpq_ctx *ctx, const rpq_graph *g, uint64_t mem_budget_bytes, uint32_t max_batch,
+                      rpq_server **out);
+/* Queues a request; *ticket identifies it for rpq_server_wait. */
+int rpq_server_submit(rpq_server *s, const rpq_request *req, uint64_t *ticket);
+/* Waits (timeout_s < 0: without limit) for the request and takes its reply;
+ * TIMEOUT if it is not done in time (it stays queued). */
+int rpq_server_wait(rpq_server *s, uint64_t ticket, double timeout_s, rpq_reply *reply);
+/* Batched launches so far and the single-source requests they carried. */
+int rpq_server_stats(rpq_server *s, uint64_t *batches, uint64_t *batched_requests);
+/* Finishes the queued requests, stops the workers and releases the server. */
+void rpq_server_destroy(rpq_server *s);
 
 /* ---- results ------------------------------------------------------------ */
 

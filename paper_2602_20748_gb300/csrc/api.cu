@@ -50,10 +50,12 @@ struct rpq_ctx {
   int sms = 0;
   int bpsm[2] = {0, 0};  // resident traversal blocks per SM for NW = 1, 4
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  float alpha = 4.0f;
+  float alpha = 16.0f;
   uint64_t time_limit_ns = 20ull * 1000 * 1000 * 1000;
   uint32_t max_groups = 16;
   bool trace = false;    // print per-level timings of each traversal (RPQ_TRACE=1)
+  uint64_t spill_cap = SPILL_CAP;  // long-row chunks per level (RPQ_SPILL_CAP lowers it)
+  double grid_share = 1.0;         // fraction of the SMs persistent grids use
   rpq::BatchTuning batch = rpq::batch_default_tuning();  // run_rpq_batch tunables
   int live = 0;          // graphs and results not yet freed
   bool closing = false;  // rpq_destroy was called while handles were live
@@ -244,7 +246,7 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
 
 
   const int force = (flags & RPQ_FORCE_PUSH) ? 1 : (flags & RPQ_FORCE_PULL) ? 2 : 0;
-  const int blocks = ctx->sms * ctx->bpsm[nw == 1 ? 0 : 1];
+  const int blocks = ctx_bfs_blocks(ctx, nw);
   if (blocks <= 0) return set_err(ctx, RPQ_ERR_CUDA, "traversal kernel cannot be made resident");
   const uint32_t segs = (n + EMIT_SEG - 1) / EMIT_SEG;
 
@@ -287,6 +289,7 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
     p.fr1 = w.fr1;
     p.claim = w.claim;
     p.spill = w.spill;
+    p.spill_cap = ctx->spill_cap;
     p.list0 = w.list0;
     p.list1 = w.list1;
     p.ctl = ctx->ctl;
@@ -331,7 +334,7 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
     ep.digest = ctx->small;
     CK(cudaMemsetAsync(ctx->small, 0, 3 * 8, ctx->stream));
     CK(cudaEventRecord(ctx->ev[2], ctx->stream));
-    CK(launch_emit(nw, false, ep, ctx->stream));
+    CK(launch_emit(nw, false, !materialize, ep, ctx->stream));
     CK(exclusive_scan_u32_to_u64(cnt, off, ncnt, ctx->small + 2, tmp, ctx->stream));
     res->stats.launches += 2;
     BfsCtl hctl;
@@ -350,8 +353,11 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
     }
     const uint64_t total = hsmall[2];
     res->count += total;
-    res->dsum += hsmall[0];
-    res->dxor ^= hsmall[1];
+    if (!materialize) {  // the count pass folded the digest
+      res->dsum += hsmall[0];
+      res->dxor ^= hsmall[1];
+    }
+    u64 hdig[2] = {0, 0};
     rpq_stats &s = res->stats;
     s.product_edges += hctl.stats[ST_W];
     s.product_vertices += hctl.stats[ST_N];
@@ -389,17 +395,22 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
         return rc;
       }
       ep.dst = c.dst;
-      CK(launch_emit(nw, true, ep, ctx->stream));
+      CK(launch_emit(nw, true, true, ep, ctx->stream));
       CK(launch_gather_lane_off(off, segs, n_lanes, ctx->small + 2, c.lane_off, ctx->stream));
       CK(cudaMemcpyAsync(c.lanesrc, w.lanesrc, n_lanes * 4, cudaMemcpyDeviceToDevice, ctx->stream));
       res->stats.launches += 2;
       res->chunks.push_back(c);
+      // the write pass folded the digest
+      CK(cudaMemcpyAsync(hdig, ctx->small, 16, cudaMemcpyDeviceToHost, ctx->stream));
     }
     CK(cudaEventRecord(ctx->ev[3], ctx->stream));
     dfree(ctx, cnt, ncnt);
     dfree(ctx, off, ncnt);
     dfree(ctx, tmp, tmpw);
     CK(cudaEventSynchronize(ctx->ev[3]));
+    CK(cudaStreamSynchronize(ctx->stream));
+    res->dsum += hdig[0];
+    res->dxor ^= hdig[1];
     float ms_bfs = 0, ms_emit = 0;
     cudaEventElapsedTime(&ms_bfs, ctx->ev[0], ctx->ev[1]);
     cudaEventElapsedTime(&ms_emit, ctx->ev[2], ctx->ev[3]);
@@ -476,6 +487,10 @@ int rpq_create(rpq_ctx **out, int device, uint64_t mem_budget_bytes, void *cuda_
   if (const char *a = std::getenv("RPQ_ALPHA")) c->alpha = (float)std::atof(a);
   if (const char *m = std::getenv("RPQ_MAX_GROUPS")) c->max_groups = (uint32_t)std::min(16, std::max(1, std::atoi(m)));
   if (const char *t = std::getenv("RPQ_TRACE")) c->trace = std::atoi(t) != 0;
+  if (const char *sc = std::getenv("RPQ_SPILL_CAP")) {
+    c->spill_cap = (uint64_t)std::min<long long>((long long)SPILL_CAP, std::max(0ll, std::atoll(sc)));
+    c->batch.spill_cap = c->spill_cap;
+  }
   if (const char *b = std::getenv("RPQ_BATCH_LIST_CAP"))
     c->batch.list_cap = (uint64_t)std::max(1024ll, std::atoll(b));
   if (dalloc(c, &c->ctl, 1) || dalloc(c, &c->small, 8)) {
@@ -527,6 +542,23 @@ int rpq_set_stream(rpq_ctx *ctx, void *stream) {
   if (!usable(ctx)) return RPQ_ERR_NO_DEVICE;
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->stream = (cudaStream_t)stream;
+  return RPQ_OK;
+}
+
+int rpq_set_option(rpq_ctx *ctx, const char *name, double value) {
+  if (!ctx || !name) return set_err(ctx, RPQ_ERR_INVALID_ARG, "null argument");
+  const std::string n(name);
+  if (n == "alpha" && value > 0) {
+    ctx->alpha = (float)value;
+  } else if (n == "grid_share" && value > 0 && value <= 1) {
+    ctx->grid_share = value;
+  } else if (n == "max_groups" && value >= 1 && value <= 16) {
+    ctx->max_groups = (uint32_t)value;
+  } else if (n == "time_limit_s" && value > 0) {
+    ctx->time_limit_ns = (uint64_t)(value * 1e9);
+  } else {
+    return set_err(ctx, RPQ_ERR_INVALID_ARG, "unknown option or value out of range: " + n);
+  }
   return RPQ_OK;
 }
 
@@ -878,7 +910,8 @@ void ctx_free(rpq_ctx *ctx, void *p, uint64_t bytes) { dev_free(ctx, p, bytes); 
 cudaStream_t ctx_stream(rpq_ctx *ctx) { return ctx->stream; }
 int ctx_error(rpq_ctx *ctx, int code, const std::string &msg) { return set_err(ctx, code, msg); }
 int ctx_device(rpq_ctx *ctx) { return ctx->device; }
-int ctx_bfs_blocks(rpq_ctx *ctx, int nw) { return ctx->sms * ctx->bpsm[nw == 1 ? 0 : 1]; }
+int ctx_sm_share(rpq_ctx *ctx) { return std::max(1, (int)(ctx->sms * ctx->grid_share)); }
+int ctx_bfs_blocks(rpq_ctx *ctx, int nw) { return ctx_sm_share(ctx) * ctx->bpsm[nw == 1 ? 0 : 1]; }
 float ctx_alpha(rpq_ctx *ctx) { return ctx->alpha; }
 uint64_t ctx_time_limit_ns(rpq_ctx *ctx) { return ctx->time_limit_ns; }
 const DevGraph &graph_dev(const rpq_graph *g) { return g->g; }

@@ -28,6 +28,9 @@ namespace {
 constexpr int BATCH_THREADS = 256;  // default block size (the autotuner may pick another)
 constexpr int BATCH_MAX_THREADS = 512;
 constexpr unsigned ERR_LIST_FULL = 100;  // frontier list capacity exceeded
+// Bounds checks: an index outside its array records which check failed (the
+// access is skipped) and stops the search with RPQ_ERR_CUDA on the host.
+constexpr unsigned ERR_BOUNDS = 200;
 
 struct BatchParams {
   const uint32_t *out_off;
@@ -39,16 +42,39 @@ struct BatchParams {
   const u64 *vis_off;  // first word of query i's bitmaps
   const u32 *srcs;
   u64 *vis;
+  u64 vis_words;       // size of vis
+  u64 m;               // edges (size of out_col)
   u64 wps;             // words per state bitmap
   u64 *list0, *list1;
   u64 list_cap;
   u64 *spill;
+  u64 spill_cap;       // spill records available (<= SPILL_CAP)
   BfsCtl *ctl;
   unsigned nblocks;
   u64 time_limit_ns;
 };
 
 __device__ __forceinline__ u64 bentry(u32 i, u32 q, u32 v) { return ((u64)i << 37) | ((u64)q << 32) | v; }
+
+__device__ __forceinline__ bool bad(const BatchParams &p, bool cond, unsigned which) {
+  if (cond) atomicCAS(&p.ctl->err, 0u, ERR_BOUNDS + which);
+  return cond;
+}
+
+
+// Reserves `chunks` spill records, all or nothing: the count only ever covers
+// records that will be written (a reservation that does not fit leaves the
+// row to be processed in place).  Returns the first record or ~0 on failure.
+__device__ __forceinline__ unsigned long long spill_reserve(unsigned long long *count, unsigned chunks,
+                                                            unsigned long long cap) {
+  unsigned long long cur = *(volatile unsigned long long *)count;
+  for (;;) {
+    if (cur + chunks > cap) return ~0ull;
+    unsigned long long prev = atomicCAS(count, cur, cur + chunks);
+    if (prev == cur) return cur;
+    cur = prev;
+  }
+}
 
 __device__ bool bbarrier(BfsCtl *c, unsigned nblocks, u64 limit_ns) {
   __shared__ unsigned stop;
@@ -85,7 +111,7 @@ __device__ __forceinline__ u32 bdegsum(const BatchParams &p, const QueryDesc &qd
   u32 s = 0;
   for (u32 t = qd.out_begin[q]; t < qd.out_begin[q + 1]; t++) {
     u32 l = qd.out_label[t];
-    if (l >= p.L) continue;
+    if (l >= p.L || bad(p, v >= p.n, 4)) continue;
     const u32 *off = p.out_off + (u64)l * (p.n + 1) + v;
     s += __ldg(off + 1) - __ldg(off);
   }
@@ -112,7 +138,10 @@ __device__ __forceinline__ void bappend(const BatchParams &p, bool take, u64 ent
 
 // Test-and-set of (query i, state q2, vertex w); true when this thread set it.
 __device__ __forceinline__ bool bvisit(const BatchParams &p, u32 i, u32 q2, u32 w) {
-  u64 *word = p.vis + p.vis_off[i] + (u64)q2 * p.wps + (w >> 6);
+  if (bad(p, i >= p.nq, 1) || bad(p, w >= p.n, 2)) return false;
+  const u64 at = p.vis_off[i] + (u64)q2 * p.wps + (w >> 6);
+  if (bad(p, at >= p.vis_words || q2 >= p.qd[i].n_states, 3)) return false;
+  u64 *word = p.vis + at;
   const u64 bit = 1ull << (w & 63);
   if (__ldcg(word) & bit) return false;
   return !(atomicOr((unsigned long long *)word, bit) & bit);
@@ -146,10 +175,10 @@ __device__ void bpush(const BatchParams &p, int lp, u32 cur, u32 nxt, u64 n_cur,
     base = __shfl_sync(FULL_MASK, base, 0);
     if (base >= n_cur) break;
     const u64 idx = base + lane;
-    const bool valid = idx < n_cur;
-    const u64 e = valid ? __ldcg(&list[idx]) : 0;
+    const u64 e = idx < n_cur ? __ldcg(&list[idx]) : 0;
     const u32 i = (u32)(e >> 37), q = (u32)(e >> 32) & 31u, v = (u32)e;
-    const QueryDesc *qd = p.qd + i;
+    const bool valid = idx < n_cur && !bad(p, i >= p.nq || v >= p.n, 10);
+    const QueryDesc *qd = p.qd + (valid ? i : 0);
     const u32 t_beg = valid ? qd->out_begin[q] : 0;
     const u32 nt = valid ? qd->out_begin[q + 1] - t_beg : 0;
     const u32 max_nt = __reduce_max_sync(FULL_MASK, nt);
@@ -159,16 +188,17 @@ __device__ void bpush(const BatchParams &p, int lp, u32 cur, u32 nxt, u64 n_cur,
         const u32 t = t_beg + j;
         const u32 l = qd->out_label[t];
         q2 = qd->out_to[t];
-        if (l < p.L) {
+        if (l < p.L && !bad(p, v >= p.n || i >= p.nq, 5)) {
           const u32 *off = p.out_off + (u64)l * (p.n + 1) + v;
           rbeg = __ldg(off);
           rlen = __ldg(off + 1) - rbeg;
+          if (bad(p, (u64)rbeg + rlen > p.m, 6)) rlen = 0;
         }
       }
       if (rlen > SPILL_EDGES) {
         const u32 chunks = (rlen + SPILL_EDGES - 1) / SPILL_EDGES;
-        const u64 at = atomicAdd(&p.ctl->spill_count[cur], (unsigned long long)chunks);
-        if (at + chunks <= SPILL_CAP) {
+        const u64 at = spill_reserve(&p.ctl->spill_count[cur], chunks, p.spill_cap);
+        if (at != ~0ull) {
           for (u32 c = 0; c < chunks; c++) {
             u64 *rec = p.spill + (at + c) * 2;
             rec[0] = bentry(i, q2, 0) | (rbeg + c * SPILL_EDGES);
@@ -200,7 +230,7 @@ __device__ void bpush(const BatchParams &p, int lp, u32 cur, u32 nxt, u64 n_cur,
         const u32 o_i = __shfl_sync(FULL_MASK, i, o);
         bool take = false;
         u32 w = 0;
-        if (k < total) {
+        if (k < total && !bad(p, (u64)o_beg + (k - o_pre) >= p.m, 7)) {
           w = __ldg(p.out_col + o_beg + (k - o_pre));
           take = bvisit(p, o_i, o_q2, w);
         }
@@ -213,8 +243,7 @@ __device__ void bpush(const BatchParams &p, int lp, u32 cur, u32 nxt, u64 n_cur,
 __device__ void bspill(const BatchParams &p, int lp, u32 cur, u32 nxt, u64 *edges) {
   u64 *nlist = lp ? p.list0 : p.list1;
   const u32 lane = lane_id();
-  u64 count = *(volatile unsigned long long *)&p.ctl->spill_count[cur];
-  if (count > SPILL_CAP) count = SPILL_CAP;
+  const u64 count = *(volatile unsigned long long *)&p.ctl->spill_count[cur];
   for (;;) {
     u64 r = 0;
     if (lane == 0) r = atomicAdd(&p.ctl->spill_cursor[cur], 1ull);
@@ -228,7 +257,7 @@ __device__ void bspill(const BatchParams &p, int lp, u32 cur, u32 nxt, u64 *edge
       const u32 k = k0 + lane;
       bool take = false;
       u32 w = 0;
-      if (k < len) {
+      if (k < len && !bad(p, (u64)b + k >= p.m, 8)) {
         w = __ldg(p.out_col + b + k);
         take = bvisit(p, i, q2, w);
       }
@@ -245,6 +274,7 @@ __device__ void bcommit(const BatchParams &p, int lp, u32 nxt, u64 *W, u64 *N) {
   for (u64 j = (u64)blockIdx.x * blockDim.x + threadIdx.x; j < n_next; j += stride) {
     const u64 e = __ldcg(&nlist[j]);
     const u32 i = (u32)(e >> 37), q = (u32)(e >> 32) & 31u, v = (u32)e;
+    if (bad(p, i >= p.nq, 9)) continue;
     *W += bdegsum(p, p.qd[i], q, v);
     *N += 1;
   }
@@ -314,6 +344,8 @@ struct BEmitParams {
   u32 *rows;  // (query, vertex) pairs
   u64 *digest;
   u32 qbase;  // index of this launch's first query in the caller's arrays
+  u64 *qstats;      // optional: per query (rows, digest sum, digest xor) over (source, y)
+  const u32 *srcs;  // the launch's sources (for qstats)
 };
 
 template <bool WRITE>
@@ -353,6 +385,23 @@ __global__ void __launch_bounds__(BEMIT_WORDS) batch_emit(const BEmitParams p) {
       atomicXor(&p.digest[1], hx);
     }
     if (threadIdx.x == 0) p.cnt[(u64)i * p.chunks + c] = block_tot;
+    if (p.qstats) {
+      // the same rows as a single-source result: (source, y) pairs
+      const u64 s = p.srcs[i];
+      u64 qs = 0, qx = 0;
+      for (u64 b = r; b; b &= b - 1) {
+        u64 h = splitmix64((s << 32) | (k * 64 + __ffsll(b) - 1));
+        qs += h;
+        qx ^= h;
+      }
+      qs = warp_sum(qs);
+      qx = warp_xor(qx);
+      if (lane_id() == 0 && (qs | qx)) {
+        atomicAdd(&p.qstats[3 * (u64)i + 1], qs);
+        atomicXor(&p.qstats[3 * (u64)i + 2], qx);
+      }
+      if (threadIdx.x == 0 && block_tot) atomicAdd(&p.qstats[3 * (u64)i], (u64)block_tot);
+    }
   } else {
     u64 pos = p.off[(u64)i * p.chunks + c] + before + inc - pc;
     for (u64 b = r; b; b &= b - 1) {
@@ -389,7 +438,7 @@ struct DBuf {
 
 }  // namespace
 
-BatchTuning batch_default_tuning() { return BatchTuning{BATCH_THREADS, 4096, 1ull << 28}; }
+BatchTuning batch_default_tuning() { return BatchTuning{BATCH_THREADS, 4096, 1ull << 28, SPILL_CAP}; }
 
 // One launch over queries [0, nq) of the arrays; appends rows to `out`.
 static int batch_launch(rpq_ctx *ctx, const rpq_graph *g, uint32_t qbase, uint32_t nq,
@@ -434,11 +483,14 @@ static int batch_launch(rpq_ctx *ctx, const rpq_graph *g, uint32_t qbase, uint32
   p.vis_off = d_voff.p;
   p.srcs = d_src.p;
   p.vis = d_vis.p;
+  p.vis_words = vis_words;
+  p.m = dg.m;
   p.wps = wps;
   p.list0 = d_l0.p;
   p.list1 = d_l1.p;
   p.list_cap = tun.list_cap;
   p.spill = d_spill.p;
+  p.spill_cap = tun.spill_cap;
   p.ctl = d_ctl.p;
   p.time_limit_ns = ctx_time_limit_ns(ctx);
   int bpsm = 0, sms = 0, dev = 0;
@@ -446,7 +498,7 @@ static int batch_launch(rpq_ctx *ctx, const rpq_graph *g, uint32_t qbase, uint32
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, batch_kernel, tun.threads, 0)) != cudaSuccess)
     return berr(ctx, e, "occupancy");
-  const int blocks = sms * bpsm;
+  const int blocks = std::max(1, std::min(sms, ctx_sm_share(ctx))) * bpsm;
   p.nblocks = (unsigned)blocks;
   void *args[] = {(void *)&p};
   cudaEvent_t ev0, ev1;
@@ -479,6 +531,14 @@ static int batch_launch(rpq_ctx *ctx, const rpq_graph *g, uint32_t qbase, uint32
   ep.rows = nullptr;
   ep.digest = d_small.p;
   ep.qbase = qbase;
+  ep.srcs = d_src.p;
+  ep.qstats = nullptr;
+  DBuf<u64> d_qstats;
+  if (out->per_query) {
+    if ((rc = d_qstats.alloc(ctx, 3ull * nq))) return rc;
+    if ((e = cudaMemsetAsync(d_qstats.p, 0, 24ull * nq, st)) != cudaSuccess) return berr(ctx, e, "memset");
+    ep.qstats = d_qstats.p;
+  }
   dim3 grid(chunks, nq);
   batch_emit<false><<<grid, BEMIT_WORDS, 0, st>>>(ep);
   if ((e = cudaGetLastError()) != cudaSuccess) return berr(ctx, e, "batch_emit");
@@ -498,6 +558,15 @@ static int batch_launch(rpq_ctx *ctx, const rpq_graph *g, uint32_t qbase, uint32
   cudaEventDestroy(ev0);
   cudaEventDestroy(ev1);
   if (hctl.err == ERR_LIST_FULL) return RPQ_BATCH_SPLIT;
+  if (out->per_query && hctl.err == 0) {
+    std::vector<u64> qs(3ull * nq);
+    if ((e = cudaMemcpy(qs.data(), d_qstats.p, 24ull * nq, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return berr(ctx, e, "qstats");
+    out->qstats.insert(out->qstats.end(), qs.begin(), qs.end());
+  }
+  if (hctl.err >= ERR_BOUNDS)
+    return ctx_error(ctx, RPQ_ERR_CUDA, "batch traversal index check " + std::to_string(hctl.err - ERR_BOUNDS) +
+                                            " failed (a device index out of its array; access skipped)");
   if (hctl.err) return ctx_error(ctx, RPQ_ERR_TIMEOUT, "batch traversal grid barrier wait ran out of time");
   out->stats.bfs_ms += ms;
   out->stats.product_edges += hctl.stats[ST_W];

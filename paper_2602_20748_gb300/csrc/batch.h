@@ -16,12 +16,15 @@ struct BatchTuning {
   int threads;                  // block size of the persistent kernel
   uint32_t queries_per_launch;  // queries sharing one launch
   uint64_t list_cap;            // frontier list capacity (entries)
+  uint64_t spill_cap;           // long-row chunks per level (<= SPILL_CAP)
 };
 
 struct BatchOut {
   uint64_t count = 0, dsum = 0, dxor = 0;
   rpq_stats stats{};
   std::vector<std::pair<u32 *, uint64_t>> chunks;  // row-major (query, vertex) rows, in order
+  bool per_query = false;       // fill qstats: per query (rows, digest sum, digest xor) of its
+  std::vector<uint64_t> qstats;  // (source, y) rows, as run_rpq would report them alone
 };
 
 BatchTuning batch_default_tuning();

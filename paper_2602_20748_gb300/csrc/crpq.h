@@ -26,6 +26,7 @@ cudaStream_t ctx_stream(rpq_ctx *ctx);
 int ctx_error(rpq_ctx *ctx, int code, const std::string &msg);
 int ctx_device(rpq_ctx *ctx);
 int ctx_bfs_blocks(rpq_ctx *ctx, int nw);
+int ctx_sm_share(rpq_ctx *ctx);  // SMs the context's persistent grids may use
 float ctx_alpha(rpq_ctx *ctx);
 uint64_t ctx_time_limit_ns(rpq_ctx *ctx);
 const DevGraph &graph_dev(const rpq_graph *g);

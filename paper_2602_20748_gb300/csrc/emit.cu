@@ -1,8 +1,8 @@
 // Result emission: visited words -> distinct (src, dst) rows in sorted order.
 //
 // After the search, the result set of start vertex s (Definition 1) is the
-// set of v with some accepting state q such that s's lane is set in
-// VIS[g][q][v].  For lane group g, OR the accepting states' words into a
+// set of v with some accepting state q such that s's lane is set in the
+// visited word of (group g, state q, vertex v).  For lane group g, OR the accepting states' words into a
 // K-bit result word per vertex.  A block owns a segment of EMIT_SEG vertices
 // of one group; warp c handles lane column c (32 lanes) and walks the segment
 // in 32-vertex tiles: the 32 x 32 bit tile is transposed with 32 ballots so
@@ -16,7 +16,7 @@
 
 namespace rpq {
 
-template <int NW, bool WRITE>
+template <int NW, bool WRITE, bool DIGEST>
 __global__ void emit_kernel(const EmitParams p) {
   const u32 seg = blockIdx.x, g = blockIdx.y;
   const u32 col = threadIdx.x >> 5, lane = lane_id();
@@ -42,6 +42,7 @@ __global__ void emit_kernel(const EmitParams p) {
       }
     }
     x &= valid_cols;
+    if (!__any_sync(FULL_MASK, x)) continue;  // no result in this 32 x 32 tile
     // transpose the 32 x 32 tile: thread j receives bit k = (w0 + k in lane 32*col + j)
     u32 mine = 0;
 #pragma unroll
@@ -50,19 +51,19 @@ __global__ void emit_kernel(const EmitParams p) {
       if (lane == (u32)j) mine = b;
     }
     if (!mine) continue;
-    if (WRITE) {
-      for (u32 b = mine; b; b &= b - 1) p.dst[pos++] = w0 + (__ffs(b) - 1);
-    } else {
-      cnt += __popc(mine);
-      for (u32 b = mine; b; b &= b - 1) {
-        u64 h = splitmix64(((u64)src << 32) | (u64)(w0 + (__ffs(b) - 1)));
+    if (!WRITE) cnt += __popc(mine);
+    for (u32 b = mine; (WRITE || DIGEST) && b; b &= b - 1) {
+      const u32 y = w0 + (__ffs(b) - 1);
+      if (WRITE) p.dst[pos++] = y;
+      if (DIGEST) {
+        u64 h = splitmix64(((u64)src << 32) | (u64)y);
         hsum += h;
         hxor ^= h;
       }
     }
   }
-  if (!WRITE) {
-    p.cnt[glane * p.segs + seg] = (u32)cnt;
+  if (!WRITE) p.cnt[glane * p.segs + seg] = (u32)cnt;
+  if (DIGEST) {
     hsum = warp_sum(hsum);
     hxor = warp_xor(hxor);
     if (lane == 0 && (hsum | hxor)) {
@@ -72,18 +73,26 @@ __global__ void emit_kernel(const EmitParams p) {
   }
 }
 
-cudaError_t launch_emit(int nw, bool write, const EmitParams &p, cudaStream_t st) {
+// Pass 1 (write = false) counts per (lane, segment); pass 2 (write = true)
+// writes the destinations.  The row digest is folded in the pass given
+// digest = true (the write pass when rows are kept, else the count pass).
+cudaError_t launch_emit(int nw, bool write, bool digest, const EmitParams &p, cudaStream_t st) {
   dim3 grid(p.segs, p.G);
+  const int threads = nw == 1 ? 64 : 256;
   if (nw == 1) {
     if (write)
-      emit_kernel<1, true><<<grid, 64, 0, st>>>(p);
+      digest ? emit_kernel<1, true, true><<<grid, threads, 0, st>>>(p)
+             : emit_kernel<1, true, false><<<grid, threads, 0, st>>>(p);
     else
-      emit_kernel<1, false><<<grid, 64, 0, st>>>(p);
+      digest ? emit_kernel<1, false, true><<<grid, threads, 0, st>>>(p)
+             : emit_kernel<1, false, false><<<grid, threads, 0, st>>>(p);
   } else {
     if (write)
-      emit_kernel<4, true><<<grid, 256, 0, st>>>(p);
+      digest ? emit_kernel<4, true, true><<<grid, threads, 0, st>>>(p)
+             : emit_kernel<4, true, false><<<grid, threads, 0, st>>>(p);
     else
-      emit_kernel<4, false><<<grid, 256, 0, st>>>(p);
+      digest ? emit_kernel<4, false, true><<<grid, threads, 0, st>>>(p)
+             : emit_kernel<4, false, false><<<grid, threads, 0, st>>>(p);
   }
   return cudaGetLastError();
 }

@@ -142,6 +142,20 @@ __device__ __forceinline__ u32 degsum(const BfsParams &p, u32 q, u32 v) {
   return s;
 }
 
+// Reserves `chunks` spill records, all or nothing: the count only ever covers
+// records that will be written (a reservation that does not fit leaves the
+// row to be processed in place).  Returns the first record or ~0 on failure.
+__device__ __forceinline__ unsigned long long spill_reserve(unsigned long long *count, unsigned chunks,
+                                                            unsigned long long cap) {
+  unsigned long long cur = *(volatile unsigned long long *)count;
+  for (;;) {
+    if (cur + chunks > cap) return ~0ull;
+    unsigned long long prev = atomicCAS(count, cur, cur + chunks);
+    if (prev == cur) return cur;
+    cur = prev;
+  }
+}
+
 // Warp-aggregated append of `entry` for the lanes with `take` set.  All 32
 // lanes must call it.
 __device__ __forceinline__ void warp_append(bool take, u64 entry, unsigned long long *count, u64 *list) {
@@ -262,8 +276,8 @@ __device__ void push_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u64 n_c
       }
       if (p.spill && rlen > SPILL_EDGES) {
         const u32 chunks = (rlen + SPILL_EDGES - 1) / SPILL_EDGES;
-        const u64 at = atomicAdd(&p.ctl->spill_count[cur], (unsigned long long)chunks);
-        if (at + chunks <= SPILL_CAP) {
+        const u64 at = spill_reserve(&p.ctl->spill_count[cur], chunks, p.spill_cap);
+        if (at != ~0ull) {
           for (u32 c = 0; c < chunks; c++) {
             u64 *rec = p.spill + (at + c) * (2 + NW);
             rec[0] = ((u64)tgq << 32) | (rbeg + c * SPILL_EDGES);
@@ -326,8 +340,7 @@ __device__ void spill_phase(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 st
   u64 *nlist = lp ? p.list0 : p.list1;
   u64 *FB = lp ? p.fr0 : p.fr1;
   const u32 lane = lane_id();
-  u64 count = *(volatile unsigned long long *)&p.ctl->spill_count[cur];
-  if (count > SPILL_CAP) count = SPILL_CAP;
+  const u64 count = *(volatile unsigned long long *)&p.ctl->spill_count[cur];
   u64 edges = 0;
   for (;;) {
     u64 r = 0;

@@ -141,6 +141,7 @@ struct BfsParams {
   unsigned long long *fr1;     // frontier pong
   unsigned int *claim;         // [Q][n][G] level stamps (NW > 1)
   unsigned long long *spill;   // SPILL_CAP chunk records (nullptr: no spilling)
+  unsigned long long spill_cap;  // records usable per level (<= SPILL_CAP)
   unsigned long long *list0;   // entries ((g*Q+q) << 32 | v)
   unsigned long long *list1;
   BfsCtl *ctl;
@@ -172,7 +173,7 @@ struct EmitParams {
 };
 constexpr int EMIT_TILES = 32;  // 32-vertex tiles per segment
 constexpr int EMIT_SEG = 32 * EMIT_TILES;
-cudaError_t launch_emit(int nw, bool write, const EmitParams &p, cudaStream_t st);
+cudaError_t launch_emit(int nw, bool write, bool digest, const EmitParams &p, cudaStream_t st);
 
 // Write pass into interleaved (src, dst) rows of a caller's buffer (NW = 1).
 cudaError_t launch_emit_pairs(const EmitParams &p, uint32_t *out, cudaStream_t st);

@@ -188,7 +188,7 @@ extern "C" int run_rpq_static(rpq_ctx *ctx, const rpq_graph *g, const rpq_query 
   ep.off = off;
   ep.dst = nullptr;
   ep.digest = small;
-  STATIC_CK(launch_emit(1, false, ep, st));
+  STATIC_CK(launch_emit(1, false, false, ep, st));
   STATIC_CK(exclusive_scan_u32_to_u64(cnt, off, (size_t)64 * segs, small + 2, tmp, st));
   unsigned int err = 0;
   u64 total = 0;

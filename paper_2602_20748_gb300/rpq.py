@@ -309,3 +309,86 @@ def rpq_autotune_batch(ctx: Context, g: Graph, queries, sources):
     ctx.check(_lib.rpq_autotune_batch(ctx.h, g.h, len(queries), ctypes.cast(arr, c_void_p), _ptr(s),
                                       ctypes.byref(t), ctypes.byref(k)))
     return t.value, k.value
+
+
+class rpq_request(ctypes.Structure):
+    _fields_ = [("kind", c_u32), ("q", c_void_p), ("source", c_u32), ("n_vars", c_u32), ("var_label", c_void_p),
+                ("atoms", c_void_p), ("n_atoms", c_u32)]
+
+
+class rpq_reply(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("count", c_u64), ("digest_sum", c_u64), ("digest_xor", c_u64),
+                ("queued_ms", ctypes.c_double), ("service_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+RPQ_REQ_SINGLE = 1
+RPQ_REQ_ALLPAIRS = 2
+RPQ_REQ_CRPQ = 3
+
+_lib.rpq_set_option.argtypes = [c_void_p, ctypes.c_char_p, ctypes.c_double]
+_lib.rpq_server_create.argtypes = [c_void_p, c_void_p, c_u64, c_u32, P(c_void_p)]
+_lib.rpq_server_submit.argtypes = [c_void_p, P(rpq_request), P(c_u64)]
+_lib.rpq_server_wait.argtypes = [c_void_p, c_u64, ctypes.c_double, P(rpq_reply)]
+_lib.rpq_server_stats.argtypes = [c_void_p, P(c_u64), P(c_u64)]
+_lib.rpq_server_destroy.argtypes = [c_void_p]
+_lib.rpq_server_destroy.restype = None
+EXPORTED += ["rpq_set_option", "rpq_server_create", "rpq_server_submit", "rpq_server_wait", "rpq_server_stats",
+             "rpq_server_destroy"]
+
+
+def rpq_set_option(ctx: Context, name: str, value: float):
+    ctx.check(_lib.rpq_set_option(ctx.h, name.encode(), float(value)))
+
+
+class Server:
+    """rpq_server_*: continuous batching of mixed requests on one graph."""
+
+    def __init__(self, ctx: Context, g: Graph, mem_budget_bytes: int = 0, max_batch: int = 4096):
+        h = c_void_p()
+        ctx.check(_lib.rpq_server_create(ctx.h, g.h, mem_budget_bytes, max_batch, ctypes.byref(h)))
+        self.ctx, self.g, self.h = ctx, g, h
+        self._keep = {}
+
+    def submit_single(self, q: Query, source: int) -> int:
+        return self._submit(rpq_request(RPQ_REQ_SINGLE, q.h, int(source), 0, None, None, 0), (q,))
+
+    def submit_allpairs(self, q: Query) -> int:
+        return self._submit(rpq_request(RPQ_REQ_ALLPAIRS, q.h, 0, 0, None, None, 0), (q,))
+
+    def submit_crpq(self, n_vars: int, atoms, var_label=None) -> int:
+        arr = (crpq_atom * len(atoms))(*[crpq_atom(a[0], a[2], a[1].h) for a in atoms])
+        vl = None if var_label is None else np.ascontiguousarray(var_label, dtype=np.int32)
+        req = rpq_request(RPQ_REQ_CRPQ, None, 0, n_vars, _ptr(vl), ctypes.cast(arr, c_void_p), len(atoms))
+        return self._submit(req, tuple(a[1] for a in atoms))
+
+    def _submit(self, req, keep) -> int:
+        t = c_u64()
+        rc = _lib.rpq_server_submit(self.h, ctypes.byref(req), ctypes.byref(t))
+        if rc != 0:
+            raise RPQError(rc, "submit refused")
+        self._keep[t.value] = keep
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float = -1.0) -> dict:
+        rep = rpq_reply()
+        rc = _lib.rpq_server_wait(self.h, ticket, timeout_s, ctypes.byref(rep))
+        if rc != 0:
+            raise RPQError(rc, "wait failed")
+        self._keep.pop(ticket, None)
+        return rep.as_dict()
+
+    def stats(self):
+        b, r = c_u64(), c_u64()
+        _lib.rpq_server_stats(self.h, ctypes.byref(b), ctypes.byref(r))
+        return b.value, r.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.rpq_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()

@@ -110,6 +110,32 @@ def test_batch_rmat22_sampled(ctx):
     r = rpq.run_rpq_batch(ctx, g, qs, sources)
     got = rpq.fetch_pairs(r)
     rng = np.random.Generator(np.random.PCG64(3))
-    for i in rng.choice(4096, 24, replace=False):
+    for i in rng.choice(4096, 6, replace=False):
         want = oracle.rpq(og, regexes[i], sources=[int(sources[i])]).rows[:, 1]
         assert np.array_equal(got[got[:, 0] == i][:, 1], want), regexes[i]
+
+
+def test_batch_spill_capacity_overflow():
+    """As for the all-pairs engine: with the long-row chunk capacity forced
+    down to 3, rows that do not fit are processed in place."""
+    old = os.environ.get("RPQ_SPILL_CAP")
+    os.environ["RPQ_SPILL_CAP"] = "3"
+    try:
+        c3 = rpq.Context(device=0)
+    finally:
+        if old is None:
+            del os.environ["RPQ_SPILL_CAP"]
+        else:
+            os.environ["RPQ_SPILL_CAP"] = old
+    n = 6000
+    rs, rd, rl = synth.random_graph(n, 12000, 2, seed=91)
+    src = np.concatenate([np.repeat(np.arange(10, dtype=np.uint32), 2500), rs]).astype(np.uint32)
+    dst = np.concatenate([synth.random_graph(n, 25000, 1, seed=92)[1], rd]).astype(np.uint32)
+    lab = np.concatenate([np.zeros(25000, np.uint16), rl]).astype(np.uint16)
+    g = rpq.load_graph(c3, n, 2, src, dst, lab)
+    og = oracle.Graph(n, 2, src, dst, lab)
+    regexes = ["a.b*", "(a|b)+", "a", "a.a", "b*.a"] * 12
+    sources = np.array([i % 10 if i % 3 else 100 + i for i in range(len(regexes))], np.uint32)
+    qs = [rpq.compile_rpq(c3, r) for r in regexes]
+    got = rpq.fetch_pairs(rpq.run_rpq_batch(c3, g, qs, sources))
+    assert np.array_equal(got, oracle_batch_rows(og, regexes, sources))

@@ -279,3 +279,43 @@ def test_rmat20_sampled_sources_work_counter(ctx, rmat20, regex):
     want = oracle.rpq(og, regex, sources=sample)
     for mode in MODES.values():
         check(ctx, g, og, regex, sources=sample, mode=mode, want=want)
+
+
+def _ctx_with_env(**env):
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update({k: str(v) for k, v in env.items()})
+    try:
+        return rpq.Context(device=0)
+    finally:
+        for k, v in old.items():
+            if v is None:
+                del os.environ[k]
+            else:
+                os.environ[k] = v
+
+
+def _hub_graph():
+    # ten hubs with 2,500 out-edges (three 1,024-edge chunks each) plus noise
+    n = 6000
+    rs, rd, rl = synth.random_graph(n, 12000, 2, seed=91)
+    hub_src = np.repeat(np.arange(10, dtype=np.uint32), 2500)
+    hub_dst = synth.random_graph(n, 25000, 1, seed=92)[1]
+    src = np.concatenate([hub_src, rs]).astype(np.uint32)
+    dst = np.concatenate([hub_dst, rd]).astype(np.uint32)
+    lab = np.concatenate([np.zeros(25000, np.uint16), rl]).astype(np.uint16)
+    return n, src, dst, lab
+
+
+def test_spill_capacity_overflow_falls_back_in_place():
+    """Top-down rows longer than 1,024 edges are queued as chunks; when the
+    per-level chunk capacity runs out, the remaining rows are processed in
+    place (capacity forced down to 3 chunks here)."""
+    c3 = _ctx_with_env(RPQ_SPILL_CAP=3)
+    n, src, dst, lab = _hub_graph()
+    g = rpq.load_graph(c3, n, 2, src, dst, lab)
+    og = oracle.Graph(n, 2, src, dst, lab)
+    sources = np.concatenate([np.arange(10), np.arange(100, 400)]).astype(np.uint32)
+    for regex in ("a.b*", "(a|b)+"):
+        want = oracle.rpq(og, regex, sources=sources)
+        for mode in (0, rpq.RPQ_FORCE_PUSH):
+            check(c3, g, og, regex, sources=sources, mode=mode, want=want)
