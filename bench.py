@@ -53,11 +53,15 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="allpairs", choices=["allpairs", "batch", "crpq"],
+    ap.add_argument("--workload", default="allpairs", choices=["allpairs", "batch", "crpq", "serve"],
                     help="allpairs: the R-MAT 2^20 all-pairs line (default); batch: 4,096 single-source "
-                         "queries on R-MAT 2^22; crpq: the 3-atom triangle CRPQ on R-MAT 2^22")
-    ap.add_argument("--scale", type=int, default=SCALE,
+                         "queries on R-MAT 2^22; crpq: the 3-atom triangle CRPQ on R-MAT 2^22; serve: a Poisson "
+                         "stream of mixed requests on R-MAT 2^24")
+    ap.add_argument("--scale", type=int, default=None,
                     help="R-MAT scale (vertices 2^scale, 16 * 2^scale edges); smaller cases are for profiling")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: mean arrivals per second")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="serve: arrival window (s)")
+    ap.add_argument("--drain", type=float, default=10.0, help="serve: time after the window before cancelling (s)")
     return ap.parse_args()
 
 
@@ -205,6 +209,8 @@ def ours(args, rank: int, world: int, local_rank: int):
         dist.init_process_group("nccl")
     from paper_2602_20748_gb300 import rpq
 
+    if args.scale is None:
+        args.scale = SCALE
     n, src, dst, lab = make_graph(args.scale)
     ctx = rpq.Context(device=local_rank)
     t0 = time.perf_counter()
@@ -269,30 +275,30 @@ def ours(args, rank: int, world: int, local_rank: int):
         dist.barrier()
     value = W_all / (ms_max / 1000.0)
 
-    # end to end through the public API: host source list in, rows out to pinned host memory
+    # End to end through the public API: every row goes to pinned host memory
+    # through rpq_stream_* (the rows of one launch are copied while the next
+    # launch explores).  Each rank streams a contiguous range of steps * B
+    # start vertices per query; bytes are counted from what crosses the link:
+    # the lane source ids the library uploads per launch, and per launch the
+    # destinations (4 B per row) plus the lane offsets and sources.
     e2e = None
     if not args.no_e2e:
-        buf = None
-        h2d = d2h = 0
-        W_e2e = 0
+        W_e2e = rows_e2e = 0
+        launches = 0
+        base = ((args.warmup + args.steps) * B + rank * args.steps * B) % n
+        lo, hi = base, min(n, base + args.steps * B)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
-        for i in range(args.steps):
-            b0 = batch_of(args.warmup + args.steps + i) * B
-            sources = np.arange(b0, b0 + B, dtype=np.uint32)
-            for q in qs:
-                r = rpq.run_rpq(ctx, g, q, sources, rpq.RPQ_MATERIALIZE)
-                cnt = rpq.result_info(r)[0]
-                if buf is None or buf.numel() < 2 * cnt:
-                    buf = torch.empty(max(2 * cnt, 1 << 20), dtype=torch.int32, pin_memory=True)
-                rows = rpq.fetch_pairs(r, 0, cnt, out=buf.numpy().view(np.uint32))
-                assert len(rows) == cnt
-                W_e2e += rpq.result_stats(r)["product_edges"]
-                h2d += sources.nbytes
-                d2h += rows.nbytes
-                r.free()
+        for q in qs:
+            st_ = rpq.Stream(ctx, g, q, lo, hi)
+            while (blk := st_.next_block()) is not None:
+                rows_e2e += len(blk[2])
+            r_, _, _, sst = st_.info()
+            W_e2e += sst["product_edges"]
+            launches += sst["bfs_launches"]
+            st_.close()
         t_e2e = time.perf_counter() - t0
         if dist:
             tt = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
@@ -301,8 +307,11 @@ def ours(args, rank: int, world: int, local_rank: int):
             tw = torch.tensor([W_e2e], dtype=torch.float64, device="cuda")
             dist.all_reduce(tw)
             W_e2e = int(tw.item())
-        e2e = {"value": W_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
-               "d2h_bytes_per_step": d2h // args.steps}
+        lane_meta = launches * (B * 4 + (B + 1) * 8)
+        e2e = {"value": W_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": launches * B * 4 // args.steps,
+               "d2h_bytes_per_step": (rows_e2e * 4 + lane_meta) // args.steps,
+               "api": "rpq_stream_* (rows copied to pinned host memory while the next launch runs)",
+               "rows_per_step": rows_e2e // args.steps}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -353,8 +362,10 @@ def ours(args, rank: int, world: int, local_rank: int):
 def bench_batch(args):
     """4,096 single-source RPQs (1-6 Zipf symbols, 0-2 stars, 1/4 alternation
     pairs, sources proportional to out-degree) on R-MAT 2^22 / 2^26 edges /
-    8 labels Zipf(1.2): one run_rpq_batch call per step against run_rpq one
-    query per launch, equal results checked on the plain subset."""
+    8 labels Zipf(1.2): one run_rpq_batch call (RPQ_PER_QUERY: each query's
+    own row count and digest) per step, against run_rpq one query per launch
+    (count only) on the first 512 queries; every one of those 512 replies must
+    agree exactly."""
     import torch
     from paper_2602_20748_gb300 import rpq, synth
 
@@ -368,55 +379,54 @@ def bench_batch(args):
     threads, per_launch = rpq.rpq_autotune_batch(ctx, g, qs, sources)
     tune_s = time.perf_counter() - t0
     for _ in range(args.warmup):
-        rpq.run_rpq_batch(ctx, g, qs, sources).free()
+        rpq.run_rpq_batch(ctx, g, qs, sources, flags=rpq.RPQ_PER_QUERY).free()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(0)
     sampler.start()
     torch.cuda.synchronize()
     ev0.record()
     W = rows = launches = 0
-    info = None
-    for _ in range(args.steps):
-        r = rpq.run_rpq_batch(ctx, g, qs, sources)
+    r = None
+    for k in range(args.steps):
+        if r is not None:
+            r.free()
+        r = rpq.run_rpq_batch(ctx, g, qs, sources, flags=rpq.RPQ_PER_QUERY)
         st = rpq.result_stats(r)
         W += st["product_edges"]
         launches += st["launches"]
-        info = rpq.result_info(r)
-        rows += info[0]
-        r.free()
+        rows += rpq.result_info(r)[0]
     ev1.record()
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
-    # plain path: one run_rpq launch per query, on a subset, timed per query
+    batched = [rpq.result_query_stats(r, i) for i in range(512)]
+    r.free()
+    # plain path: one run_rpq launch per query, timed per query
     k = 512
     lat = []
-    plain_rows = 0
-    plain_digest = [0, 0]
+    agree = 0
     for i in range(k):
         t1 = time.perf_counter()
-        r = rpq.run_rpq(ctx, g, qs[i], [sources[i]])
-        c, _, hs, hx = rpq.result_info(r)
+        one = rpq.run_rpq(ctx, g, qs[i], [sources[i]], flags=rpq.RPQ_COUNT_ONLY)
+        c, _, hs, hx = rpq.result_info(one)
         lat.append(time.perf_counter() - t1)
-        plain_rows += c
-        r.free()
+        one.free()
+        agree += (c, hs, hx) == batched[i]
     plain_qps = k / sum(lat)
-    # equal results: the batched rows of the first k queries against the plain ones
-    rb = rpq.run_rpq_batch(ctx, g, qs[:k], sources[:k])
-    eq = rpq.result_info(rb)[0] == plain_rows
-    rb.free()
     qps = 4096 / (ms / 1000.0)
     out = {
         "metric": "queries_per_s", "value": qps, "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32", "data": "synthetic",
         "config": {"workload": "rmat22-batched-single-source", "queries": 4096, "vertices": n,
-                   "generated_edges": 1 << 26, "labels": 8, "zipf_s": 1.2, "autotuned_threads": threads,
-                   "autotuned_queries_per_launch": per_launch, "autotune_s": round(tune_s, 3)},
-        "batched_latency_ms": ms, "product_edges_per_s": W / (ms * args.steps / 1000.0), "rows_per_step": rows // args.steps,
+                   "generated_edges": 1 << 26, "labels": 8, "zipf_s": 1.2, "mode": "per-query count + digest",
+                   "autotuned_threads": threads, "autotuned_queries_per_launch": per_launch,
+                   "autotune_s": round(tune_s, 3)},
+        "batched_latency_ms": ms, "product_edges_per_s": W / (ms * args.steps / 1000.0),
+        "rows_per_step": rows // args.steps,
         "plain": {"queries_per_s": plain_qps, "p50_ms": 1000 * float(np.percentile(lat, 50)),
                   "p99_ms": 1000 * float(np.percentile(lat, 99)), "queries_timed": k},
-        "speedup_vs_plain": qps / plain_qps, "equal_results_on_plain_subset": bool(eq),
+        "speedup_vs_plain": qps / plain_qps, "equal_results": {"compared": k, "agree": int(agree)},
         "clocks": clocks, "gpu_launches": launches,
     }
     print(json.dumps(out), flush=True)
@@ -467,6 +477,196 @@ def bench_crpq(args):
     return 0
 
 
+def _pct(lat_ms, offered: int, q: float):
+    """Latency percentile over all offered requests; requests not completed in
+    the run count as slower than any completed one (None if the percentile
+    falls among them)."""
+    if offered == 0:
+        return None
+    k = int(np.ceil(q / 100.0 * offered)) - 1
+    lat = sorted(lat_ms)
+    return float(lat[k]) if k < len(lat) else None
+
+
+def _class_summary(kinds, lat, status, wall_s):
+    out = {}
+    for k, name in ((1, "single"), (2, "allpairs"), (3, "crpq")):
+        idx = [i for i in range(len(kinds)) if kinds[i] == k]
+        done = [lat[i] for i in idx if status[i] == 0]
+        out[name] = {"offered": len(idx), "completed": len(done),
+                     "not_completed": len(idx) - len(done),
+                     "p50_ms": _pct(done, len(idx), 50), "p99_ms": _pct(done, len(idx), 99),
+                     "completed_per_s": len(done) / wall_s}
+    return out
+
+
+def bench_serve(args):
+    """Mixed serving: a Poisson stream (mean --rate requests/s over
+    --serve-seconds) of single-source RPQs (80%), all-pairs RPQs (15%) and
+    triangle CRPQs (5%) on R-MAT 2^24 / 2^28 edges / 16 labels Zipf(1.2);
+    all-pairs and CRPQ labels come from the Zipf tail (ranks 9-16).  The
+    stream runs through the server (continuous batching of singles, a bulk
+    worker beside it) and through a plain FIFO (one request at a time in
+    arrival order: run_rpq / run_crpq per request, all-pairs and CRPQs in
+    slices of 4,096 start values).  Each run lasts the arrival window plus
+    --drain seconds; what is not done then is cancelled and counted as not
+    completed.  Latency = arrival -> result ready; results are counted and
+    digested, not kept.  Replies of requests both runs completed must agree."""
+    import torch
+    from paper_2602_20748_gb300 import rpq, synth
+
+    scale = args.scale if args.scale is not None else 24
+    n = 1 << scale
+    L = 16
+    t_gen = time.perf_counter()
+    src, dst, lab = synth.rmat_graph(scale, 16 << scale, L, 1.2, seed=synth.BASE_SEED + 5)
+    t_arr, kinds, spec = synth.serve_stream(args.rate, args.serve_seconds, L, 1.2, src, n,
+                                            seed=synth.BASE_SEED + 5)
+    gen_s = time.perf_counter() - t_gen
+    ctx = rpq.Context(device=0)
+    g = rpq.load_graph(ctx, n, L, src, dst, lab)
+    del src, dst, lab
+    cache = {}
+
+    def comp(rx):
+        if rx not in cache:
+            cache[rx] = rpq.compile_rpq(ctx, rx)
+        return cache[rx]
+
+    reqs = []
+    for k, sp in zip(kinds, spec):
+        if k == 1:
+            reqs.append((1, (comp(sp[0]), sp[1])))
+        elif k == 2:
+            reqs.append((2, comp(sp)))
+        else:
+            l1, l2, l3, l4 = sp
+            reqs.append((3, [(0, comp(l1), 1), (0, comp(f"{l2}.{l3}*"), 2), (1, comp(f"{l4}*"), 2)]))
+    m = len(reqs)
+    horizon = args.serve_seconds + args.drain
+    # warm-up of both paths (not timed)
+    for k, p in reqs[:64]:
+        if k == 1:
+            rpq.run_rpq(ctx, g, p[0], [p[1]], flags=rpq.RPQ_COUNT_ONLY).free()
+
+    # ---- served -------------------------------------------------------------
+    sampler = ClockSampler(0)
+    sampler.start()
+    server = rpq.Server(ctx, g, max_batch=4096)
+    tickets = [0] * m
+    t0 = time.perf_counter()
+    for i, (k, p) in enumerate(reqs):
+        d = t_arr[i] - (time.perf_counter() - t0)
+        if d > 0:
+            time.sleep(d)
+        if k == 1:
+            tickets[i] = server.submit_single(*p)
+        elif k == 2:
+            tickets[i] = server.submit_allpairs(p)
+        else:
+            tickets[i] = server.submit_crpq(3, p)
+    submit_lag = (time.perf_counter() - t0) - float(t_arr[-1]) if m else 0.0
+    deadline = t0 + horizon
+    s_lat = [0.0] * m
+    s_stat = [1] * m
+    s_val = [None] * m
+    pending = []
+    for i in range(m):
+        try:
+            rep = server.wait(tickets[i], timeout_s=max(0.0, deadline - time.perf_counter()))
+        except rpq.RPQError:
+            pending.append(i)
+            continue
+        s_lat[i], s_stat[i] = rep["latency_ms"], rep["status"]
+        s_val[i] = (rep["count"], rep["digest_sum"], rep["digest_xor"])
+    server.cancel()
+    for i in pending:
+        rep = server.wait(tickets[i], timeout_s=-1)
+        s_stat[i] = rep["status"] if rep["status"] != 0 or rep["latency_ms"] > horizon * 1000 else 0
+        s_lat[i] = rep["latency_ms"]
+        if s_stat[i] == 0:
+            s_val[i] = (rep["count"], rep["digest_sum"], rep["digest_xor"])
+    batches, carried = server.stats()
+    server.close()
+    served_wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    # a request counts as completed only if it was done within the horizon
+    for i in range(m):
+        if s_stat[i] == 0 and s_lat[i] / 1000.0 + float(t_arr[i]) > horizon:
+            s_stat[i] = 1
+
+    # ---- plain FIFO -----------------------------------------------------------
+    f_lat = [0.0] * m
+    f_stat = [1] * m
+    f_val = [None] * m
+    SL = 4096
+    t0 = time.perf_counter()
+    deadline = t0 + horizon
+    for i, (k, p) in enumerate(reqs):
+        d = t_arr[i] - (time.perf_counter() - t0)
+        if d > 0:
+            time.sleep(d)
+        if time.perf_counter() >= deadline:
+            break
+        cnt = dsum = dxor = 0
+        ok = True
+        if k == 1:
+            r = rpq.run_rpq(ctx, g, p[0], [p[1]], flags=rpq.RPQ_COUNT_ONLY)
+            cnt, _, dsum, dxor = rpq.result_info(r)
+            r.free()
+        else:
+            for b in range(0, n, SL):
+                if time.perf_counter() >= deadline:
+                    ok = False
+                    break
+                if k == 2:
+                    r = rpq.run_rpq_range(ctx, g, p, b, min(n, b + SL), rpq.RPQ_COUNT_ONLY)
+                else:
+                    r = rpq.run_crpq(ctx, g, 3, p, restrict0=np.arange(b, min(n, b + SL), dtype=np.uint32),
+                                     flags=rpq.RPQ_COUNT_ONLY)
+                c, _, hs, hx = rpq.result_info(r)
+                r.free()
+                cnt += c
+                dsum = (dsum + hs) & 0xFFFFFFFFFFFFFFFF
+                dxor ^= hx
+        done = time.perf_counter()
+        if ok and done <= deadline:
+            f_stat[i] = 0
+            f_lat[i] = (done - (t0 + float(t_arr[i]))) * 1000.0
+            f_val[i] = (cnt, dsum, dxor)
+    fifo_wall = time.perf_counter() - t0
+
+    both = [i for i in range(m) if s_stat[i] == 0 and f_stat[i] == 0]
+    agree = sum(1 for i in both if s_val[i] == f_val[i])
+    served = _class_summary(kinds, s_lat, s_stat, horizon)
+    fifo = _class_summary(kinds, f_lat, f_stat, horizon)
+    s_done = sum(1 for x in s_stat if x == 0)
+    f_done = sum(1 for x in f_stat if x == 0)
+
+    def ratio(a, b):
+        return None if a is None or b is None or b == 0 else a / b
+
+    out = {
+        "metric": "served_requests_per_s", "value": s_done / horizon, "unit": "requests/s", "n_gpus": 1,
+        "steps": 1, "warmup": 1, "ms_per_step": horizon * 1000.0, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"rmat{scale}-served-mix", "vertices": n, "generated_edges": 16 * n, "labels": L,
+                   "zipf_s": 1.2, "rate_per_s": args.rate, "arrival_window_s": args.serve_seconds,
+                   "drain_s": args.drain, "mix": {"single": 0.80, "allpairs": 0.15, "crpq": 0.05},
+                   "bulk_labels": "Zipf tail, ranks 9-16", "generation_s": round(gen_s, 1)},
+        "offered": m, "served": served, "fifo": fifo,
+        "fifo_requests_per_s": f_done / horizon,
+        "single_p99_fifo_over_served": ratio(fifo["single"]["p99_ms"], served["single"]["p99_ms"]),
+        "completed_ratio_served_over_fifo": ratio(s_done, f_done),
+        "batches": batches, "batched_singles": carried, "submit_lag_s": round(submit_lag, 4),
+        "equal_results": {"compared": len(both), "agree": agree},
+        "wall_s": {"served": round(served_wall, 2), "fifo": round(fifo_wall, 2)},
+        "clocks": clocks,
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -478,6 +678,8 @@ def main():
         return bench_batch(args)
     if args.workload == "crpq":
         return bench_crpq(args)
+    if args.workload == "serve":
+        return bench_serve(args)
     return ours(args, rank, world, local_rank)
 
 

@@ -58,6 +58,7 @@ extern "C" {
 #define RPQ_ERR_CUDA -6          /* a CUDA runtime call failed               */
 #define RPQ_ERR_TIMEOUT -7       /* a device-side wait ran out of time       */
 #define RPQ_ERR_NO_DEVICE -8     /* context has no GPU (host-only context)   */
+#define RPQ_ERR_CANCELLED -9     /* server request cancelled before it ended */
 
 /* ---- limits ------------------------------------------------------------- */
 #define RPQ_MAX_LABELS 64      /* edge labels per graph                      */
@@ -71,6 +72,8 @@ extern "C" {
 #define RPQ_MATERIALIZE 0x1u   /* keep result rows on the device (fetch_pairs) */
 #define RPQ_COUNT_ONLY 0x2u    /* count rows and digest them; keep no rows    */
 #define RPQ_REVERSE 0x4u       /* evaluate from the target end (see run_rpq)  */
+#define RPQ_PER_QUERY 0x8u     /* run_rpq_batch: a row count and digest per
+                                  query (result_query_stats); no rows kept    */
 #define RPQ_FORCE_PUSH 0x100u  /* every level expands top-down (testing)      */
 #define RPQ_FORCE_PULL 0x200u  /* every level expands bottom-up (testing)     */
 
@@ -112,7 +115,9 @@ int rpq_set_stream(rpq_ctx *ctx, void *cuda_stream);
  *                  occupy (default 1; 0.5 lets two contexts' searches run
  *                  side by side)
  *   "max_groups"   lane groups (256 start vertices each) per launch, 1 .. 16
- *   "time_limit_s" bound on each device-side wait (default 20 s) */
+ *   "time_limit_s" bound on each device-side wait (default 20 s)
+ *   "batch_evict"  run_rpq_batch with RPQ_PER_QUERY: product vertices after
+ *                  which a query leaves the shared launch (0: never) */
 int rpq_set_option(rpq_ctx *ctx, const char *name, double value);
 
 /* ---- graph store (Section 2.1 data graph; Section 2.4 keeps one grid per
@@ -190,16 +195,24 @@ int run_rpq_range(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, uint32_t
  * do not fit the device together).  Rows are (i, y) for every y with
  * sources[i] -rho_i-> y, sorted by i then y; arity 2.  The digest of
  * result_info is taken over these (i, y) rows.  flags: RPQ_MATERIALIZE or
- * RPQ_COUNT_ONLY.  Block size and queries per launch come from the last
- * rpq_autotune_batch on the context (defaults otherwise).
+ * RPQ_COUNT_ONLY, or RPQ_PER_QUERY: every query's own rows (sources[i], y)
+ * are counted and digested as run_rpq(queries[i], {sources[i]}) would report
+ * them (result_query_stats), and result_info totals those summaries.  In
+ * that mode a query whose product graph grows past a threshold (option
+ * "batch_evict", product vertices; default 65,536) leaves the shared launch,
+ * and such queries are then evaluated together by the multi-source engine,
+ * one bit-sliced traversal per distinct automaton over their distinct start
+ * vertices.  Block size, queries per launch and the threshold come from the
+ * last rpq_autotune_batch on the context (defaults otherwise).
  * Errors: INVALID_ARG, OUT_OF_BUDGET, CUDA, TIMEOUT. */
 int run_rpq_batch(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_queries, const rpq_query *const *queries,
                   const uint32_t *sources, uint32_t flags, rpq_result **out);
 
-/* Times run_rpq_batch (count only) on the given batch for each candidate
- * block size (128, 256, 512 threads) and queries-per-launch (1024, 2048,
- * 4096, capped by n_queries), keeps the fastest on the context for later
- * run_rpq_batch calls and reports it (out pointers may be NULL).
+/* Times run_rpq_batch (RPQ_PER_QUERY) on a sample of the given batch (its
+ * first 512 queries) for each candidate block size (256, 512 threads) and
+ * eviction threshold (2^12, 2^14, 2^16, 2^18 product vertices), keeps the
+ * fastest on the context for later run_rpq_batch calls and reports it (out
+ * pointers may be NULL; queries per launch is reported as set).
  * Errors: as run_rpq_batch. */
 int rpq_autotune_batch(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_queries, const rpq_query *const *queries,
                        const uint32_t *sources, uint32_t *threads_out, uint32_t *queries_per_launch_out);
@@ -303,6 +316,12 @@ int rpq_server_submit(rpq_server *s, const rpq_request *req, uint64_t *ticket);
 int rpq_server_wait(rpq_server *s, uint64_t ticket, double timeout_s, rpq_reply *reply);
 /* Batched launches so far and the single-source requests they carried. */
 int rpq_server_stats(rpq_server *s, uint64_t *batches, uint64_t *batched_requests);
+/* Cancels every request not yet done: queued ones complete at once, and the
+ * all-pairs request or CRPQ in service stops before its next launch (next
+ * slice of start vertices, next batch of variable-0 values), all with status
+ * RPQ_ERR_CANCELLED.  A single-source batch already on the device runs to its
+ * end and keeps its replies.  The server stays usable. */
+int rpq_server_cancel(rpq_server *s);
 /* Finishes the queued requests, stops the workers and releases the server. */
 void rpq_server_destroy(rpq_server *s);
 
@@ -348,6 +367,44 @@ typedef struct {
 } rpq_stats;
 
 int result_stats(const rpq_result *r, rpq_stats *out);
+/* Row count and digest of query i of a run_rpq_batch result made with
+ * RPQ_PER_QUERY (INVALID_ARG otherwise or when i is out of range). */
+int result_query_stats(const rpq_result *r, uint32_t i, uint64_t *count, uint64_t *digest_sum, uint64_t *digest_xor);
+
+/* ---- streamed materialization ------------------------------------------- */
+/* The rows of rho from start vertices [src_begin, src_end), delivered to the
+ * host while the device keeps exploring: the start vertices run in batches of
+ * one traversal launch (4,096 sources), and the rows of a finished batch are
+ * copied into pinned host memory on a copy stream of the library's own while
+ * the next batch's traversal runs -- the batch-wise transfer of results to the
+ * host that Section 5 of the paper describes, here with the rows of a block in
+ * compressed form (one 4-byte destination per row).  Rows arrive in the order
+ * run_rpq_range would list them (ascending (src, dst)).  flags: 0 or
+ * RPQ_REVERSE.  The context serves only this stream until rpq_stream_close
+ * (the library runs it from two threads of its own); the graph and query must
+ * outlive the stream.  Device memory held by rows not yet copied is bounded by
+ * three batches; host memory is three pinned slots of 256 MiB. */
+typedef struct rpq_stream rpq_stream;
+
+typedef struct {
+  uint32_t n_sources;        /* start vertices with rows in this block        */
+  const uint32_t *sources;   /* [n_sources], ascending                        */
+  const uint64_t *offsets;   /* [n_sources + 1]: rows of sources[i] are
+                                dst[offsets[i] .. offsets[i + 1])             */
+  const uint32_t *dst;       /* destinations, ascending per source            */
+  uint64_t n_rows;           /* rows in this block; 0 marks the end           */
+} rpq_row_block;
+
+int rpq_stream_open(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, uint32_t src_begin, uint32_t src_end,
+                    uint32_t flags, rpq_stream **out);
+/* Fills *block with the next block of rows.  Its arrays belong to the stream
+ * and stay valid until the next rpq_stream_next or rpq_stream_close on it.
+ * n_rows = 0 at the end; a failure of the evaluation is returned here (after
+ * the blocks that completed before it). */
+int rpq_stream_next(rpq_stream *s, rpq_row_block *block);
+/* Totals over the batches evaluated so far: rows, row digest, counters. */
+int rpq_stream_info(rpq_stream *s, uint64_t *rows, uint64_t *digest_sum, uint64_t *digest_xor, rpq_stats *stats);
+void rpq_stream_close(rpq_stream *s);
 
 /* Copies rows [offset, offset + max_rows) (clipped to the row count) into
  * host memory out[arity * k], k rows, and stores k in *n_rows.

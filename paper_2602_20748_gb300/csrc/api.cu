@@ -2,6 +2,7 @@
 // budget, graph loading, query compilation, batched evaluation driving the
 // traversal and emission kernels, results and fetch.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -40,6 +41,7 @@ struct Workspace {
 struct rpq_ctx {
   int device = -1;
   cudaStream_t stream = nullptr;
+  cudaMemPool_t pool = nullptr;  // the context's own pool: freed blocks stay reserved for reuse
   uint64_t budget = 0;
   uint64_t used = 0;
   std::string err;
@@ -57,6 +59,7 @@ struct rpq_ctx {
   uint64_t spill_cap = SPILL_CAP;  // long-row chunks per level (RPQ_SPILL_CAP lowers it)
   double grid_share = 1.0;         // fraction of the SMs persistent grids use
   rpq::BatchTuning batch = rpq::batch_default_tuning();  // run_rpq_batch tunables
+  std::atomic<int> cancel{0};  // set by a server to stop the request in service
   int live = 0;          // graphs and results not yet freed
   bool closing = false;  // rpq_destroy was called while handles were live
 };
@@ -94,6 +97,7 @@ struct rpq_result {
   u32 *tuples = nullptr;  // CRPQ rows, arity values each
   uint64_t tuple_bytes = 0;
   rpq_stats stats;
+  std::vector<uint64_t> qstats;  // run_rpq_batch with RPQ_PER_QUERY: 3 values per query
 };
 
 namespace {
@@ -119,10 +123,11 @@ int dev_alloc(rpq_ctx *ctx, void **p, uint64_t bytes) {
     return set_err(ctx, RPQ_ERR_OUT_OF_BUDGET,
                    "device memory budget exceeded (" + std::to_string(ctx->used + bytes) + " > " +
                        std::to_string(ctx->budget) + " bytes)");
-  cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
+  cudaError_t e = ctx->pool ? cudaMallocFromPoolAsync(p, bytes, ctx->pool, ctx->stream)
+                            : cudaMallocAsync(p, bytes, ctx->stream);
   if (e != cudaSuccess) {
     *p = nullptr;
-    return cuda_err(ctx, e, "cudaMallocAsync");
+    return cuda_err(ctx, e, "stream-ordered allocation");
   }
   ctx->used += bytes;
   return RPQ_OK;
@@ -211,8 +216,10 @@ void free_chunk(rpq_ctx *ctx, Chunk &c) {
 }
 
 // Evaluates one RPQ from the sorted, distinct start vertices `srcs`.
+// With lane_stats (count-only), (rows, digest sum, digest xor) of every
+// source's own rows are stored at lane_stats[3 * i ..] for srcs[i].
 int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::vector<uint32_t> &srcs,
-             uint32_t flags, rpq_result *res) {
+             uint32_t flags, rpq_result *res, std::vector<uint64_t> *lane_stats = nullptr) {
   const DevGraph &g = gr->g;
   const bool reverse = (flags & RPQ_REVERSE) != 0;
   if (reverse && !qr->hq.has_rev)
@@ -220,6 +227,7 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
   const QueryDesc &qd = reverse ? qr->hq.rev : qr->hq.d;
   const uint32_t Q = qd.n_states;
   const bool materialize = (flags & RPQ_MATERIALIZE) != 0;
+  if (lane_stats) lane_stats->assign(3 * srcs.size(), 0);
   res->stats.lane_words = srcs.size() <= 64 ? 1 : 4;
   if (Q == 0 || srcs.empty()) return RPQ_OK;
   const int nw = srcs.size() <= 64 ? 1 : 4;
@@ -253,6 +261,7 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
   std::vector<uint32_t> lanes;
   std::vector<uint64_t> empty;
   for (uint64_t g0 = 0; g0 < groups_total; g0 += G) {
+    if (ctx->cancel.load(std::memory_order_relaxed)) return set_err(ctx, RPQ_ERR_CANCELLED, "cancelled");
     const uint32_t Gb = (uint32_t)std::min<uint64_t>(G, groups_total - g0);
     const uint32_t n_lanes = Gb * K;
     lanes.assign(n_lanes, NO_SOURCE);
@@ -307,6 +316,68 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
     CK(cudaEventRecord(ctx->ev[1], ctx->stream));
     res->stats.launches += 3;
     res->stats.bfs_launches += 1;
+
+    if (lane_stats && !materialize) {
+      // per-lane summaries instead of the count pass
+      u64 *ls = nullptr;
+      int rc2 = dalloc(ctx, &ls, 3ull * n_lanes);
+      if (rc2) return rc2;
+      EmitParams ep;
+      std::memset(&ep, 0, sizeof(ep));
+      ep.vis = w.vis;
+      ep.n = n;
+      ep.G = Gb;
+      ep.Q = Q;
+      ep.final_mask = qd.final_mask;
+      ep.lanesrc = w.lanesrc;
+      ep.segs = segs;
+      CK(cudaMemsetAsync(ls, 0, 24ull * n_lanes, ctx->stream));
+      CK(cudaEventRecord(ctx->ev[2], ctx->stream));
+      CK(launch_emit_lane_stats(nw, ep, ls, ctx->stream));
+      CK(cudaEventRecord(ctx->ev[3], ctx->stream));
+      res->stats.launches += 1;
+      std::vector<uint64_t> hls(3ull * n_lanes);
+      BfsCtl hctl;
+      CK(cudaMemcpyAsync(&hctl, ctx->ctl, sizeof(BfsCtl), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaMemcpyAsync(hls.data(), ls, 24ull * n_lanes, cudaMemcpyDeviceToHost, ctx->stream));
+      dfree(ctx, ls, 3ull * n_lanes);
+      CK(cudaStreamSynchronize(ctx->stream));
+      if (hctl.err) {
+        cudaMemsetAsync(w.fr0, 0, w.vis_words * 8, ctx->stream);
+        cudaMemsetAsync(w.fr1, 0, w.vis_words * 8, ctx->stream);
+        return set_err(ctx, RPQ_ERR_TIMEOUT, "traversal grid barrier wait ran out of time");
+      }
+      for (uint32_t i = 0; i < n_lanes; i++) {
+        const uint64_t si = g0 * K + i;
+        if (si >= srcs.size()) break;
+        (*lane_stats)[3 * si] = hls[3 * i];
+        (*lane_stats)[3 * si + 1] = hls[3 * i + 1];
+        (*lane_stats)[3 * si + 2] = hls[3 * i + 2];
+        res->count += hls[3 * i];
+        res->dsum += hls[3 * i + 1];
+        res->dxor ^= hls[3 * i + 2];
+      }
+      rpq_stats &s = res->stats;
+      s.product_edges += hctl.stats[ST_W];
+      s.product_vertices += hctl.stats[ST_N];
+      s.levels += hctl.levels;
+      s.push_levels += hctl.stats[ST_PUSH_LEVELS];
+      s.pull_levels += hctl.stats[ST_PULL_LEVELS];
+      s.group_edges += hctl.stats[ST_GROUP_EDGES];
+      s.group_rows += hctl.stats[ST_GROUP_ROWS];
+      s.group_vertices += hctl.stats[ST_GROUP_VERTICES];
+      s.pull_edges += hctl.stats[ST_PULL_EDGES];
+      s.pull_vertices += hctl.stats[ST_PULL_VERTICES];
+      s.alg_bytes += hctl.stats[ST_ALG_BYTES];
+      s.lane_groups += Gb;
+      ctx->stamp += (uint32_t)hctl.levels + 2;
+      float ms_bfs = 0, ms_emit = 0;
+      cudaEventElapsedTime(&ms_bfs, ctx->ev[0], ctx->ev[1]);
+      cudaEventElapsedTime(&ms_emit, ctx->ev[2], ctx->ev[3]);
+      s.bfs_ms += ms_bfs;
+      s.emit_ms += ms_emit;
+      continue;
+    }
 
     // emission pass 1: counts and digest
     u32 *cnt = nullptr;
@@ -478,6 +549,24 @@ int rpq_create(rpq_ctx **out, int device, uint64_t mem_budget_bytes, void *cuda_
   }
   c->stream = (cudaStream_t)cuda_stream;
   c->budget = mem_budget_bytes ? mem_budget_bytes : (uint64_t)(free_b * 0.9);
+  {
+    // Per-launch buffers (emission counts, result rows) come and go every
+    // launch; a pool that keeps freed memory mapped makes those allocations
+    // free of page-mapping work.  The pool never holds more than the peak the
+    // budget allowed, and it is released with the context.
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&c->pool, &props) == cudaSuccess) {
+      uint64_t keep = ~0ull;
+      cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    } else {
+      c->pool = nullptr;
+      cudaGetLastError();
+    }
+  }
   for (int i = 0; i < 4; i++) cudaEventCreate(&c->ev[i]);
   if (msbfs_max_blocks(1, BFS_THREADS_HOST, &c->bpsm[0], &c->sms) || msbfs_max_blocks(4, BFS_THREADS_HOST, &c->bpsm[1], &c->sms)) {
     g_create_error = "occupancy query failed";
@@ -515,6 +604,7 @@ void destroy_now(rpq_ctx *c) {
     cudaStreamSynchronize(c->stream);
     for (int i = 0; i < 4; i++)
       if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    if (c->pool) cudaMemPoolDestroy(c->pool);
   }
   delete c;
 }
@@ -556,6 +646,8 @@ int rpq_set_option(rpq_ctx *ctx, const char *name, double value) {
     ctx->max_groups = (uint32_t)value;
   } else if (n == "time_limit_s" && value > 0) {
     ctx->time_limit_ns = (uint64_t)(value * 1e9);
+  } else if (n == "batch_evict" && value >= 0) {
+    ctx->batch.evict_at = (uint64_t)value;
   } else {
     return set_err(ctx, RPQ_ERR_INVALID_ARG, "unknown option or value out of range: " + n);
   }
@@ -757,15 +849,19 @@ int run_rpq_batch(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_queries, const rp
     return set_err(ctx, RPQ_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
   if (!usable(ctx)) return RPQ_ERR_NO_DEVICE;
+  const bool per_query = (flags & RPQ_PER_QUERY) != 0;
+  if (per_query) flags = (flags & ~(uint32_t)RPQ_PER_QUERY) | RPQ_COUNT_ONLY;
   uint32_t mode = flags & (RPQ_MATERIALIZE | RPQ_COUNT_ONLY);
   if ((mode != RPQ_MATERIALIZE && mode != RPQ_COUNT_ONLY) || (flags & ~(RPQ_MATERIALIZE | RPQ_COUNT_ONLY)))
-    return set_err(ctx, RPQ_ERR_INVALID_ARG, "run_rpq_batch takes RPQ_MATERIALIZE or RPQ_COUNT_ONLY only");
+    return set_err(ctx, RPQ_ERR_INVALID_ARG,
+                   "run_rpq_batch takes RPQ_MATERIALIZE, RPQ_COUNT_ONLY or RPQ_PER_QUERY (alone)");
   for (uint32_t i = 0; i < n_queries; i++) {
     if (!queries[i]) return set_err(ctx, RPQ_ERR_INVALID_ARG, "null query");
     if (sources[i] >= g->g.n) return set_err(ctx, RPQ_ERR_INVALID_ARG, "source id out of range");
   }
   const bool materialize = mode == RPQ_MATERIALIZE;
   BatchOut bo;
+  bo.per_query = per_query;
   int rc = n_queries ? batch_run(ctx, g, n_queries, queries, sources, materialize, ctx->batch, &bo) : RPQ_OK;
   auto drop = [&]() {
     for (auto &c : bo.chunks) dev_free(ctx, c.first, c.second * 8);
@@ -794,7 +890,9 @@ int run_rpq_batch(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_queries, const rp
     }
   }
   bo.stats.lane_words = 0;
-  return make_tuple_result(ctx, 2, tuples, bo.count, bo.dsum, bo.dxor, materialize, bo.stats, out);
+  rc = make_tuple_result(ctx, 2, tuples, bo.count, bo.dsum, bo.dxor, materialize, bo.stats, out);
+  if (rc == RPQ_OK && per_query) (*out)->qstats.swap(bo.qstats);
+  return rc;
 }
 
 int rpq_autotune_batch(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_queries, const rpq_query *const *queries,
@@ -803,20 +901,21 @@ int rpq_autotune_batch(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_queries, con
   if (!usable(ctx)) return RPQ_ERR_NO_DEVICE;
   for (uint32_t i = 0; i < n_queries; i++)
     if (!queries[i] || sources[i] >= g->g.n) return set_err(ctx, RPQ_ERR_INVALID_ARG, "bad query or source");
+  const uint32_t sample = std::min<uint32_t>(n_queries, 512);
   BatchTuning best = ctx->batch;
   double best_s = -1;
-  const int threads[] = {128, 256, 512};
-  const uint32_t qpls[] = {1024, 2048, 4096};
+  const int threads[] = {256, 512};
+  const uint64_t evicts[] = {1ull << 12, 1ull << 14, 1ull << 16, 1ull << 18};
   for (int t : threads)
-    for (uint32_t qpl : qpls) {
-      if (qpl > n_queries && qpl != qpls[0] && n_queries) continue;
+    for (uint64_t ev : evicts) {
       BatchTuning cand = ctx->batch;
       cand.threads = t;
-      cand.queries_per_launch = qpl;
+      cand.evict_at = ev;
       BatchOut bo;
+      bo.per_query = true;
       cudaStreamSynchronize(ctx->stream);
       auto t0 = std::chrono::steady_clock::now();
-      int rc = n_queries ? batch_run(ctx, g, n_queries, queries, sources, false, cand, &bo) : RPQ_OK;
+      int rc = sample ? batch_run(ctx, g, sample, queries, sources, false, cand, &bo) : RPQ_OK;
       cudaStreamSynchronize(ctx->stream);
       double s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       if (rc) return rc;
@@ -837,6 +936,14 @@ int result_info(const rpq_result *r, uint64_t *count, uint32_t *arity, uint64_t 
   if (arity) *arity = r->arity;
   if (digest_sum) *digest_sum = r->dsum;
   if (digest_xor) *digest_xor = r->dxor;
+  return RPQ_OK;
+}
+
+int result_query_stats(const rpq_result *r, uint32_t i, uint64_t *count, uint64_t *digest_sum, uint64_t *digest_xor) {
+  if (!r || 3ull * i + 2 >= r->qstats.size()) return RPQ_ERR_INVALID_ARG;
+  if (count) *count = r->qstats[3ull * i];
+  if (digest_sum) *digest_sum = r->qstats[3ull * i + 1];
+  if (digest_xor) *digest_xor = r->qstats[3ull * i + 2];
   return RPQ_OK;
 }
 
@@ -912,6 +1019,9 @@ int ctx_error(rpq_ctx *ctx, int code, const std::string &msg) { return set_err(c
 int ctx_device(rpq_ctx *ctx) { return ctx->device; }
 int ctx_sm_share(rpq_ctx *ctx) { return std::max(1, (int)(ctx->sms * ctx->grid_share)); }
 int ctx_bfs_blocks(rpq_ctx *ctx, int nw) { return ctx_sm_share(ctx) * ctx->bpsm[nw == 1 ? 0 : 1]; }
+bool ctx_trace(rpq_ctx *ctx) { return ctx->trace; }
+bool ctx_cancelled(rpq_ctx *ctx) { return ctx->cancel.load(std::memory_order_relaxed) != 0; }
+void ctx_set_cancel(rpq_ctx *ctx, bool on) { ctx->cancel.store(on ? 1 : 0); }
 float ctx_alpha(rpq_ctx *ctx) { return ctx->alpha; }
 uint64_t ctx_time_limit_ns(rpq_ctx *ctx) { return ctx->time_limit_ns; }
 const DevGraph &graph_dev(const rpq_graph *g) { return g->g; }
@@ -920,12 +1030,15 @@ const HostQuery &query_host(const rpq_query *q) { return q->hq; }
 // Runs an RPQ from the given sorted distinct sources, materialized, and hands
 // back the per-lane CSR chunks (ownership passes to the caller).
 int rpq_rows_for_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, std::vector<uint32_t> &srcs,
-                         bool reverse, std::vector<RowChunk> *chunks, rpq_stats *stats) {
+                         bool reverse, std::vector<RowChunk> *chunks, rpq_stats *stats, uint64_t *dsum,
+                         uint64_t *dxor) {
   rpq_result r;
   r.ctx = ctx;
   r.materialized = true;
   std::memset(&r.stats, 0, sizeof(r.stats));
   int rc = eval_rpq(ctx, g, q, srcs, RPQ_MATERIALIZE | (reverse ? RPQ_REVERSE : 0u), &r);
+  if (dsum) *dsum += r.dsum;
+  if (dxor) *dxor ^= r.dxor;
   if (stats) {
     stats->product_edges += r.stats.product_edges;
     stats->product_vertices += r.stats.product_vertices;
@@ -958,6 +1071,30 @@ int rpq_rows_for_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, s
     }
   }
   r.chunks.clear();
+  return rc;
+}
+
+// Count-only evaluation from sorted distinct sources with each source's own
+// (rows, digest sum, digest xor) in lane_stats[3 * i ..]; counters added to *stats.
+int rpq_lane_stats_for_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q,
+                               const std::vector<uint32_t> &srcs, std::vector<uint64_t> *lane_stats,
+                               rpq_stats *stats) {
+  rpq_result r;
+  r.ctx = ctx;
+  std::memset(&r.stats, 0, sizeof(r.stats));
+  int rc = eval_rpq(ctx, g, q, srcs, RPQ_COUNT_ONLY, &r, lane_stats);
+  if (stats) {
+    stats->product_edges += r.stats.product_edges;
+    stats->product_vertices += r.stats.product_vertices;
+    stats->levels += r.stats.levels;
+    stats->push_levels += r.stats.push_levels;
+    stats->pull_levels += r.stats.pull_levels;
+    stats->bfs_ms += r.stats.bfs_ms;
+    stats->emit_ms += r.stats.emit_ms;
+    stats->bfs_launches += r.stats.bfs_launches;
+    stats->launches += r.stats.launches;
+    stats->alg_bytes += r.stats.alg_bytes;
+  }
   return rc;
 }
 

@@ -13,6 +13,9 @@
 // than SPILL_EDGES are cut into chunks shared by all warps.  Results are the
 // accepting states' bitmaps, emitted as (query index, vertex) rows.
 #include <algorithm>
+#include <map>
+#include <string>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -52,6 +55,11 @@ struct BatchParams {
   BfsCtl *ctl;
   unsigned nblocks;
   u64 time_limit_ns;
+  // per-query accounting and eviction (qn/qw may be null: no eviction)
+  unsigned long long *qn;  // product vertices found per query
+  unsigned long long *qw;  // product edges per query (W)
+  u32 *evicted;            // 1 = query left the batch (too large)
+  u64 evict_at;            // evict a query once qn exceeds this (0: never)
 };
 
 __device__ __forceinline__ u64 bentry(u32 i, u32 q, u32 v) { return ((u64)i << 37) | ((u64)q << 32) | v; }
@@ -157,8 +165,13 @@ __device__ void bseed(const BatchParams &p, u64 *W, u64 *N) {
       s = p.srcs[i];
       take = bvisit(p, (u32)i, 0, s);
       if (take) {
-        *W += bdegsum(p, p.qd[i], 0, s);
+        const u32 d = bdegsum(p, p.qd[i], 0, s);
+        *W += d;
         *N += 1;
+        if (p.qn) {
+          p.qn[i] = 1;
+          p.qw[i] = d;
+        }
       }
     }
     bappend(p, take, bentry((u32)i, 0, s), &p.ctl->n_list[0], p.list0);
@@ -177,7 +190,8 @@ __device__ void bpush(const BatchParams &p, int lp, u32 cur, u32 nxt, u64 n_cur,
     const u64 idx = base + lane;
     const u64 e = idx < n_cur ? __ldcg(&list[idx]) : 0;
     const u32 i = (u32)(e >> 37), q = (u32)(e >> 32) & 31u, v = (u32)e;
-    const bool valid = idx < n_cur && !bad(p, i >= p.nq || v >= p.n, 10);
+    bool valid = idx < n_cur && !bad(p, i >= p.nq || v >= p.n, 10);
+    if (valid && p.evict_at && __ldcg(&p.evicted[i])) valid = false;
     const QueryDesc *qd = p.qd + (valid ? i : 0);
     const u32 t_beg = valid ? qd->out_begin[q] : 0;
     const u32 nt = valid ? qd->out_begin[q + 1] - t_beg : 0;
@@ -252,6 +266,7 @@ __device__ void bspill(const BatchParams &p, int lp, u32 cur, u32 nxt, u64 *edge
     const u64 h = __ldcg(p.spill + 2 * r);
     const u32 len = (u32)__ldcg(p.spill + 2 * r + 1);
     const u32 i = (u32)(h >> 37), q2 = (u32)(h >> 32) & 31u, b = (u32)h;
+    if (p.evict_at && i < p.nq && __ldcg(&p.evicted[i])) continue;  // warp-uniform
     *edges += (lane == 0) ? len : 0;
     for (u32 k0 = 0; k0 < len; k0 += 32) {
       const u32 k = k0 + lane;
@@ -271,12 +286,37 @@ __device__ void bcommit(const BatchParams &p, int lp, u32 nxt, u64 *W, u64 *N) {
   u64 n_next = *(volatile unsigned long long *)&p.ctl->n_list[nxt];
   if (n_next > p.list_cap) n_next = p.list_cap;
   const u64 stride = (u64)gridDim.x * blockDim.x;
-  for (u64 j = (u64)blockIdx.x * blockDim.x + threadIdx.x; j < n_next; j += stride) {
-    const u64 e = __ldcg(&nlist[j]);
-    const u32 i = (u32)(e >> 37), q = (u32)(e >> 32) & 31u, v = (u32)e;
-    if (bad(p, i >= p.nq, 9)) continue;
-    *W += bdegsum(p, p.qd[i], q, v);
-    *N += 1;
+  for (u64 j0 = (u64)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); j0 < n_next; j0 += stride) {
+    const u64 j = j0 + lane_id();
+    bool ok = j < n_next;
+    u32 i = 0;
+    u64 d = 0;
+    if (ok) {
+      const u64 e = __ldcg(&nlist[j]);
+      i = (u32)(e >> 37);
+      const u32 q = (u32)(e >> 32) & 31u, v = (u32)e;
+      ok = !bad(p, i >= p.nq, 9);
+      if (ok) d = bdegsum(p, p.qd[i], q, v);
+    }
+    *W += d;
+    *N += ok ? 1 : 0;
+    if (p.qn) {
+      // per-query counters; the entries of a warp usually share one query
+      const u32 i0 = __shfl_sync(FULL_MASK, i, 0);
+      const bool same = __all_sync(FULL_MASK, !ok || i == i0);
+      if (same) {
+        const u64 dn = warp_sum((u64)(ok ? 1 : 0)), dw = warp_sum(d);
+        if (lane_id() == 0 && dn) {
+          const u64 before = atomicAdd(&p.qn[i0], dn);
+          atomicAdd(&p.qw[i0], dw);
+          if (p.evict_at && before + dn > p.evict_at) p.evicted[i0] = 1u;
+        }
+      } else if (ok) {
+        const u64 before = atomicAdd(&p.qn[i], 1ull);
+        atomicAdd(&p.qw[i], d);
+        if (p.evict_at && before + 1 > p.evict_at) p.evicted[i] = 1u;
+      }
+    }
   }
 }
 
@@ -346,6 +386,7 @@ struct BEmitParams {
   u32 qbase;  // index of this launch's first query in the caller's arrays
   u64 *qstats;      // optional: per query (rows, digest sum, digest xor) over (source, y)
   const u32 *srcs;  // the launch's sources (for qstats)
+  const u32 *evicted;  // optional: queries whose rows are not emitted here
 };
 
 template <bool WRITE>
@@ -353,7 +394,7 @@ __global__ void __launch_bounds__(BEMIT_WORDS) batch_emit(const BEmitParams p) {
   const u32 c = blockIdx.x, i = blockIdx.y;
   const u64 k = (u64)c * BEMIT_WORDS + threadIdx.x;
   u64 r = 0;
-  const u32 fm_all = p.qd[i].final_mask;
+  const u32 fm_all = (p.evicted && p.evicted[i]) ? 0u : p.qd[i].final_mask;
   if (k < p.wps)
     for (u32 fm = fm_all; fm; fm &= fm - 1) r |= __ldcg(p.vis + p.vis_off[i] + (u64)(__ffs(fm) - 1) * p.wps + k);
   const u32 pc = __popcll(r);
@@ -438,7 +479,7 @@ struct DBuf {
 
 }  // namespace
 
-BatchTuning batch_default_tuning() { return BatchTuning{BATCH_THREADS, 4096, 1ull << 28, SPILL_CAP}; }
+BatchTuning batch_default_tuning() { return BatchTuning{BATCH_THREADS, 4096, 1ull << 28, SPILL_CAP, 1ull << 16}; }
 
 // One launch over queries [0, nq) of the arrays; appends rows to `out`.
 static int batch_launch(rpq_ctx *ctx, const rpq_graph *g, uint32_t qbase, uint32_t nq,
@@ -472,8 +513,21 @@ static int batch_launch(rpq_ctx *ctx, const rpq_graph *g, uint32_t qbase, uint32
       (e = cudaMemsetAsync(d_small.p, 0, 32, st)))
     return berr(ctx, e, "batch upload");
 
+  const bool evict = out->per_query && !materialize && tun.evict_at > 0;
+  DBuf<u64> d_qn, d_qw;
+  DBuf<u32> d_ev;
+  if (evict) {
+    if ((rc = d_qn.alloc(ctx, nq)) || (rc = d_qw.alloc(ctx, nq)) || (rc = d_ev.alloc(ctx, nq))) return rc;
+    if ((e = cudaMemsetAsync(d_qn.p, 0, 8ull * nq, st)) || (e = cudaMemsetAsync(d_qw.p, 0, 8ull * nq, st)) ||
+        (e = cudaMemsetAsync(d_ev.p, 0, 4ull * nq, st)))
+      return berr(ctx, e, "batch counters");
+  }
   BatchParams p;
   std::memset(&p, 0, sizeof(p));
+  p.qn = evict ? d_qn.p : nullptr;
+  p.qw = evict ? d_qw.p : nullptr;
+  p.evicted = evict ? d_ev.p : nullptr;
+  p.evict_at = evict ? tun.evict_at : 0;
   p.out_off = dg.out_off;
   p.out_col = dg.out_col;
   p.n = dg.n;
@@ -533,6 +587,7 @@ static int batch_launch(rpq_ctx *ctx, const rpq_graph *g, uint32_t qbase, uint32
   ep.qbase = qbase;
   ep.srcs = d_src.p;
   ep.qstats = nullptr;
+  ep.evicted = evict ? d_ev.p : nullptr;
   DBuf<u64> d_qstats;
   if (out->per_query) {
     if ((rc = d_qstats.alloc(ctx, 3ull * nq))) return rc;
@@ -558,19 +613,52 @@ static int batch_launch(rpq_ctx *ctx, const rpq_graph *g, uint32_t qbase, uint32
   cudaEventDestroy(ev0);
   cudaEventDestroy(ev1);
   if (hctl.err == ERR_LIST_FULL) return RPQ_BATCH_SPLIT;
+  std::vector<u64> hqn, hqw;
+  std::vector<u32> hev;
   if (out->per_query && hctl.err == 0) {
     std::vector<u64> qs(3ull * nq);
     if ((e = cudaMemcpy(qs.data(), d_qstats.p, 24ull * nq, cudaMemcpyDeviceToHost)) != cudaSuccess)
       return berr(ctx, e, "qstats");
     out->qstats.insert(out->qstats.end(), qs.begin(), qs.end());
+    if (evict) {
+      hqn.resize(nq);
+      hqw.resize(nq);
+      hev.resize(nq);
+      if ((e = cudaMemcpy(hqn.data(), d_qn.p, 8ull * nq, cudaMemcpyDeviceToHost)) ||
+          (e = cudaMemcpy(hqw.data(), d_qw.p, 8ull * nq, cudaMemcpyDeviceToHost)) ||
+          (e = cudaMemcpy(hev.data(), d_ev.p, 4ull * nq, cudaMemcpyDeviceToHost)))
+        return berr(ctx, e, "batch counters");
+    }
   }
   if (hctl.err >= ERR_BOUNDS)
     return ctx_error(ctx, RPQ_ERR_CUDA, "batch traversal index check " + std::to_string(hctl.err - ERR_BOUNDS) +
                                             " failed (a device index out of its array; access skipped)");
   if (hctl.err) return ctx_error(ctx, RPQ_ERR_TIMEOUT, "batch traversal grid barrier wait ran out of time");
+  if (ctx_trace(ctx)) {
+    const uint32_t nl = (uint32_t)std::min<u64>(hctl.levels, TRACE_LEVELS);
+    std::fprintf(stderr, "[rpq trace] batch nq=%u threads=%d blocks=%d levels=%llu W=%llu N=%llu %.3f ms\n", nq,
+                 tun.threads, blocks, (unsigned long long)hctl.levels, (unsigned long long)hctl.stats[ST_W],
+                 (unsigned long long)hctl.stats[ST_N], ms);
+    for (uint32_t l = 0; l < nl; l++)
+      std::fprintf(stderr, "[rpq trace]   level %3u n=%10llu %9.3f ms\n", l, (unsigned long long)hctl.trace_n[l],
+                   (hctl.trace_t[l + 1] - hctl.trace_t[l]) * 1e-6);
+  }
   out->stats.bfs_ms += ms;
-  out->stats.product_edges += hctl.stats[ST_W];
-  out->stats.product_vertices += hctl.stats[ST_N];
+  if (evict) {
+    // exact work of the queries that stayed; evicted ones are counted by their
+    // multi-source evaluation
+    for (uint32_t i = 0; i < nq; i++) {
+      if (hev[i]) {
+        out->evicted_idx.push_back(qbase + i);
+        continue;
+      }
+      out->stats.product_edges += hqw[i];
+      out->stats.product_vertices += hqn[i];
+    }
+  } else {
+    out->stats.product_edges += hctl.stats[ST_W];
+    out->stats.product_vertices += hctl.stats[ST_N];
+  }
   out->stats.levels += hctl.levels;
   out->stats.push_levels += hctl.stats[ST_PUSH_LEVELS];
   out->stats.group_edges += hctl.stats[ST_GROUP_EDGES];
@@ -607,6 +695,38 @@ int batch_run(rpq_ctx *ctx, const rpq_graph *g, uint32_t nq, const rpq_query *co
       k = (k + 1) / 2;  // frontier list too small for this many queries at once: halve
     }
     b0 += k;
+  }
+  if (!out->per_query) return RPQ_OK;
+  // Queries that left the batch: one multi-source (bit-sliced) evaluation per
+  // distinct automaton over the distinct start vertices of its queries, with
+  // every start vertex's own row count and digest.
+  std::map<std::string, std::vector<uint32_t>> groups;
+  for (uint32_t i : out->evicted_idx) {
+    const QueryDesc &d = query_host(queries[i]).d;
+    groups[std::string(reinterpret_cast<const char *>(&d), sizeof(d))].push_back(i);
+  }
+  for (auto &kv : groups) {
+    std::vector<uint32_t> srcs;
+    for (uint32_t i : kv.second) srcs.push_back(sources[i]);
+    std::sort(srcs.begin(), srcs.end());
+    srcs.erase(std::unique(srcs.begin(), srcs.end()), srcs.end());
+    std::vector<uint64_t> ls;
+    int rc = rpq_lane_stats_for_sources(ctx, g, queries[kv.second[0]], srcs, &ls, &out->stats);
+    if (rc) return rc;
+    out->regroup_launches++;
+    for (uint32_t i : kv.second) {
+      const size_t k = std::lower_bound(srcs.begin(), srcs.end(), sources[i]) - srcs.begin();
+      for (int c = 0; c < 3; c++) out->qstats[3ull * i + c] = ls[3 * k + c];
+    }
+  }
+  out->evicted += out->evicted_idx.size();
+  // with per-query summaries the totals are theirs: rows and digests of the
+  // (source, y) rows every query would report alone
+  out->count = out->dsum = out->dxor = 0;
+  for (size_t i = 0; 3 * i + 2 < out->qstats.size(); i++) {
+    out->count += out->qstats[3 * i];
+    out->dsum += out->qstats[3 * i + 1];
+    out->dxor ^= out->qstats[3 * i + 2];
   }
   return RPQ_OK;
 }

@@ -17,6 +17,8 @@ struct BatchTuning {
   uint32_t queries_per_launch;  // queries sharing one launch
   uint64_t list_cap;            // frontier list capacity (entries)
   uint64_t spill_cap;           // long-row chunks per level (<= SPILL_CAP)
+  uint64_t evict_at;            // per-query mode: a query with more product vertices leaves the
+                                // batch and is evaluated with the multi-source engine (0: never)
 };
 
 struct BatchOut {
@@ -25,6 +27,9 @@ struct BatchOut {
   std::vector<std::pair<u32 *, uint64_t>> chunks;  // row-major (query, vertex) rows, in order
   bool per_query = false;       // fill qstats: per query (rows, digest sum, digest xor) of its
   std::vector<uint64_t> qstats;  // (source, y) rows, as run_rpq would report them alone
+  uint64_t evicted = 0;          // queries that left the batch for the multi-source engine
+  std::vector<uint32_t> evicted_idx;
+  uint64_t regroup_launches = 0; // multi-source evaluations (one per distinct automaton)
 };
 
 BatchTuning batch_default_tuning();

@@ -635,6 +635,10 @@ int crpq_eval(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_vars, const int32_t *
   }
 
   for (size_t b0 = 0; b0 < first.size() && rc == RPQ_OK; b0 += BATCH0) {
+    if (ctx_cancelled(ctx)) {
+      rc = ctx_error(ctx, RPQ_ERR_CANCELLED, "cancelled");
+      break;
+    }
     uint64_t nb = std::min<size_t>(BATCH0, first.size() - b0);
     Buf<u32> vals;
     if ((rc = vals.alloc(ctx, nb))) break;

@@ -28,12 +28,19 @@ int ctx_device(rpq_ctx *ctx);
 int ctx_bfs_blocks(rpq_ctx *ctx, int nw);
 int ctx_sm_share(rpq_ctx *ctx);  // SMs the context's persistent grids may use
 float ctx_alpha(rpq_ctx *ctx);
+bool ctx_trace(rpq_ctx *ctx);              // per-level trace printing (RPQ_TRACE=1)
+bool ctx_cancelled(rpq_ctx *ctx);          // a server asked the request in service to stop
+void ctx_set_cancel(rpq_ctx *ctx, bool on);
 uint64_t ctx_time_limit_ns(rpq_ctx *ctx);
 const DevGraph &graph_dev(const rpq_graph *g);
 const HostQuery &query_host(const rpq_query *q);
 int rpq_rows_for_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, std::vector<uint32_t> &srcs,
-                         bool reverse, std::vector<RowChunk> *chunks, rpq_stats *stats);
+                         bool reverse, std::vector<RowChunk> *chunks, rpq_stats *stats, uint64_t *dsum = nullptr,
+                         uint64_t *dxor = nullptr);
 void free_row_chunk(rpq_ctx *ctx, RowChunk &c);
+int rpq_lane_stats_for_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q,
+                               const std::vector<uint32_t> &srcs, std::vector<uint64_t> *lane_stats,
+                               rpq_stats *stats);
 int make_tuple_result(rpq_ctx *ctx, uint32_t arity, u32 *tuples, uint64_t rows, uint64_t dsum, uint64_t dxor,
                       bool materialized, const rpq_stats &stats, rpq_result **out);
 

@@ -2,15 +2,18 @@
 //
 // After the search, the result set of start vertex s (Definition 1) is the
 // set of v with some accepting state q such that s's lane is set in the
-// visited word of (group g, state q, vertex v).  For lane group g, OR the accepting states' words into a
-// K-bit result word per vertex.  A block owns a segment of EMIT_SEG vertices
-// of one group; warp c handles lane column c (32 lanes) and walks the segment
-// in 32-vertex tiles: the 32 x 32 bit tile is transposed with 32 ballots so
-// that thread j holds the 32 membership bits of lane 32c + j, in vertex
-// order.  Pass 1 counts per (lane, segment) and folds the row digest; an
-// exclusive scan over the counts laid out [lane][segment] gives every row its
-// output position directly (lanes are in source order, segments in vertex
-// order), and pass 2 writes the destinations.
+// visited word of (group g, state q, vertex v).  For lane group g, OR the
+// accepting states' words into a K-bit result word per vertex.  A block owns
+// a segment of EMIT_SEG vertices of one group; warp c handles lane column c
+// (32 lanes) and walks the segment in 32-vertex tiles, thread i holding the
+// 32 lane bits of vertex w0 + i.  For every lane j with a bit in the tile, a
+// ballot over bit j gives the tile's members of lane j's row in vertex order:
+// the count pass adds its popcount to lane j's (lane, segment) count, and the
+// write pass stores the members at consecutive positions of lane j's row (one
+// coalesced store per lane and tile).  An exclusive scan over the counts laid
+// out [lane][segment] gives every row its output position directly (lanes
+// are in source order, segments in vertex order).  The row digest is folded
+// by the thread that holds the member.
 #include "device_common.cuh"
 #include "rpq_internal.h"
 
@@ -18,15 +21,18 @@ namespace rpq {
 
 template <int NW, bool WRITE, bool DIGEST>
 __global__ void emit_kernel(const EmitParams p) {
-  const u32 seg = blockIdx.x, g = blockIdx.y;
+  // groups of one segment are adjacent blocks, so they read the same
+  // visited lines close together in time
+  const u32 g = blockIdx.x % p.G, seg = blockIdx.x / p.G;
   const u32 col = threadIdx.x >> 5, lane = lane_id();
   const u32 K = 64 * NW;
   const u64 glane = (u64)g * K + col * 32 + lane;
   const u32 src = p.lanesrc[glane];
   const u32 valid_cols = __ballot_sync(FULL_MASK, src != NO_SOURCE);
   const u32 *vis32 = reinterpret_cast<const u32 *>(p.vis);
+  const u32 lt = (1u << lane) - 1u;
   u64 cnt = 0, hsum = 0, hxor = 0;
-  u64 pos = 0;
+  u64 pos = 0;  // lane `lane`'s next output position (write pass)
   if (WRITE) pos = p.off[glane * p.segs + seg];
   const u32 w_begin = seg * EMIT_SEG;
   for (u32 t = 0; t < EMIT_TILES; t++) {
@@ -42,23 +48,27 @@ __global__ void emit_kernel(const EmitParams p) {
       }
     }
     x &= valid_cols;
-    if (!__any_sync(FULL_MASK, x)) continue;  // no result in this 32 x 32 tile
-    // transpose the 32 x 32 tile: thread j receives bit k = (w0 + k in lane 32*col + j)
-    u32 mine = 0;
-#pragma unroll
-    for (int j = 0; j < 32; j++) {
-      u32 b = __ballot_sync(FULL_MASK, (x >> j) & 1u);
-      if (lane == (u32)j) mine = b;
-    }
-    if (!mine) continue;
-    if (!WRITE) cnt += __popc(mine);
-    for (u32 b = mine; (WRITE || DIGEST) && b; b &= b - 1) {
-      const u32 y = w0 + (__ffs(b) - 1);
-      if (WRITE) p.dst[pos++] = y;
+    for (u32 rows = __reduce_or_sync(FULL_MASK, x); rows; rows &= rows - 1) {
+      const u32 j = __ffs(rows) - 1;
+      const u32 mine = (x >> j) & 1u;
+      const u32 m = __ballot_sync(FULL_MASK, mine);
+      if (WRITE) {
+        const u64 base = __shfl_sync(FULL_MASK, pos, j);
+        if (mine) p.dst[base + __popc(m & lt)] = w;
+      }
       if (DIGEST) {
-        u64 h = splitmix64(((u64)src << 32) | (u64)y);
-        hsum += h;
-        hxor ^= h;
+        const u32 sj = __shfl_sync(FULL_MASK, src, j);
+        if (mine) {
+          u64 h = splitmix64(((u64)sj << 32) | (u64)w);
+          hsum += h;
+          hxor ^= h;
+        }
+      }
+      if (lane == j) {
+        if (WRITE)
+          pos += __popc(m);
+        else
+          cnt += __popc(m);
       }
     }
   }
@@ -77,7 +87,7 @@ __global__ void emit_kernel(const EmitParams p) {
 // writes the destinations.  The row digest is folded in the pass given
 // digest = true (the write pass when rows are kept, else the count pass).
 cudaError_t launch_emit(int nw, bool write, bool digest, const EmitParams &p, cudaStream_t st) {
-  dim3 grid(p.segs, p.G);
+  const unsigned grid = p.segs * p.G;
   const int threads = nw == 1 ? 64 : 256;
   if (nw == 1) {
     if (write)
@@ -94,6 +104,65 @@ cudaError_t launch_emit(int nw, bool write, bool digest, const EmitParams &p, cu
       digest ? emit_kernel<4, false, true><<<grid, threads, 0, st>>>(p)
              : emit_kernel<4, false, false><<<grid, threads, 0, st>>>(p);
   }
+  return cudaGetLastError();
+}
+
+// Per-lane statistics (count, digest) of every lane's rows, for callers that
+// need each start vertex's result summary separately.  Same tile walk as the
+// count pass; the 32 x 32 tile is transposed with 32 ballots so that thread j
+// holds lane 32c + j's members and folds its own digest; one set of atomics
+// per lane and segment.
+template <int NW>
+__global__ void emit_lane_stats_kernel(const EmitParams p, u64 *__restrict__ lane_stats) {
+  const u32 g = blockIdx.x % p.G, seg = blockIdx.x / p.G;
+  const u32 col = threadIdx.x >> 5, lane = lane_id();
+  const u32 K = 64 * NW;
+  const u64 glane = (u64)g * K + col * 32 + lane;
+  const u32 src = p.lanesrc[glane];
+  const u32 valid_cols = __ballot_sync(FULL_MASK, src != NO_SOURCE);
+  const u32 *vis32 = reinterpret_cast<const u32 *>(p.vis);
+  u64 cnt = 0, hsum = 0, hxor = 0;
+  const u32 w_begin = seg * EMIT_SEG;
+  for (u32 t = 0; t < EMIT_TILES; t++) {
+    const u32 w0 = w_begin + t * 32;
+    if (w0 >= p.n) break;
+    const u32 w = w0 + lane;
+    u32 x = 0;
+    if (w < p.n) {
+      for (u32 fm = p.final_mask; fm; fm &= fm - 1) {
+        u32 q = __ffs(fm) - 1;
+        u64 word = (((u64)q * p.n + w) * p.G + g) * NW;
+        x |= __ldcg(vis32 + word * 2 + col);
+      }
+    }
+    x &= valid_cols;
+    if (!__any_sync(FULL_MASK, x)) continue;
+    u32 mine = 0;
+#pragma unroll
+    for (int j = 0; j < 32; j++) {
+      u32 b = __ballot_sync(FULL_MASK, (x >> j) & 1u);
+      if (lane == (u32)j) mine = b;
+    }
+    cnt += __popc(mine);
+    for (u32 b = mine; b; b &= b - 1) {
+      u64 h = splitmix64(((u64)src << 32) | (u64)(w0 + __ffs(b) - 1));
+      hsum += h;
+      hxor ^= h;
+    }
+  }
+  if (cnt) {
+    atomicAdd(&lane_stats[3 * glane], cnt);
+    atomicAdd(&lane_stats[3 * glane + 1], hsum);
+    atomicXor(&lane_stats[3 * glane + 2], hxor);
+  }
+}
+
+cudaError_t launch_emit_lane_stats(int nw, const EmitParams &p, unsigned long long *lane_stats, cudaStream_t st) {
+  const unsigned grid = p.segs * p.G;
+  if (nw == 1)
+    emit_lane_stats_kernel<1><<<grid, 64, 0, st>>>(p, lane_stats);
+  else
+    emit_lane_stats_kernel<4><<<grid, 256, 0, st>>>(p, lane_stats);
   return cudaGetLastError();
 }
 

@@ -444,10 +444,13 @@ __device__ __forceinline__ void pull_finish(const BfsParams &p, u64 *FB, u64 *nl
   warp_append(take, ((u64)(my_g * p.Q + q2) << 32) | w, &p.ctl->n_list[nxt], nlist);
 }
 
-// Bottom-up expansion.  Light rows: a warp per vertex, all groups at once
-// (lane L holds words [L*PER, L*PER+PER) of the vertex's G*NW words).  Long
-// rows: their precomputed chunks, a warp per chunk, taken dynamically over
-// the (target state, transition group) pairs whose source states are active.
+// Bottom-up expansion.  Light rows: one vertex per sub-warp of SW lanes (the
+// smallest power of two holding the vertex's G * NW words at PER words per
+// lane), all groups at once, so a warp covers 32 / SW vertices (32 for a
+// single start vertex).  Long rows: their precomputed chunks, a warp per
+// chunk taken dynamically over the (target state, transition group) pairs
+// whose source states are active; the sub-warps split the chunk's edges and
+// OR their gathers together.
 template <int NW>
 __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 active, u32 stamp, u64 *stat) {
   constexpr int PER = (NW >= 2) ? 2 : 1;
@@ -457,8 +460,13 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
   const u32 n = p.n, Q = p.Q, n1 = p.n + 1;
   const u32 lane = lane_id();
   const u32 lanes_used = p.G * NW / PER;
-  const bool lane_on = lane < lanes_used;
-  const u32 lane_off = lane * PER;
+  u32 SW = 1;
+  while (SW < lanes_used) SW <<= 1;
+  const u32 VPW = 32 / SW;  // vertices per warp
+  const u32 sg = lane / SW, li = lane % SW;
+  const u32 sg_mask = SW == 32 ? FULL_MASK : (((1u << SW) - 1u) << (sg * SW));
+  const bool lane_on = li < lanes_used;
+  const u32 lane_off = li * PER;
   const u32 my_g = lane_on ? lane_off / NW : 0;
   const u64 wpv = (u64)p.G * NW;
   const u64 warp = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -467,45 +475,50 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
   const u64 gword = 8ull * NW * p.G;  // bytes of the G words of one (state, vertex)
   u64 edges = 0, words = 0, bytes = 0;
 
-  for (u64 w64 = warp; w64 < n; w64 += n_warps) {
-    const u32 w = (u32)w64;
+  for (u64 b64 = warp * VPW; b64 < n; b64 += n_warps * VPW) {
+    const u64 w64 = b64 + sg;
+    const bool wv = w64 < n;
+    const u32 w = wv ? (u32)w64 : 0;
     for (u32 q2 = 0; q2 < Q; q2++) {
       const u32 gb = p.q.in_begin[q2], ge = p.q.in_begin[q2 + 1];
       bool any = false;
-      for (u32 j = gb; j < ge && !any; j++) {
+      for (u32 j = gb; j < ge && !any && wv; j++) {
         const u32 l = p.q.in_label[j];
         if (!(p.q.in_from[j] & active) || l >= p.L) continue;
         const u32 *off = p.in_off + (u64)l * n1 + w;
         const u32 len = __ldg(off + 1) - __ldg(off);
         any = len > 0 && (len < HEAVY_ROW || !chunked);
       }
-      if (!any) continue;
       const u64 base = ((u64)q2 * n + w) * wpv + lane_off;
       u64 vis[PER];
       bool full = true;
 #pragma unroll
       for (int k = 0; k < PER; k++) {
-        vis[k] = lane_on ? __ldcg(p.vis + base + k) : ~0ull;
+        vis[k] = (lane_on && any) ? __ldcg(p.vis + base + k) : ~0ull;
         full &= vis[k] == ~0ull;
       }
-      if (__all_sync(FULL_MASK, full)) continue;
+      const u32 fb = __ballot_sync(FULL_MASK, full);
+      const bool work = any && (fb & sg_mask) != sg_mask;
+      if (!__any_sync(FULL_MASK, work)) continue;
       u64 acc[PER];
 #pragma unroll
       for (int k = 0; k < PER; k++) acc[k] = 0;
-      for (u32 j = gb; j < ge; j++) {
-        const u32 l = p.q.in_label[j];
-        const u32 from = p.q.in_from[j] & active;
-        if (!from || l >= p.L) continue;
-        const u32 *off = p.in_off + (u64)l * n1 + w;
-        const u32 beg = __ldg(off), end = __ldg(off + 1);
-        if (end - beg >= HEAVY_ROW && chunked) continue;
-        edges += (lane == 0) ? (end - beg) : 0;
-        bytes += (lane == 0) ? 8 + (u64)(end - beg) * (4 + gword * __popc(from)) : 0;
-        gather_row<NW, PER>(p, F, from, beg, end, lane_off, lane_on, acc);
+      if (work) {
+        for (u32 j = gb; j < ge; j++) {
+          const u32 l = p.q.in_label[j];
+          const u32 from = p.q.in_from[j] & active;
+          if (!from || l >= p.L) continue;
+          const u32 *off = p.in_off + (u64)l * n1 + w;
+          const u32 beg = __ldg(off), end = __ldg(off + 1);
+          if (end - beg >= HEAVY_ROW && chunked) continue;
+          edges += (li == 0) ? (end - beg) : 0;
+          bytes += (li == 0) ? 8 + (u64)(end - beg) * (4 + gword * __popc(from)) : 0;
+          gather_row<NW, PER>(p, F, from, beg, end, lane_off, lane_on, acc);
+        }
+        words += (li == 0);
+        bytes += (li == 0) ? gword : 0;
       }
-      words += (lane == 0);
-      bytes += (lane == 0) ? gword : 0;
-      pull_finish<NW, PER>(p, FB, nlist, nxt, q2, w, stamp, lane, lane_on, my_g, vis, acc);
+      pull_finish<NW, PER>(p, FB, nlist, nxt, q2, w, stamp, li, lane_on && work, my_g, vis, acc);
     }
   }
 
@@ -547,11 +560,18 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
       u64 acc[PER];
 #pragma unroll
       for (int k = 0; k < PER; k++) acc[k] = 0;
-      edges += (lane == 0) ? (end - beg) : 0;
-      bytes += (lane == 0) ? 12 + gword + (u64)(end - beg) * (4 + gword * __popc(from)) : 0;
-      gather_row<NW, PER>(p, F, from, beg, end, lane_off, lane_on, acc);
+      // the sub-warps take consecutive slices of the chunk's edges
+      const u32 len = end - beg, per = (len + VPW - 1) / VPW;
+      const u32 sb = beg + min(len, sg * per), se = beg + min(len, (sg + 1) * per);
+      gather_row<NW, PER>(p, F, from, sb, se, lane_off, lane_on, acc);
+      for (u32 o = SW; o < 32; o <<= 1) {
+#pragma unroll
+        for (int k = 0; k < PER; k++) acc[k] |= __shfl_xor_sync(FULL_MASK, acc[k], o);
+      }
+      edges += (lane == 0) ? len : 0;
+      bytes += (lane == 0) ? 12 + gword + (u64)len * (4 + gword * __popc(from)) : 0;
       words += (lane == 0);
-      pull_finish<NW, PER>(p, FB, nlist, nxt, q2s, w, stamp, lane, lane_on, my_g, vis, acc);
+      pull_finish<NW, PER>(p, FB, nlist, nxt, q2s, w, stamp, li, lane_on && sg == 0, my_g, vis, acc);
     }
   }
   stat[ST_PULL_EDGES] += warp_sum(edges);
@@ -640,7 +660,7 @@ __device__ double pull_bytes(const BfsParams &p, u32 active) {
 }
 
 template <int NW>
-__global__ void __launch_bounds__(BFS_THREADS) msbfs_kernel(const __grid_constant__ BfsParams p) {
+__global__ void __launch_bounds__(BFS_THREADS, 4) msbfs_kernel(const __grid_constant__ BfsParams p) {
   // per-warp statistics, summed into the control block at the end
   u64 stat[ST_COUNT];
 #pragma unroll

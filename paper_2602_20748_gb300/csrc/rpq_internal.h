@@ -174,6 +174,10 @@ struct EmitParams {
 constexpr int EMIT_TILES = 32;  // 32-vertex tiles per segment
 constexpr int EMIT_SEG = 32 * EMIT_TILES;
 cudaError_t launch_emit(int nw, bool write, bool digest, const EmitParams &p, cudaStream_t st);
+// Per-lane row count and digest (lane_stats[3 * lane + {0, 1, 2}] = rows,
+// digest sum, digest xor over the lane's (source, y) rows); lane_stats zeroed
+// by the caller.
+cudaError_t launch_emit_lane_stats(int nw, const EmitParams &p, unsigned long long *lane_stats, cudaStream_t st);
 
 // Write pass into interleaved (src, dst) rows of a caller's buffer (NW = 1).
 cudaError_t launch_emit_pairs(const EmitParams &p, uint32_t *out, cudaStream_t st);

@@ -69,6 +69,7 @@ struct rpq_server {
   std::map<uint64_t, std::unique_ptr<Req>> reqs;
   uint64_t next_ticket = 1;
   bool stop = false;
+  std::atomic<uint64_t> cancel_upto{0};  // tickets <= this are cancelled
   std::thread t_single, t_bulk;
   std::atomic<uint64_t> batches{0}, batched_requests{0};
 };
@@ -138,12 +139,17 @@ void bulk_worker(rpq_server *s) {
       if (s->stop && s->bulk.empty()) return;
       r = s->bulk.front();
       s->bulk.pop_front();
+      rpq::ctx_set_cancel(s->ctx_bulk, false);
     }
     r->t_start = Clock::now();
     int rc = RPQ_OK;
     uint64_t count = 0, dsum = 0, dxor = 0;
     if (r->kind == RPQ_REQ_ALLPAIRS) {
       for (uint32_t b = 0; b < dg.n && rc == RPQ_OK; b += s->slice) {
+        if (r->ticket <= s->cancel_upto.load()) {
+          rc = RPQ_ERR_CANCELLED;
+          break;
+        }
         rpq_result *res = nullptr;
         rc = run_rpq_range(s->ctx_bulk, s->g, r->q, b, std::min<uint32_t>(dg.n, b + s->slice), RPQ_COUNT_ONLY, &res);
         if (rc == RPQ_OK) {
@@ -275,6 +281,26 @@ int rpq_server_wait(rpq_server *s, uint64_t ticket, double timeout_s, rpq_reply 
   reply->service_ms = ms_between(r->t_start, r->t_done);
   reply->latency_ms = ms_between(r->t_submit, r->t_done);
   s->reqs.erase(it);
+  return RPQ_OK;
+}
+
+int rpq_server_cancel(rpq_server *s) {
+  if (!s) return RPQ_ERR_INVALID_ARG;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->cancel_upto = s->next_ticket - 1;
+    rpq::ctx_set_cancel(s->ctx_bulk, true);  // the bulk request in service, if any
+    const auto now = Clock::now();
+    for (auto *q : {&s->singles, &s->bulk}) {
+      for (Req *r : *q) {
+        r->status = RPQ_ERR_CANCELLED;
+        r->t_start = r->t_done = now;
+        r->done = true;
+      }
+      q->clear();
+    }
+  }
+  s->cv_done.notify_all();
   return RPQ_OK;
 }
 

@@ -36,10 +36,12 @@ RPQ_ERR_OUT_OF_BUDGET = -5
 RPQ_ERR_CUDA = -6
 RPQ_ERR_TIMEOUT = -7
 RPQ_ERR_NO_DEVICE = -8
+RPQ_ERR_CANCELLED = -9
 
 RPQ_MATERIALIZE = 0x1
 RPQ_COUNT_ONLY = 0x2
 RPQ_REVERSE = 0x4
+RPQ_PER_QUERY = 0x8
 RPQ_FORCE_PUSH = 0x100
 RPQ_FORCE_PULL = 0x200
 
@@ -282,7 +284,15 @@ def run_rpq_static(ctx: Context, g: Graph, q: Query, sources, out_pairs_ptr: int
 
 _lib.run_rpq_batch.argtypes = [c_void_p, c_void_p, c_u32, c_void_p, c_void_p, c_u32, P(c_void_p)]
 _lib.rpq_autotune_batch.argtypes = [c_void_p, c_void_p, c_u32, c_void_p, c_void_p, P(c_u32), P(c_u32)]
-EXPORTED += ["run_rpq_batch", "rpq_autotune_batch"]
+_lib.result_query_stats.argtypes = [c_void_p, c_u32, P(c_u64), P(c_u64), P(c_u64)]
+EXPORTED += ["run_rpq_batch", "rpq_autotune_batch", "result_query_stats"]
+
+
+def result_query_stats(r: Result, i: int):
+    """(rows, digest sum, digest xor) of query i of a RPQ_PER_QUERY batch."""
+    c, s, x = c_u64(), c_u64(), c_u64()
+    r.ctx.check(_lib.result_query_stats(r.h, i, ctypes.byref(c), ctypes.byref(s), ctypes.byref(x)))
+    return c.value, s.value, x.value
 
 
 def _query_array(queries):
@@ -333,10 +343,11 @@ _lib.rpq_server_create.argtypes = [c_void_p, c_void_p, c_u64, c_u32, P(c_void_p)
 _lib.rpq_server_submit.argtypes = [c_void_p, P(rpq_request), P(c_u64)]
 _lib.rpq_server_wait.argtypes = [c_void_p, c_u64, ctypes.c_double, P(rpq_reply)]
 _lib.rpq_server_stats.argtypes = [c_void_p, P(c_u64), P(c_u64)]
+_lib.rpq_server_cancel.argtypes = [c_void_p]
 _lib.rpq_server_destroy.argtypes = [c_void_p]
 _lib.rpq_server_destroy.restype = None
 EXPORTED += ["rpq_set_option", "rpq_server_create", "rpq_server_submit", "rpq_server_wait", "rpq_server_stats",
-             "rpq_server_destroy"]
+             "rpq_server_cancel", "rpq_server_destroy"]
 
 
 def rpq_set_option(ctx: Context, name: str, value: float):
@@ -380,6 +391,10 @@ class Server:
         self._keep.pop(ticket, None)
         return rep.as_dict()
 
+    def cancel(self):
+        """Cancels every request not yet done (status RPQ_ERR_CANCELLED)."""
+        _lib.rpq_server_cancel(self.h)
+
     def stats(self):
         b, r = c_u64(), c_u64()
         _lib.rpq_server_stats(self.h, ctypes.byref(b), ctypes.byref(r))
@@ -388,6 +403,66 @@ class Server:
     def close(self):
         if getattr(self, "h", None):
             _lib.rpq_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+
+# ---- streamed materialization ------------------------------------------------
+
+class rpq_row_block(ctypes.Structure):
+    _fields_ = [("n_sources", c_u32), ("sources", P(c_u32)), ("offsets", P(c_u64)), ("dst", P(c_u32)),
+                ("n_rows", c_u64)]
+
+
+_lib.rpq_stream_open.argtypes = [c_void_p, c_void_p, c_void_p, c_u32, c_u32, c_u32, P(c_void_p)]
+_lib.rpq_stream_next.argtypes = [c_void_p, P(rpq_row_block)]
+_lib.rpq_stream_info.argtypes = [c_void_p, P(c_u64), P(c_u64), P(c_u64), P(rpq_stats)]
+_lib.rpq_stream_close.argtypes = [c_void_p]
+_lib.rpq_stream_close.restype = None
+EXPORTED += ["rpq_stream_open", "rpq_stream_next", "rpq_stream_info", "rpq_stream_close"]
+
+
+class Stream:
+    """rpq_stream_*: rows of rho from start vertices [begin, end), block by
+    block, copied to the host while the device keeps exploring."""
+
+    def __init__(self, ctx: Context, g: Graph, q: Query, begin: int, end: int, flags: int = 0):
+        h = c_void_p()
+        ctx.check(_lib.rpq_stream_open(ctx.h, g.h, q.h, begin, end, flags, ctypes.byref(h)))
+        self.ctx, self.g, self.q, self.h = ctx, g, q, h
+        self._blk = rpq_row_block()
+
+    def next_block(self):
+        """(sources, offsets, dst) as numpy views of the library's pinned slot
+        (valid until the next call), or None at the end."""
+        self.ctx.check(_lib.rpq_stream_next(self.h, ctypes.byref(self._blk)))
+        b = self._blk
+        if b.n_rows == 0:
+            return None
+        src = np.ctypeslib.as_array(b.sources, shape=(b.n_sources,))
+        off = np.ctypeslib.as_array(b.offsets, shape=(b.n_sources + 1,))
+        dst = np.ctypeslib.as_array(b.dst, shape=(b.n_rows,))
+        return src, off, dst
+
+    def pairs(self) -> np.ndarray:
+        """Every remaining row as an (n, 2) uint32 array (copied)."""
+        out = []
+        while (blk := self.next_block()) is not None:
+            src, off, dst = blk
+            out.append(np.stack([np.repeat(src, np.diff(off).astype(np.int64)), dst], axis=1).astype(np.uint32))
+        return np.concatenate(out) if out else np.zeros((0, 2), dtype=np.uint32)
+
+    def info(self):
+        rows, s, x = c_u64(), c_u64(), c_u64()
+        st = rpq_stats()
+        _lib.rpq_stream_info(self.h, ctypes.byref(rows), ctypes.byref(s), ctypes.byref(x), ctypes.byref(st))
+        return rows.value, s.value, x.value, st.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.rpq_stream_close(self.h)
             self.h = None
 
     def __del__(self):

@@ -204,6 +204,33 @@ def random_regex(seed: int, n_labels: int, max_symbols: int = 5, p_star: float =
     return text
 
 
+def _draw_regex(st: _Stream, cdf: np.ndarray, n_ranks: int, first_rank: int) -> str:
+    """One regex of the single-source mix: 1..6 symbols, each a label of rank
+    first_rank + (a draw from cdf); stars on k in {0, 1, 2} distinct symbols;
+    with probability 1/4 two adjacent symbols become an alternation."""
+    k = 1 + int(st.below(1, 6)[0])
+    syms = [chr(ord("a") + first_rank + min(int(np.searchsorted(cdf, st.unit(1)[0], side="right")), n_ranks - 1))
+            for _ in range(k)]
+    n_star = min(k, int(st.below(1, 3)[0]))
+    starred = set()
+    while len(starred) < n_star:
+        starred.add(int(st.below(1, k)[0]))
+    parts = [s + ("*" if i in starred else "") for i, s in enumerate(syms)]
+    if k >= 2 and st.unit(1)[0] < 0.25:
+        i = int(st.below(1, k - 1)[0])
+        a, b = syms[i], syms[i + 1]
+        star = "*" if (i in starred or i + 1 in starred) else ""
+        parts = parts[:i] + [f"({a}|{b}){star}"] + parts[i + 2:]
+    return ".".join(parts)
+
+
+def _degree_sources(st: _Stream, n: int, src: np.ndarray, n_vertices: int) -> np.ndarray:
+    deg = np.bincount(np.asarray(src, dtype=np.int64), minlength=n_vertices).astype(np.float64)
+    cum = np.cumsum(deg)
+    u = st.unit(n) * cum[-1]
+    return np.minimum(np.searchsorted(cum, u, side="right"), n_vertices - 1).astype(np.uint32)
+
+
 def batch_queries(n_queries: int, n_labels: int, zipf_s: float, src: np.ndarray, n_vertices: int, seed: int):
     """Single-source query mix: each regex has 1..6 symbols, each a label drawn
     Zipf(zipf_s); Kleene stars on k in {0, 1, 2} (uniform) distinct symbols; with
@@ -213,24 +240,46 @@ def batch_queries(n_queries: int, n_labels: int, zipf_s: float, src: np.ndarray,
     st = _Stream(seed)
     cdf = np.cumsum(zipf_probs(n_labels, zipf_s))
     cdf[-1] = 1.0
-    regexes = []
-    for _ in range(n_queries):
-        k = 1 + int(st.below(1, 6)[0])
-        syms = [chr(ord("a") + min(int(np.searchsorted(cdf, st.unit(1)[0], side="right")), n_labels - 1))
-                for _ in range(k)]
-        n_star = min(k, int(st.below(1, 3)[0]))
-        starred = set()
-        while len(starred) < n_star:
-            starred.add(int(st.below(1, k)[0]))
-        parts = [s + ("*" if i in starred else "") for i, s in enumerate(syms)]
-        if k >= 2 and st.unit(1)[0] < 0.25:
-            i = int(st.below(1, k - 1)[0])
-            a, b = syms[i], syms[i + 1]
-            star = "*" if (i in starred or i + 1 in starred) else ""
-            parts = parts[:i] + [f"({a}|{b}){star}"] + parts[i + 2:]
-        regexes.append(".".join(parts))
-    deg = np.bincount(np.asarray(src, dtype=np.int64), minlength=n_vertices).astype(np.float64)
-    cum = np.cumsum(deg)
-    u = st.unit(n_queries) * cum[-1]
-    sources = np.minimum(np.searchsorted(cum, u, side="right"), n_vertices - 1).astype(np.uint32)
-    return regexes, sources
+    regexes = [_draw_regex(st, cdf, n_labels, 0) for _ in range(n_queries)]
+    return regexes, _degree_sources(st, n_queries, src, n_vertices)
+
+
+def serve_stream(rate: float, seconds: float, n_labels: int, zipf_s: float, src: np.ndarray, n_vertices: int,
+                 seed: int, mix=(0.80, 0.15, 0.05), tail_rank: int = 8):
+    """Mixed request stream with Poisson arrivals (mean `rate` per second over
+    `seconds`).  Each request is, with the probabilities of `mix`:
+    1 single-source -- a regex of the batch_queries mix from a start vertex
+      drawn proportional to out-degree;
+    2 all-pairs -- a regex of the same shape whose labels come from the Zipf
+      tail (ranks tail_rank .. n_labels - 1, Zipf(zipf_s) renormalized there);
+    3 CRPQ -- the triangle x -l1-> y, x -l2.l3*-> z, y -l4*-> z with l1..l4
+      drawn from the same tail.
+    Returns (t: arrival seconds ascending, kind: uint8, spec: list) where spec
+    is (regex, source), regex, or (l1, l2, l3, l4) as label letters."""
+    st = _Stream(seed)
+    gaps = -np.log1p(-st.unit(int(rate * seconds * 1.2) + 64)) / rate
+    t = np.cumsum(gaps)
+    t = t[t < seconds]
+    m = len(t)
+    u = st.unit(m)
+    kind = np.where(u < mix[0], 1, np.where(u < mix[0] + mix[1], 2, 3)).astype(np.uint8)
+    head = np.cumsum(zipf_probs(n_labels, zipf_s))
+    head[-1] = 1.0
+    n_tail = n_labels - tail_rank
+    tw = zipf_probs(n_labels, zipf_s)[tail_rank:]
+    tail = np.cumsum(tw / tw.sum())
+    tail[-1] = 1.0
+    srcs = _degree_sources(st, m, src, n_vertices)
+
+    def tail_letter():
+        return chr(ord("a") + tail_rank + min(int(np.searchsorted(tail, st.unit(1)[0], side="right")), n_tail - 1))
+
+    spec = []
+    for i in range(m):
+        if kind[i] == 1:
+            spec.append((_draw_regex(st, head, n_labels, 0), int(srcs[i])))
+        elif kind[i] == 2:
+            spec.append(_draw_regex(st, tail, n_tail, tail_rank))
+        else:
+            spec.append(tuple(tail_letter() for _ in range(4)))
+    return t, kind, spec

@@ -98,6 +98,47 @@ def test_batch_autotune_and_edge_cases(ctx, er):
     assert e.value.code == rpq.RPQ_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("evict", [0, 40, 65536])
+def test_batch_per_query_matches_standalone(evict):
+    """RPQ_PER_QUERY: every query's row count and digest equal run_rpq's for
+    that query alone, whether it stays in the shared launch or is evicted and
+    evaluated by the multi-source engine (threshold 40 evicts most queries,
+    0 none); the work counter stays exact."""
+    c = rpq.Context(device=0)
+    rpq.rpq_set_option(c, "batch_evict", evict)
+    n = 20000
+    src, dst, lab = synth.rmat_graph(15, 8 * n, 4, 1.2, seed=57)
+    src %= n
+    dst %= n
+    g = rpq.load_graph(c, n, 4, src, dst, lab)
+    regexes, sources = synth.batch_queries(400, 4, 1.2, src, n, seed=59)
+    regexes[5] = "z"  # label absent: empty
+    sources[7] = sources[8]  # duplicate start vertex
+    regexes[7] = regexes[8]
+    qs = [rpq.compile_rpq(c, r) for r in regexes]
+    r = rpq.run_rpq_batch(c, g, qs, sources, flags=rpq.RPQ_PER_QUERY)
+    tot = [0, 0, 0]
+    W = 0
+    for i, (q, s) in enumerate(zip(qs, sources)):
+        one = rpq.run_rpq(c, g, q, [s], flags=rpq.RPQ_COUNT_ONLY)
+        cnt, _, hs, hx = rpq.result_info(one)
+        W += rpq.result_stats(one)["product_edges"]
+        one.free()
+        assert rpq.result_query_stats(r, i) == (cnt, hs, hx), (i, regexes[i])
+        tot[0] += cnt
+        tot[1] = (tot[1] + hs) & 0xFFFFFFFFFFFFFFFF
+        tot[2] ^= hx
+    assert rpq.result_info(r) == (tot[0], 2, tot[1], tot[2])
+    assert rpq.result_stats(r)["product_edges"] == W
+    with pytest.raises(rpq.RPQError):
+        rpq.result_query_stats(r, 400)
+    # a few queries against the oracle directly
+    og = oracle.Graph(n, 4, src, dst, lab)
+    for i in (0, 5, 7, 123):
+        want = oracle.rpq(og, regexes[i], sources=[int(sources[i])]).rows
+        assert rpq.result_query_stats(r, i) == oracle.pair_digest(want)
+
+
 def test_batch_rmat22_sampled(ctx):
     """4,096 queries on R-MAT scale 22 (2^26 edges, 8 labels Zipf 1.2),
     sources proportional to out-degree; sampled queries row by row."""

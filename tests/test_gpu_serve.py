@@ -84,3 +84,20 @@ def test_set_option(setup):
         rpq.rpq_set_option(c2, "no_such_option", 1)
     with pytest.raises(rpq.RPQError):
         rpq.rpq_set_option(c2, "grid_share", 2)
+
+
+def test_cancel_stops_queued_and_running_requests(setup):
+    ctx, g, n, regexes, sources = setup
+    ap = rpq.compile_rpq(ctx, "(a|b|c|d|e|f)*")
+    q = rpq.compile_rpq(ctx, regexes[0])
+    want = standalone(ctx, g, "single", (q, int(sources[0])))
+    server = rpq.Server(ctx, g, max_batch=64)
+    bulk = [server.submit_allpairs(ap) for _ in range(20)]
+    server.cancel()
+    statuses = [server.wait(t, timeout_s=120)["status"] for t in bulk]
+    assert all(s in (0, rpq.RPQ_ERR_CANCELLED) for s in statuses)
+    assert statuses[-1] == rpq.RPQ_ERR_CANCELLED
+    # the server keeps serving after a cancel
+    rep = server.wait(server.submit_single(q, int(sources[0])), timeout_s=120)
+    assert rep["status"] == 0 and (rep["count"], rep["digest_sum"], rep["digest_xor"]) == want
+    server.close()
