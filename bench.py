@@ -19,6 +19,7 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|referenc
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import signal
@@ -128,6 +129,32 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+KERNEL_SOURCES = ("msbfs.cu", "rpq_internal.h", "device_common.cuh")
+
+
+def kernel_source_sha1() -> str:
+    """SHA-1 over the traversal kernel's source files, to tell whether stored
+    ncu counters still describe the kernel that runs."""
+    h = hashlib.sha1()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2602_20748_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    """DRAM bytes per traversal launch from the committed ncu summary
+    (profiles/msbfs_traffic.json), or None when the kernel's sources changed
+    since those counters were taken."""
+    path = os.path.join(ROOT, "profiles", "msbfs_traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    return t.get("bytes_per_launch") if t.get("source_sha1") == kernel_source_sha1() else None
+
+
 def algorithmic_bytes(st: dict) -> float:
     """Bytes the traversal kernel must move for the work it did, counted by the
     kernel itself (rpq_stats.alg_bytes): per top-down relaxation a 4-byte
@@ -222,8 +249,10 @@ def ours(args, rank: int, world: int, local_rank: int):
     B = args.batch
     n_batches = n // B
 
+    from paper_2602_20748_gb300 import shard
+
     def batch_of(step_index: int) -> int:
-        return (step_index * world + rank) % n_batches
+        return shard.rank_batches(n_batches, step_index, 1, world, rank)[0]
 
     def run_step(step_index: int, acc: dict):
         b0 = batch_of(step_index) * B
@@ -266,12 +295,10 @@ def ours(args, rank: int, world: int, local_rank: int):
     ms = ev0.elapsed_time(ev1)
     W_all, pairs_all, ms_max = acc["W"], acc["pairs"], ms
     if dist:
-        t = torch.tensor([acc["W"], acc["pairs"]], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t)
-        W_all, pairs_all = int(t[0].item()), int(t[1].item())
-        tm = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        ms_max = float(tm.item())
+        # the only exchange: per-rank summaries (no rows cross ranks)
+        tot = shard.gather_combine(dist, {"rows": acc["pairs"], "digest_sum": 0, "digest_xor": 0,
+                                          "work": acc["W"], "ms": ms})
+        W_all, pairs_all, ms_max = tot["work"], tot["rows"], tot["ms"]
         dist.barrier()
     value = W_all / (ms_max / 1000.0)
 
@@ -301,12 +328,9 @@ def ours(args, rank: int, world: int, local_rank: int):
             st_.close()
         t_e2e = time.perf_counter() - t0
         if dist:
-            tt = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_e2e = float(tt.item())
-            tw = torch.tensor([W_e2e], dtype=torch.float64, device="cuda")
-            dist.all_reduce(tw)
-            W_e2e = int(tw.item())
+            tot = shard.gather_combine(dist, {"rows": rows_e2e, "digest_sum": 0, "digest_xor": 0,
+                                              "work": W_e2e, "ms": t_e2e * 1000.0})
+            W_e2e, t_e2e = tot["work"], tot["ms"] / 1000.0
         lane_meta = launches * (B * 4 + (B + 1) * 8)
         e2e = {"value": W_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": launches * B * 4 // args.steps,
                "d2h_bytes_per_step": (rows_e2e * 4 + lane_meta) // args.steps,
@@ -321,14 +345,7 @@ def ours(args, rank: int, world: int, local_rank: int):
 
     peak, peak_kind = peaks()
     achieved = acc["alg_bytes"] / max(1, acc["bfs_launches"]) / (acc["bfs_ms"] / max(1, acc["bfs_launches"]) / 1e3) / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "msbfs_traffic.json")
-    if os.path.exists(tpath):
-        try:
-            with open(tpath) as f:
-                traffic = json.load(f).get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = measured_traffic()
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

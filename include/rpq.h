@@ -201,9 +201,9 @@ int run_rpq_range(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, uint32_t
  * that mode a query whose product graph grows past a threshold (option
  * "batch_evict", product vertices; default 65,536) leaves the shared launch,
  * and such queries are then evaluated together by the multi-source engine,
- * one bit-sliced traversal per distinct automaton over their distinct start
- * vertices.  Block size, queries per launch and the threshold come from the
- * last rpq_autotune_batch on the context (defaults otherwise).
+ * one bit-sliced traversal per distinct automaton with a lane per query.
+ * Block size, queries per launch and the threshold come from the last
+ * rpq_autotune_batch on the context (defaults otherwise).
  * Errors: INVALID_ARG, OUT_OF_BUDGET, CUDA, TIMEOUT. */
 int run_rpq_batch(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_queries, const rpq_query *const *queries,
                   const uint32_t *sources, uint32_t flags, rpq_result **out);
@@ -383,7 +383,8 @@ int result_query_stats(const rpq_result *r, uint32_t i, uint64_t *count, uint64_
  * RPQ_REVERSE.  The context serves only this stream until rpq_stream_close
  * (the library runs it from two threads of its own); the graph and query must
  * outlive the stream.  Device memory held by rows not yet copied is bounded by
- * three batches; host memory is three pinned slots of 256 MiB. */
+ * three batches; host memory is three pinned slots of 256 MiB, allocated by
+ * the first stream on the context and kept by the context for later ones. */
 typedef struct rpq_stream rpq_stream;
 
 typedef struct {

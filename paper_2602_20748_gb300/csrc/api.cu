@@ -34,6 +34,8 @@ struct Workspace {
   u32 *lanesrc = nullptr;
   u64 *empty = nullptr;
   u64 *spill = nullptr;  // SPILL_CAP chunk records of 6 words
+  u32 *fbits = nullptr;  // two frontier bitmaps of fbits_words() words each
+  uint64_t fbits_words() const { return (list_cap + 31) / 32; }  // list_cap >= Q * n
 };
 
 }  // namespace
@@ -60,6 +62,10 @@ struct rpq_ctx {
   double grid_share = 1.0;         // fraction of the SMs persistent grids use
   rpq::BatchTuning batch = rpq::batch_default_tuning();  // run_rpq_batch tunables
   std::atomic<int> cancel{0};  // set by a server to stop the request in service
+  std::vector<void *> pinned;  // pinned host slots lent to streams (kept for reuse)
+  std::vector<rpq_ctx *> helpers;  // contexts for concurrent sub-evaluations (own streams)
+  std::vector<cudaStream_t> helper_streams;
+  size_t pinned_bytes = 0;
   int live = 0;          // graphs and results not yet freed
   bool closing = false;  // rpq_destroy was called while handles were live
 };
@@ -170,13 +176,15 @@ void free_workspace(rpq_ctx *ctx) {
   dfree(ctx, w.list1, w.list_cap);
   dfree(ctx, w.claim, w.claim_cap);
   dfree(ctx, w.lanesrc, w.lane_cap);
-  dfree(ctx, w.empty, w.lane_cap / 64);
+  dfree(ctx, w.empty, w.lane_cap / 64 + 1);
   dfree(ctx, w.spill, SPILL_CAP * 6);
+  dfree(ctx, w.fbits, 2 * w.fbits_words());
   w = Workspace();
 }
 
 uint64_t workspace_bytes(uint64_t words, uint64_t lists, uint64_t claims, uint32_t lanes) {
-  return words * 8 * 3 + lists * 8 * 2 + claims * 4 + (uint64_t)lanes * 4 + (uint64_t)lanes / 64 * 8;
+  return words * 8 * 3 + lists * 8 * 2 + (lists + 31) / 32 * 8 + claims * 4 + (uint64_t)lanes * 4 +
+         (uint64_t)lanes / 64 * 8;
 }
 
 // Makes sure the traversal workspace holds at least the given capacities.
@@ -190,18 +198,21 @@ int ensure_workspace(rpq_ctx *ctx, uint64_t words, uint64_t lists, uint64_t clai
   claims = std::max(claims, w.claim_cap);
   lanes = std::max(lanes, w.lane_cap);
   free_workspace(ctx);
-  int rc;
-  if ((rc = dalloc(ctx, &w.vis, words)) || (rc = dalloc(ctx, &w.fr0, words)) || (rc = dalloc(ctx, &w.fr1, words)) ||
-      (rc = dalloc(ctx, &w.list0, lists)) || (rc = dalloc(ctx, &w.list1, lists)) ||
-      (rc = dalloc(ctx, &w.claim, claims ? claims : 1)) || (rc = dalloc(ctx, &w.lanesrc, lanes)) ||
-      (rc = dalloc(ctx, &w.empty, lanes / 64 + 1)) || (rc = dalloc(ctx, &w.spill, SPILL_CAP * 6))) {
-    free_workspace(ctx);
-    return rc;
-  }
+  // capacities first, so that a failed allocation releases what it got
   w.vis_words = words;
   w.list_cap = lists;
   w.claim_cap = claims ? claims : 1;
   w.lane_cap = lanes;
+  int rc;
+  if ((rc = dalloc(ctx, &w.vis, words)) || (rc = dalloc(ctx, &w.fr0, words)) || (rc = dalloc(ctx, &w.fr1, words)) ||
+      (rc = dalloc(ctx, &w.list0, lists)) || (rc = dalloc(ctx, &w.list1, lists)) ||
+      (rc = dalloc(ctx, &w.claim, claims ? claims : 1)) || (rc = dalloc(ctx, &w.lanesrc, lanes)) ||
+      (rc = dalloc(ctx, &w.empty, lanes / 64 + 1)) || (rc = dalloc(ctx, &w.spill, SPILL_CAP * 6)) ||
+      (rc = dalloc(ctx, &w.fbits, 2 * ((lists + 31) / 32)))) {
+    free_workspace(ctx);
+    return rc;
+  }
+  CK(cudaMemsetAsync(w.fbits, 0, 2 * w.fbits_words() * 4, ctx->stream));
   CK(cudaMemsetAsync(w.fr0, 0, words * 8, ctx->stream));
   CK(cudaMemsetAsync(w.fr1, 0, words * 8, ctx->stream));
   CK(cudaMemsetAsync(w.claim, 0, w.claim_cap * 4, ctx->stream));
@@ -297,6 +308,8 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
     p.fr0 = w.fr0;
     p.fr1 = w.fr1;
     p.claim = w.claim;
+    p.fbits = w.fbits;
+    p.fbits_words = w.fbits_words();
     p.spill = w.spill;
     p.spill_cap = ctx->spill_cap;
     p.list0 = w.list0;
@@ -345,6 +358,7 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
       if (hctl.err) {
         cudaMemsetAsync(w.fr0, 0, w.vis_words * 8, ctx->stream);
         cudaMemsetAsync(w.fr1, 0, w.vis_words * 8, ctx->stream);
+      cudaMemsetAsync(w.fbits, 0, 2 * w.fbits_words() * 4, ctx->stream);
         return set_err(ctx, RPQ_ERR_TIMEOUT, "traversal grid barrier wait ran out of time");
       }
       for (uint32_t i = 0; i < n_lanes; i++) {
@@ -370,7 +384,7 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
       s.pull_vertices += hctl.stats[ST_PULL_VERTICES];
       s.alg_bytes += hctl.stats[ST_ALG_BYTES];
       s.lane_groups += Gb;
-      ctx->stamp += (uint32_t)hctl.levels + 2;
+      ctx->stamp += (uint32_t)hctl.levels + 3;
       float ms_bfs = 0, ms_emit = 0;
       cudaEventElapsedTime(&ms_bfs, ctx->ev[0], ctx->ev[1]);
       cudaEventElapsedTime(&ms_emit, ctx->ev[2], ctx->ev[3]);
@@ -420,6 +434,7 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
       // an interrupted search may leave frontier words set: clear them
       cudaMemsetAsync(w.fr0, 0, w.vis_words * 8, ctx->stream);
       cudaMemsetAsync(w.fr1, 0, w.vis_words * 8, ctx->stream);
+      cudaMemsetAsync(w.fbits, 0, 2 * w.fbits_words() * 4, ctx->stream);
       return set_err(ctx, RPQ_ERR_TIMEOUT, "traversal grid barrier wait ran out of time");
     }
     const uint64_t total = hsmall[2];
@@ -451,7 +466,7 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
                      hctl.trace_mode[l] == 1 ? "push" : "pull", (unsigned long long)hctl.trace_n[l],
                      (unsigned long long)hctl.trace_mf[l], (hctl.trace_t[l + 1] - hctl.trace_t[l]) * 1e-6);
     }
-    ctx->stamp += (uint32_t)hctl.levels + 2;
+    ctx->stamp += (uint32_t)hctl.levels + 3;
 
     if (materialize) {
       Chunk c;
@@ -466,12 +481,13 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
         return rc;
       }
       ep.dst = c.dst;
-      CK(launch_emit(nw, true, true, ep, ctx->stream));
+      CK(launch_emit(nw, true, false, ep, ctx->stream));
       CK(launch_gather_lane_off(off, segs, n_lanes, ctx->small + 2, c.lane_off, ctx->stream));
       CK(cudaMemcpyAsync(c.lanesrc, w.lanesrc, n_lanes * 4, cudaMemcpyDeviceToDevice, ctx->stream));
-      res->stats.launches += 2;
+      // digest of the written rows, thread per row
+      CK(launch_row_digest(w.lanesrc, c.lane_off, n_lanes, c.dst, ctx->small, ctx->stream));
+      res->stats.launches += 3;
       res->chunks.push_back(c);
-      // the write pass folded the digest
       CK(cudaMemcpyAsync(hdig, ctx->small, 16, cudaMemcpyDeviceToHost, ctx->stream));
     }
     CK(cudaEventRecord(ctx->ev[3], ctx->stream));
@@ -604,7 +620,10 @@ void destroy_now(rpq_ctx *c) {
     cudaStreamSynchronize(c->stream);
     for (int i = 0; i < 4; i++)
       if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    for (rpq_ctx *h : c->helpers) rpq_destroy(h);
+    for (cudaStream_t hs : c->helper_streams) cudaStreamDestroy(hs);
     if (c->pool) cudaMemPoolDestroy(c->pool);
+    for (void *h : c->pinned) cudaFreeHost(h);
   }
   delete c;
 }
@@ -1020,6 +1039,42 @@ int ctx_device(rpq_ctx *ctx) { return ctx->device; }
 int ctx_sm_share(rpq_ctx *ctx) { return std::max(1, (int)(ctx->sms * ctx->grid_share)); }
 int ctx_bfs_blocks(rpq_ctx *ctx, int nw) { return ctx_sm_share(ctx) * ctx->bpsm[nw == 1 ? 0 : 1]; }
 bool ctx_trace(rpq_ctx *ctx) { return ctx->trace; }
+int ctx_helpers(rpq_ctx *ctx, int k, std::vector<rpq_ctx *> *out) {
+  while ((int)ctx->helpers.size() < k) {
+    cudaStream_t hs = nullptr;
+    if (cudaStreamCreateWithFlags(&hs, cudaStreamNonBlocking) != cudaSuccess)
+      return set_err(ctx, RPQ_ERR_CUDA, "helper stream creation failed");
+    rpq_ctx *h = nullptr;
+    int rc = rpq_create(&h, ctx->device, ctx->budget / 8, hs);
+    if (rc) {
+      cudaStreamDestroy(hs);
+      return set_err(ctx, rc, "helper context creation failed");
+    }
+    h->alpha = ctx->alpha;
+    h->time_limit_ns = ctx->time_limit_ns;
+    h->grid_share = ctx->grid_share / k;
+    ctx->helpers.push_back(h);
+    ctx->helper_streams.push_back(hs);
+  }
+  for (int i = 0; i < k; i++) ctx->helpers[i]->grid_share = ctx->grid_share / k;
+  out->assign(ctx->helpers.begin(), ctx->helpers.begin() + k);
+  return RPQ_OK;
+}
+int ctx_pinned(rpq_ctx *ctx, int count, size_t bytes, void **out) {
+  if (ctx->pinned_bytes < bytes) {
+    for (void *h : ctx->pinned) cudaFreeHost(h);
+    ctx->pinned.clear();
+    ctx->pinned_bytes = bytes;
+  }
+  while ((int)ctx->pinned.size() < count) {
+    void *h = nullptr;
+    cudaError_t e = cudaHostAlloc(&h, ctx->pinned_bytes, cudaHostAllocDefault);
+    if (e != cudaSuccess) return set_err(ctx, RPQ_ERR_CUDA, std::string("pinned host memory: ") + cudaGetErrorString(e));
+    ctx->pinned.push_back(h);
+  }
+  for (int i = 0; i < count; i++) out[i] = ctx->pinned[i];
+  return RPQ_OK;
+}
 bool ctx_cancelled(rpq_ctx *ctx) { return ctx->cancel.load(std::memory_order_relaxed) != 0; }
 void ctx_set_cancel(rpq_ctx *ctx, bool on) { ctx->cancel.store(on ? 1 : 0); }
 float ctx_alpha(rpq_ctx *ctx) { return ctx->alpha; }
@@ -1074,8 +1129,9 @@ int rpq_rows_for_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, s
   return rc;
 }
 
-// Count-only evaluation from sorted distinct sources with each source's own
-// (rows, digest sum, digest xor) in lane_stats[3 * i ..]; counters added to *stats.
+// Count-only evaluation from sorted sources (a repeated source is a lane of
+// its own) with each lane's own (rows, digest sum, digest xor) in
+// lane_stats[3 * i ..]; counters added to *stats.
 int rpq_lane_stats_for_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q,
                                const std::vector<uint32_t> &srcs, std::vector<uint64_t> *lane_stats,
                                rpq_stats *stats) {

@@ -13,6 +13,8 @@
 // than SPILL_EDGES are cut into chunks shared by all warps.  Results are the
 // accepting states' bitmaps, emitted as (query index, vertex) rows.
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <map>
 #include <string>
 #include <cstdio>
@@ -34,6 +36,8 @@ constexpr unsigned ERR_LIST_FULL = 100;  // frontier list capacity exceeded
 // Bounds checks: an index outside its array records which check failed (the
 // access is skipped) and stops the search with RPQ_ERR_CUDA on the host.
 constexpr unsigned ERR_BOUNDS = 200;
+// evicted queries' automaton groups evaluated side by side
+constexpr size_t REGROUP_STREAMS = 4;
 
 struct BatchParams {
   const uint32_t *out_off;
@@ -70,18 +74,17 @@ __device__ __forceinline__ bool bad(const BatchParams &p, bool cond, unsigned wh
 }
 
 
-// Reserves `chunks` spill records, all or nothing: the count only ever covers
-// records that will be written (a reservation that does not fit leaves the
-// row to be processed in place).  Returns the first record or ~0 on failure.
-__device__ __forceinline__ unsigned long long spill_reserve(unsigned long long *count, unsigned chunks,
-                                                            unsigned long long cap) {
-  unsigned long long cur = *(volatile unsigned long long *)count;
-  for (;;) {
-    if (cur + chunks > cap) return ~0ull;
-    unsigned long long prev = atomicCAS(count, cur, cur + chunks);
-    if (prev == cur) return cur;
-    cur = prev;
-  }
+// Reserves up to `chunks` spill records with one atomic add and returns how
+// many of them fit below `cap` (their first index in *at).  Records below
+// the capacity are always written by their reserver, so the spill phase,
+// which reads min(count, cap) records, never reads one nobody wrote; the
+// chunks that do not fit are processed in place.
+__device__ __forceinline__ unsigned spill_reserve(unsigned long long *count, unsigned chunks, unsigned long long cap,
+                                                  unsigned long long *at) {
+  const unsigned long long first = atomicAdd(count, (unsigned long long)chunks);
+  *at = first;
+  if (first >= cap) return 0;
+  return (unsigned)min((unsigned long long)chunks, cap - first);
 }
 
 __device__ bool bbarrier(BfsCtl *c, unsigned nblocks, u64 limit_ns) {
@@ -211,15 +214,17 @@ __device__ void bpush(const BatchParams &p, int lp, u32 cur, u32 nxt, u64 n_cur,
       }
       if (rlen > SPILL_EDGES) {
         const u32 chunks = (rlen + SPILL_EDGES - 1) / SPILL_EDGES;
-        const u64 at = spill_reserve(&p.ctl->spill_count[cur], chunks, p.spill_cap);
-        if (at != ~0ull) {
-          for (u32 c = 0; c < chunks; c++) {
-            u64 *rec = p.spill + (at + c) * 2;
-            rec[0] = bentry(i, q2, 0) | (rbeg + c * SPILL_EDGES);
-            rec[1] = min(SPILL_EDGES, rlen - c * SPILL_EDGES);
-          }
-          rlen = 0;
+        u64 at = 0;
+        const u32 fit = spill_reserve(&p.ctl->spill_count[cur], chunks, p.spill_cap, &at);
+        for (u32 c = 0; c < fit; c++) {
+          u64 *rec = p.spill + (at + c) * 2;
+          rec[0] = bentry(i, q2, 0) | (rbeg + c * SPILL_EDGES);
+          rec[1] = min(SPILL_EDGES, rlen - c * SPILL_EDGES);
         }
+        // the chunks that did not fit stay with this warp
+        const u32 moved = min(rlen, fit * SPILL_EDGES);
+        rbeg += moved;
+        rlen -= moved;
       }
       u32 pre = rlen;
 #pragma unroll
@@ -257,7 +262,7 @@ __device__ void bpush(const BatchParams &p, int lp, u32 cur, u32 nxt, u64 n_cur,
 __device__ void bspill(const BatchParams &p, int lp, u32 cur, u32 nxt, u64 *edges) {
   u64 *nlist = lp ? p.list0 : p.list1;
   const u32 lane = lane_id();
-  const u64 count = *(volatile unsigned long long *)&p.ctl->spill_count[cur];
+  const u64 count = min(*(volatile unsigned long long *)&p.ctl->spill_count[cur], (unsigned long long)p.spill_cap);
   for (;;) {
     u64 r = 0;
     if (lane == 0) r = atomicAdd(&p.ctl->spill_cursor[cur], 1ull);
@@ -698,26 +703,68 @@ int batch_run(rpq_ctx *ctx, const rpq_graph *g, uint32_t nq, const rpq_query *co
   }
   if (!out->per_query) return RPQ_OK;
   // Queries that left the batch: one multi-source (bit-sliced) evaluation per
-  // distinct automaton over the distinct start vertices of its queries, with
-  // every start vertex's own row count and digest.
+  // distinct automaton over the start vertices of its queries, with every
+  // lane's own row count and digest.
   std::map<std::string, std::vector<uint32_t>> groups;
   for (uint32_t i : out->evicted_idx) {
     const QueryDesc &d = query_host(queries[i]).d;
     groups[std::string(reinterpret_cast<const char *>(&d), sizeof(d))].push_back(i);
   }
-  for (auto &kv : groups) {
-    std::vector<uint32_t> srcs;
-    for (uint32_t i : kv.second) srcs.push_back(sources[i]);
-    std::sort(srcs.begin(), srcs.end());
-    srcs.erase(std::unique(srcs.begin(), srcs.end()), srcs.end());
-    std::vector<uint64_t> ls;
-    int rc = rpq_lane_stats_for_sources(ctx, g, queries[kv.second[0]], srcs, &ls, &out->stats);
-    if (rc) return rc;
-    out->regroup_launches++;
-    for (uint32_t i : kv.second) {
-      const size_t k = std::lower_bound(srcs.begin(), srcs.end(), sources[i]) - srcs.begin();
-      for (int c = 0; c < 3; c++) out->qstats[3ull * i + c] = ls[3 * k + c];
+  // the groups run side by side on helper contexts (own streams, a share of
+  // the SMs each), one host thread per helper taking groups in turn
+  std::vector<const std::vector<uint32_t> *> todo;
+  for (auto &kv : groups) todo.push_back(&kv.second);
+  const int k = (int)std::min<size_t>(REGROUP_STREAMS, todo.size());
+  std::vector<rpq_ctx *> helpers;
+  int rc = k > 1 ? ctx_helpers(ctx, k, &helpers) : RPQ_OK;
+  if (rc) return rc;
+  if (k <= 1) helpers.assign(1, ctx);
+  std::atomic<size_t> next{0};
+  std::vector<int> rcs(helpers.size(), RPQ_OK);
+  std::vector<rpq_stats> hst(helpers.size());
+  std::vector<uint64_t> launches(helpers.size(), 0);
+  auto work = [&](size_t h) {
+    std::memset(&hst[h], 0, sizeof(rpq_stats));
+    cudaSetDevice(ctx_device(ctx));
+    for (size_t t; (t = next.fetch_add(1)) < todo.size();) {
+      const std::vector<uint32_t> &members = *todo[t];
+      // one lane per query, in source order (a repeated start vertex gets a
+      // lane of its own, so the work counter stays the sum over queries)
+      std::vector<std::pair<uint32_t, uint32_t>> order;
+      for (uint32_t i : members) order.push_back({sources[i], i});
+      std::sort(order.begin(), order.end());
+      std::vector<uint32_t> srcs;
+      for (auto &o : order) srcs.push_back(o.first);
+      std::vector<uint64_t> ls;
+      int r = rpq_lane_stats_for_sources(helpers[h], g, queries[members[0]], srcs, &ls, &hst[h]);
+      if (r) {
+        rcs[h] = r;
+        next = todo.size();
+        return;
+      }
+      launches[h]++;
+      for (size_t j = 0; j < order.size(); j++)
+        for (int c = 0; c < 3; c++) out->qstats[3ull * order[j].second + c] = ls[3 * j + c];
     }
+  };
+  std::vector<std::thread> threads;
+  for (size_t h = 1; h < helpers.size(); h++) threads.emplace_back(work, h);
+  work(0);
+  for (auto &t : threads) t.join();
+  for (size_t h = 0; h < helpers.size(); h++) {
+    if (rcs[h]) return ctx_error(ctx, rcs[h], "multi-source evaluation of evicted queries failed");
+    rpq_stats &a = out->stats, &b = hst[h];
+    a.product_edges += b.product_edges;
+    a.product_vertices += b.product_vertices;
+    a.levels += b.levels;
+    a.push_levels += b.push_levels;
+    a.pull_levels += b.pull_levels;
+    a.bfs_ms += b.bfs_ms;
+    a.emit_ms += b.emit_ms;
+    a.bfs_launches += b.bfs_launches;
+    a.launches += b.launches;
+    a.alg_bytes += b.alg_bytes;
+    out->regroup_launches += launches[h];
   }
   out->evicted += out->evicted_idx.size();
   // with per-query summaries the totals are theirs: rows and digests of the

@@ -29,6 +29,13 @@ int ctx_bfs_blocks(rpq_ctx *ctx, int nw);
 int ctx_sm_share(rpq_ctx *ctx);  // SMs the context's persistent grids may use
 float ctx_alpha(rpq_ctx *ctx);
 bool ctx_trace(rpq_ctx *ctx);              // per-level trace printing (RPQ_TRACE=1)
+// k helper contexts (created once, kept by ctx): own streams, an eighth of
+// ctx's budget each and ctx->grid_share / k of the SMs, for evaluations that
+// run side by side from k host threads.
+int ctx_helpers(rpq_ctx *ctx, int k, std::vector<rpq_ctx *> *out);
+// `count` pinned host buffers of `bytes` each, owned by the context and kept
+// for reuse (one user at a time).
+int ctx_pinned(rpq_ctx *ctx, int count, size_t bytes, void **out);
 bool ctx_cancelled(rpq_ctx *ctx);          // a server asked the request in service to stop
 void ctx_set_cancel(rpq_ctx *ctx, bool on);
 uint64_t ctx_time_limit_ns(rpq_ctx *ctx);

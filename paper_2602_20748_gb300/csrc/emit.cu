@@ -32,6 +32,13 @@ __global__ void emit_kernel(const EmitParams p) {
   const u32 *vis32 = reinterpret_cast<const u32 *>(p.vis);
   const u32 lt = (1u << lane) - 1u;
   u64 cnt = 0, hsum = 0, hxor = 0;
+  // count pass: per-lane counts of this thread's vertices as bit planes
+  // (EMIT_TILES <= 2^CNT_PLANES - 1 vertices per thread)
+  constexpr int CNT_PLANES = 6;
+  static_assert(EMIT_TILES < (1 << CNT_PLANES), "count planes too narrow");
+  u32 planes[CNT_PLANES];
+#pragma unroll
+  for (int k = 0; k < CNT_PLANES; k++) planes[k] = 0;
   u64 pos = 0;  // lane `lane`'s next output position (write pass)
   if (WRITE) pos = p.off[glane * p.segs + seg];
   const u32 w_begin = seg * EMIT_SEG;
@@ -48,6 +55,18 @@ __global__ void emit_kernel(const EmitParams p) {
       }
     }
     x &= valid_cols;
+    if (!WRITE && !DIGEST) {
+      // count only: add x into per-thread bit-sliced counters (plane k holds
+      // bit k of each lane's count over this thread's vertices so far)
+      u32 carry = x;
+#pragma unroll
+      for (int k = 0; k < CNT_PLANES; k++) {
+        const u32 t = planes[k] & carry;
+        planes[k] ^= carry;
+        carry = t;
+      }
+      continue;
+    }
     for (u32 rows = __reduce_or_sync(FULL_MASK, x); rows; rows &= rows - 1) {
       const u32 j = __ffs(rows) - 1;
       const u32 mine = (x >> j) & 1u;
@@ -70,6 +89,21 @@ __global__ void emit_kernel(const EmitParams p) {
         else
           cnt += __popc(m);
       }
+    }
+  }
+  if (!WRITE && !DIGEST) {
+    // lane j's count = sum over planes k of 2^k * (threads with bit j set in
+    // plane k): transpose each plane with 32 ballots
+#pragma unroll
+    for (int k = 0; k < CNT_PLANES; k++) {
+      if (!__any_sync(FULL_MASK, planes[k])) continue;
+      u32 mine = 0;
+#pragma unroll
+      for (int j = 0; j < 32; j++) {
+        const u32 b = __ballot_sync(FULL_MASK, (planes[k] >> j) & 1u);
+        if (lane == (u32)j) mine = b;
+      }
+      cnt += (u64)__popc(mine) << k;
     }
   }
   if (!WRITE) p.cnt[glane * p.segs + seg] = (u32)cnt;
@@ -104,6 +138,36 @@ cudaError_t launch_emit(int nw, bool write, bool digest, const EmitParams &p, cu
       digest ? emit_kernel<4, false, true><<<grid, threads, 0, st>>>(p)
              : emit_kernel<4, false, false><<<grid, threads, 0, st>>>(p);
   }
+  return cudaGetLastError();
+}
+
+// Digest of a materialized chunk's rows, thread per row: block b takes lanes
+// b, b + gridDim.x, ...; the rows of lane i are contiguous
+// (dst[lane_off[i] .. lane_off[i + 1])) and all belong to source lanesrc[i].
+__global__ void row_digest_kernel(const u32 *__restrict__ lanesrc, const u64 *__restrict__ lane_off, u32 n_lanes,
+                                  const u32 *__restrict__ dst, u64 *__restrict__ digest) {
+  u64 hsum = 0, hxor = 0;
+  for (u32 i = blockIdx.x; i < n_lanes; i += gridDim.x) {
+    const u64 src = (u64)lanesrc[i] << 32;
+    const u64 b = lane_off[i], e = lane_off[i + 1];
+    for (u64 r = b + threadIdx.x; r < e; r += blockDim.x) {
+      const u64 h = splitmix64(src | (u64)__ldcs(dst + r));
+      hsum += h;
+      hxor ^= h;
+    }
+  }
+  hsum = warp_sum(hsum);
+  hxor = warp_xor(hxor);
+  if (lane_id() == 0 && (hsum | hxor)) {
+    atomicAdd(&digest[0], hsum);
+    atomicXor(&digest[1], hxor);
+  }
+}
+
+cudaError_t launch_row_digest(const uint32_t *lanesrc, const unsigned long long *lane_off, uint32_t n_lanes,
+                              const uint32_t *dst, unsigned long long *digest, cudaStream_t st) {
+  if (n_lanes == 0) return cudaSuccess;
+  row_digest_kernel<<<n_lanes, 256, 0, st>>>(lanesrc, lane_off, n_lanes, dst, digest);
   return cudaGetLastError();
 }
 

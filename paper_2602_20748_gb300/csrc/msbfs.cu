@@ -142,18 +142,17 @@ __device__ __forceinline__ u32 degsum(const BfsParams &p, u32 q, u32 v) {
   return s;
 }
 
-// Reserves `chunks` spill records, all or nothing: the count only ever covers
-// records that will be written (a reservation that does not fit leaves the
-// row to be processed in place).  Returns the first record or ~0 on failure.
-__device__ __forceinline__ unsigned long long spill_reserve(unsigned long long *count, unsigned chunks,
-                                                            unsigned long long cap) {
-  unsigned long long cur = *(volatile unsigned long long *)count;
-  for (;;) {
-    if (cur + chunks > cap) return ~0ull;
-    unsigned long long prev = atomicCAS(count, cur, cur + chunks);
-    if (prev == cur) return cur;
-    cur = prev;
-  }
+// Reserves up to `chunks` spill records with one atomic add and returns how
+// many of them fit below `cap` (their first index in *at).  Records below
+// the capacity are always written by their reserver, so the spill phase,
+// which reads min(count, cap) records, never reads one nobody wrote; the
+// chunks that do not fit are processed in place.
+__device__ __forceinline__ unsigned spill_reserve(unsigned long long *count, unsigned chunks, unsigned long long cap,
+                                                  unsigned long long *at) {
+  const unsigned long long first = atomicAdd(count, (unsigned long long)chunks);
+  *at = first;
+  if (first >= cap) return 0;
+  return (unsigned)min((unsigned long long)chunks, cap - first);
 }
 
 // Warp-aggregated append of `entry` for the lanes with `take` set.  All 32
@@ -182,14 +181,21 @@ __device__ void seed_phase(const BfsParams &p, u64 *stat) {
       if (s != NO_SOURCE) {
         u32 g = (u32)(i / K), lane = (u32)(i % K);
         u64 wi = widx<NW>(p, g, 0, s);  // start state 0
-        p.vis[wi + lane / 64] |= 1ull << (lane % 64);
-        p.fr0[wi + lane / 64] = 1ull << (lane % 64);
+        // lanes may repeat a start vertex, so seeds share words: atomics, and
+        // one list entry per (group, vertex)
+        const u64 bit = 1ull << (lane % 64);
+        atomicOr((unsigned long long *)(p.vis + wi + lane / 64), bit);
+        const u64 oldf = atomicOr((unsigned long long *)(p.fr0 + wi + lane / 64), bit);
+        if constexpr (NW == 1)
+          take = oldf == 0;
+        else
+          take = atomicMax(p.claim + ((u64)s * p.G + g), p.stamp_base + 1) < p.stamp_base + 1;
         entry = ((u64)g * p.Q << 32) | s;
-        take = true;
+        if (take && p.fbits) atomicOr(p.fbits + (s >> 5), 1u << (s & 31));  // state 0, bitmap 0
         u32 d = degsum(p, 0, s);
         W += d;
         N += 1;
-        mf += d;
+        if (take) mf += d;
       }
     }
     warp_append(take, entry, &p.ctl->n_list[0], p.list0);
@@ -276,17 +282,19 @@ __device__ void push_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u64 n_c
       }
       if (p.spill && rlen > SPILL_EDGES) {
         const u32 chunks = (rlen + SPILL_EDGES - 1) / SPILL_EDGES;
-        const u64 at = spill_reserve(&p.ctl->spill_count[cur], chunks, p.spill_cap);
-        if (at != ~0ull) {
-          for (u32 c = 0; c < chunks; c++) {
-            u64 *rec = p.spill + (at + c) * (2 + NW);
-            rec[0] = ((u64)tgq << 32) | (rbeg + c * SPILL_EDGES);
-            rec[1] = min(SPILL_EDGES, rlen - c * SPILL_EDGES);
+        u64 at = 0;
+        const u32 fit = spill_reserve(&p.ctl->spill_count[cur], chunks, p.spill_cap, &at);
+        for (u32 c = 0; c < fit; c++) {
+          u64 *rec = p.spill + (at + c) * (2 + NW);
+          rec[0] = ((u64)tgq << 32) | (rbeg + c * SPILL_EDGES);
+          rec[1] = min(SPILL_EDGES, rlen - c * SPILL_EDGES);
 #pragma unroll
-            for (int t = 0; t < NW; t++) rec[2 + t] = fm.w[t];
-          }
-          rlen = 0;
+          for (int t = 0; t < NW; t++) rec[2 + t] = fm.w[t];
         }
+        // the chunks that did not fit stay with this warp
+        const u32 moved = min(rlen, fit * SPILL_EDGES);
+        rbeg += moved;
+        rlen -= moved;
       }
       // exclusive prefix of row lengths across the warp
       u32 pre = rlen;
@@ -340,7 +348,7 @@ __device__ void spill_phase(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 st
   u64 *nlist = lp ? p.list0 : p.list1;
   u64 *FB = lp ? p.fr0 : p.fr1;
   const u32 lane = lane_id();
-  const u64 count = *(volatile unsigned long long *)&p.ctl->spill_count[cur];
+  const u64 count = min(*(volatile unsigned long long *)&p.ctl->spill_count[cur], (unsigned long long)p.spill_cap);
   u64 edges = 0;
   for (;;) {
     u64 r = 0;
@@ -373,43 +381,73 @@ __device__ void spill_phase(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 st
 
 // Bottom-up work for target (q2, w) over in-edges [beg, end) of one
 // transition group with active source states `from`: every lane ORs the
-// gathered frontier words of its PER words into acc.
+// gathered frontier words of its PER words into acc.  A lane stops gathering
+// once acc covers all its lanes not yet visited (nothing more can be found);
+// the sub-warp (lanes sg_mask) leaves the row when all its lanes have.
+// Returns the in-edges examined.
 template <int NW, int PER>
-__device__ __forceinline__ void gather_row(const BfsParams &p, const u64 *F, u32 from, u32 beg, u32 end,
-                                           u32 lane_off, bool lane_on, u64 (&acc)[PER]) {
+__device__ __forceinline__ u32 gather_row(const BfsParams &p, const u64 *F, const u32 *bits, u32 from, u32 beg,
+                                          u32 end, u32 lane_off, bool lane_on, u32 sg_mask,
+                                          const u64 (&vis)[PER], u64 (&acc)[PER], u32 &gathers) {
   const u32 n = p.n;
   const u64 wpv = (u64)p.G * NW;
+  auto done = [&]() {
+    bool d = true;
+#pragma unroll
+    for (int k = 0; k < PER; k++) d &= (acc[k] | vis[k]) == ~0ull;
+    return d;
+  };
+  bool fin = !lane_on || done();
+  if ((__ballot_sync(sg_mask, !fin) & sg_mask) == 0) return 0;
   u32 i = beg;
   // four in-edges per step keep four gathers in flight
   for (; i + 4 <= end; i += 4) {
     u32 v0 = __ldg(p.in_col + i), v1 = __ldg(p.in_col + i + 1), v2 = __ldg(p.in_col + i + 2),
         v3 = __ldg(p.in_col + i + 3);
-    if (!lane_on) continue;
-    for (u32 fb = from; fb; fb &= fb - 1) {
-      const u64 qb = (u64)(__ffs(fb) - 1) * n;
-      const u64 *f0 = F + (qb + v0) * wpv + lane_off, *f1 = F + (qb + v1) * wpv + lane_off;
-      const u64 *f2 = F + (qb + v2) * wpv + lane_off, *f3 = F + (qb + v3) * wpv + lane_off;
-      if constexpr (PER == 2) {
-        ulonglong2 a0 = __ldcg(reinterpret_cast<const ulonglong2 *>(f0));
-        ulonglong2 a1 = __ldcg(reinterpret_cast<const ulonglong2 *>(f1));
-        ulonglong2 a2 = __ldcg(reinterpret_cast<const ulonglong2 *>(f2));
-        ulonglong2 a3 = __ldcg(reinterpret_cast<const ulonglong2 *>(f3));
-        acc[0] |= a0.x | a1.x | a2.x | a3.x;
-        acc[1] |= a0.y | a1.y | a2.y | a3.y;
-      } else {
-        acc[0] |= __ldcg(f0) | __ldcg(f1) | __ldcg(f2) | __ldcg(f3);
+    if (!fin) {
+      for (u32 fb = from; fb; fb &= fb - 1) {
+        const u64 qb = (u64)(__ffs(fb) - 1) * n;
+        // with a frontier bitmap, neighbours outside the frontier are skipped
+        bool h0 = true, h1 = true, h2 = true, h3 = true;
+        if (bits) {
+          h0 = (__ldcg(bits + ((qb + v0) >> 5)) >> ((qb + v0) & 31)) & 1u;
+          h1 = (__ldcg(bits + ((qb + v1) >> 5)) >> ((qb + v1) & 31)) & 1u;
+          h2 = (__ldcg(bits + ((qb + v2) >> 5)) >> ((qb + v2) & 31)) & 1u;
+          h3 = (__ldcg(bits + ((qb + v3) >> 5)) >> ((qb + v3) & 31)) & 1u;
+        }
+        gathers += (u32)h0 + (u32)h1 + (u32)h2 + (u32)h3;
+        const u64 *f0 = F + (qb + v0) * wpv + lane_off, *f1 = F + (qb + v1) * wpv + lane_off;
+        const u64 *f2 = F + (qb + v2) * wpv + lane_off, *f3 = F + (qb + v3) * wpv + lane_off;
+        if constexpr (PER == 2) {
+          const ulonglong2 z = make_ulonglong2(0, 0);
+          ulonglong2 a0 = h0 ? __ldcg(reinterpret_cast<const ulonglong2 *>(f0)) : z;
+          ulonglong2 a1 = h1 ? __ldcg(reinterpret_cast<const ulonglong2 *>(f1)) : z;
+          ulonglong2 a2 = h2 ? __ldcg(reinterpret_cast<const ulonglong2 *>(f2)) : z;
+          ulonglong2 a3 = h3 ? __ldcg(reinterpret_cast<const ulonglong2 *>(f3)) : z;
+          acc[0] |= a0.x | a1.x | a2.x | a3.x;
+          acc[1] |= a0.y | a1.y | a2.y | a3.y;
+        } else {
+          acc[0] |= (h0 ? __ldcg(f0) : 0ull) | (h1 ? __ldcg(f1) : 0ull) | (h2 ? __ldcg(f2) : 0ull) |
+                    (h3 ? __ldcg(f3) : 0ull);
+        }
       }
+      fin = done();
     }
+    if ((__ballot_sync(sg_mask, !fin) & sg_mask) == 0) return i + 4 - beg;
   }
   for (; i < end; i++) {
     u32 v = __ldg(p.in_col + i);
-    if (!lane_on) continue;
+    if (fin) continue;
     for (u32 fb = from; fb; fb &= fb - 1) {
-      const u64 *f = F + ((u64)(__ffs(fb) - 1) * n + v) * wpv + lane_off;
+      const u64 bi = (u64)(__ffs(fb) - 1) * n + v;
+      if (bits && !((__ldcg(bits + (bi >> 5)) >> (bi & 31)) & 1u)) continue;
+      gathers++;
+      const u64 *f = F + bi * wpv + lane_off;
 #pragma unroll
       for (int k = 0; k < PER; k++) acc[k] |= __ldcg(f + k);
     }
   }
+  return end - beg;
 }
 
 // Bottom-up target (q2, w), all groups: new lanes = acc & ~VIS go to the next
@@ -452,7 +490,8 @@ __device__ __forceinline__ void pull_finish(const BfsParams &p, u64 *FB, u64 *nl
 // whose source states are active; the sub-warps split the chunk's edges and
 // OR their gathers together.
 template <int NW>
-__device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 active, u32 stamp, u64 *stat) {
+__device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 active, u32 stamp, const u32 *bits,
+                           u64 *stat) {
   constexpr int PER = (NW >= 2) ? 2 : 1;
   const u64 *F = lp ? p.fr1 : p.fr0;
   u64 *FB = lp ? p.fr0 : p.fr1;
@@ -511,9 +550,11 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
           const u32 *off = p.in_off + (u64)l * n1 + w;
           const u32 beg = __ldg(off), end = __ldg(off + 1);
           if (end - beg >= HEAVY_ROW && chunked) continue;
-          edges += (li == 0) ? (end - beg) : 0;
-          bytes += (li == 0) ? 8 + (u64)(end - beg) * (4 + gword * __popc(from)) : 0;
-          gather_row<NW, PER>(p, F, from, beg, end, lane_off, lane_on, acc);
+          u32 gat = 0;
+          const u32 ex = gather_row<NW, PER>(p, F, bits, from, beg, end, lane_off, lane_on, sg_mask, vis, acc, gat);
+          edges += (li == 0) ? ex : 0;
+          // column ids, frontier-bit words when tested, gathered frontier words
+          bytes += (li == 0) ? 8 + (u64)ex * (4 + (bits ? 4 * __popc(from) : 0)) + (u64)gat * gword : 0;
         }
         words += (li == 0);
         bytes += (li == 0) ? gword : 0;
@@ -563,13 +604,16 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
       // the sub-warps take consecutive slices of the chunk's edges
       const u32 len = end - beg, per = (len + VPW - 1) / VPW;
       const u32 sb = beg + min(len, sg * per), se = beg + min(len, (sg + 1) * per);
-      gather_row<NW, PER>(p, F, from, sb, se, lane_off, lane_on, acc);
+      u32 gat = 0;
+      const u32 ex = gather_row<NW, PER>(p, F, bits, from, sb, se, lane_off, lane_on, sg_mask, vis, acc, gat);
       for (u32 o = SW; o < 32; o <<= 1) {
 #pragma unroll
         for (int k = 0; k < PER; k++) acc[k] |= __shfl_xor_sync(FULL_MASK, acc[k], o);
       }
-      edges += (lane == 0) ? len : 0;
-      bytes += (lane == 0) ? 12 + gword + (u64)len * (4 + gword * __popc(from)) : 0;
+      const u64 ex_all = warp_sum((u64)(li == 0 ? ex : 0));
+      const u64 gat_all = warp_sum((u64)(li == 0 ? gat : 0));
+      edges += (lane == 0) ? ex_all : 0;
+      bytes += (lane == 0) ? 12 + gword + ex_all * (4 + (bits ? 4 * __popc(from) : 0)) + gat_all * gword : 0;
       words += (lane == 0);
       pull_finish<NW, PER>(p, FB, nlist, nxt, q2s, w, stamp, li, lane_on && sg == 0, my_g, vis, acc);
     }
@@ -603,6 +647,10 @@ __device__ void commit_phase(const BfsParams &p, int lp, u32 nxt, u64 n_cur, u64
 #pragma unroll
     for (int t = 0; t < NW; t++) v.w[t] |= m.w[t];
     store_w<NW>(p.vis + wi, v);
+    if (p.fbits) {
+      const u64 bi = (u64)q * p.n + w;
+      atomicOr(p.fbits + (lp ? 0 : p.fbits_words) + (bi >> 5), 1u << (bi & 31));
+    }
     u32 c = popc_w(m);
     u32 d = degsum(p, q, w);
     W += (u64)c * d;
@@ -619,6 +667,11 @@ __device__ void commit_phase(const BfsParams &p, int lp, u32 nxt, u64 n_cur, u64
     u32 gq = (u32)(e >> 32);
     u32 g = gq / Q;
     store_w<NW>(F + widx<NW>(p, g, gq - g * Q, (u32)e), zero);
+    if (p.fbits) {
+      // the retired frontier's bitmap: every set bit belongs to one of these entries
+      const u64 bi = (u64)(gq - g * Q) * p.n + (u32)e;
+      p.fbits[(lp ? p.fbits_words : 0) + (bi >> 5)] = 0u;
+    }
   }
   if (tid == 0) stat[ST_ALG_BYTES] += n_cur * (8 + 8 * NW);
   W = warp_sum(W);
@@ -701,7 +754,7 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) msbfs_kernel(const __grid_cons
       else
         stat[ST_PULL_LEVELS] += 1;
     }
-    const u32 stamp = p.stamp_base + level + 1;
+    const u32 stamp = p.stamp_base + level + 2;  // the seeds used stamp_base + 1
     if (push) {
       push_level<NW>(p, lp, cur, nxt, n_cur, stamp, stat);
       if (!grid_barrier(c, p.nblocks, p.time_limit_ns)) return;
@@ -710,7 +763,10 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) msbfs_kernel(const __grid_cons
         if (!grid_barrier(c, p.nblocks, p.time_limit_ns)) return;
       }
     } else {
-      pull_level<NW>(p, lp, cur, nxt, active, stamp, stat);
+      // a sparse frontier: test the frontier bitmap before each gather
+      const bool sparse = p.fbits && n_cur * 4 < (u64)p.n * __popc(active);
+      const u32 *bits = sparse ? p.fbits + (lp ? p.fbits_words : 0) : nullptr;
+      pull_level<NW>(p, lp, cur, nxt, active, stamp, bits, stat);
       if (!grid_barrier(c, p.nblocks, p.time_limit_ns)) return;
     }
     commit_phase<NW>(p, lp, nxt, n_cur, stat);

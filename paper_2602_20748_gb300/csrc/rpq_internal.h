@@ -144,6 +144,12 @@ struct BfsParams {
   unsigned long long spill_cap;  // records usable per level (<= SPILL_CAP)
   unsigned long long *list0;   // entries ((g*Q+q) << 32 | v)
   unsigned long long *list1;
+  // Optional frontier bitmaps (nullptr: none), two of fbits_words words: bit
+  // q*n + v of bitmap (level & 1) is set when some group holds (q, v) in the
+  // level's frontier; bottom-up levels over a sparse frontier test it before
+  // gathering a neighbour's frontier words.  Zero between searches.
+  unsigned int *fbits;
+  unsigned long long fbits_words;
   BfsCtl *ctl;
   unsigned int stamp_base;     // claim stamps continue across launches
   unsigned int nblocks;
@@ -174,6 +180,10 @@ struct EmitParams {
 constexpr int EMIT_TILES = 32;  // 32-vertex tiles per segment
 constexpr int EMIT_SEG = 32 * EMIT_TILES;
 cudaError_t launch_emit(int nw, bool write, bool digest, const EmitParams &p, cudaStream_t st);
+// Digest (sum, xor of splitmix64(src << 32 | dst)) of a materialized chunk's
+// rows, added into digest[0..1].
+cudaError_t launch_row_digest(const uint32_t *lanesrc, const unsigned long long *lane_off, uint32_t n_lanes,
+                              const uint32_t *dst, unsigned long long *digest, cudaStream_t st);
 // Per-lane row count and digest (lane_stats[3 * lane + {0, 1, 2}] = rows,
 // digest sum, digest xor over the lane's (source, y) rows); lane_stats zeroed
 // by the caller.

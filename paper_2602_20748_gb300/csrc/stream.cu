@@ -250,10 +250,8 @@ void destroy_stream(rpq_stream *s) {
   if (s->copy) cudaStreamSynchronize(s->copy);
   for (Batch *b : s->pending) release_batch(s, b);
   for (Batch *b : s->copied) release_batch(s, b);
-  for (Slot &sl : s->slots) {
-    if (sl.done) cudaEventDestroy(sl.done);
-    if (sl.host) cudaFreeHost(sl.host);
-  }
+  for (Slot &sl : s->slots)
+    if (sl.done) cudaEventDestroy(sl.done);  // the pinned slots stay with the context
   if (s->copy) cudaStreamDestroy(s->copy);
   delete s;
 }
@@ -283,17 +281,20 @@ int rpq_stream_open(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, uint32
   s->reverse = (flags & RPQ_REVERSE) != 0;
   s->batch = 64u * 4u * 16u;  // one traversal launch of 16 lane groups
   std::memset(&s->stats, 0, sizeof(s->stats));
+  void *hosts[N_SLOTS];
+  int prc = rpq::ctx_pinned(ctx, N_SLOTS, SLOT_ROWS * 4, hosts);
   cudaError_t e = cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking);
-  for (int i = 0; i < N_SLOTS && e == cudaSuccess; i++) {
-    e = cudaHostAlloc((void **)&s->slots[i].host, SLOT_ROWS * 4, cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->slots[i].done, cudaEventDisableTiming);
+  for (int i = 0; i < N_SLOTS && e == cudaSuccess && prc == RPQ_OK; i++) {
+    s->slots[i].host = (uint32_t *)hosts[i];
+    e = cudaEventCreateWithFlags(&s->slots[i].done, cudaEventDisableTiming);
     s->free_slots.push_back(i);
   }
-  if (e != cudaSuccess) {
+  if (e != cudaSuccess || prc != RPQ_OK) {
     s->eval_done = s->copy_done = true;
-    std::string msg = std::string("stream setup: ") + cudaGetErrorString(e);
+    std::string msg = prc != RPQ_OK ? std::string(rpq_last_error(ctx))
+                                    : std::string("stream setup: ") + cudaGetErrorString(e);
     destroy_stream(s);
-    return rpq::ctx_error(ctx, RPQ_ERR_CUDA, msg);
+    return rpq::ctx_error(ctx, prc != RPQ_OK ? prc : RPQ_ERR_CUDA, msg);
   }
   s->t_eval = std::thread(eval_thread, s);
   s->t_copy = std::thread(copy_thread, s);
