@@ -23,6 +23,7 @@ namespace {
 thread_local std::string g_create_error;
 
 constexpr int BFS_THREADS_HOST = 256;
+constexpr size_t SOURCE_FILTER_MIN = 4096;  // source lists at least this long drop edgeless start vertices
 
 struct Workspace {
   uint64_t vis_words = 0;   // capacity of vis / fr0 / fr1 in u64 words
@@ -220,6 +221,18 @@ int ensure_workspace(rpq_ctx *ctx, uint64_t words, uint64_t lists, uint64_t clai
   return RPQ_OK;
 }
 
+// A traversal launch stopped early: clear what it may have left set (the
+// frontier words and bitmaps must be zero for the next search) and map the
+// device error word to an error code.
+int traversal_error(rpq_ctx *ctx, unsigned err) {
+  Workspace &w = ctx->ws;
+  cudaMemsetAsync(w.fr0, 0, w.vis_words * 8, ctx->stream);
+  cudaMemsetAsync(w.fr1, 0, w.vis_words * 8, ctx->stream);
+  cudaMemsetAsync(w.fbits, 0, 2 * w.fbits_words() * 4, ctx->stream);
+  if (err == ERR_LIST_OVERFLOW) return set_err(ctx, RPQ_ERR_CUDA, "internal: traversal entry list overflow");
+  return set_err(ctx, RPQ_ERR_TIMEOUT, "traversal grid barrier wait ran out of time");
+}
+
 void free_chunk(rpq_ctx *ctx, Chunk &c) {
   dfree(ctx, c.lanesrc, c.n_lanes);
   dfree(ctx, c.lane_off, (uint64_t)c.n_lanes + 1);
@@ -229,7 +242,7 @@ void free_chunk(rpq_ctx *ctx, Chunk &c) {
 // Evaluates one RPQ from the sorted, distinct start vertices `srcs`.
 // With lane_stats (count-only), (rows, digest sum, digest xor) of every
 // source's own rows are stored at lane_stats[3 * i ..] for srcs[i].
-int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::vector<uint32_t> &srcs,
+int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::vector<uint32_t> &srcs_in,
              uint32_t flags, rpq_result *res, std::vector<uint64_t> *lane_stats = nullptr) {
   const DevGraph &g = gr->g;
   const bool reverse = (flags & RPQ_REVERSE) != 0;
@@ -238,19 +251,80 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
   const QueryDesc &qd = reverse ? qr->hq.rev : qr->hq.d;
   const uint32_t Q = qd.n_states;
   const bool materialize = (flags & RPQ_MATERIALIZE) != 0;
-  if (lane_stats) lane_stats->assign(3 * srcs.size(), 0);
+  if (lane_stats) lane_stats->assign(3 * srcs_in.size(), 0);
+  if (Q == 0 || srcs_in.empty()) {
+    res->stats.lane_words = srcs_in.size() <= 64 ? 1 : 4;
+    return RPQ_OK;
+  }
+  // A start vertex with no edge on a label leaving the start state reaches
+  // only (s, q0): its one possible row is (s, s), when q0 accepts.  Large
+  // source lists drop such vertices before the traversal (their rows are
+  // added here), unless rows are kept and q0 accepts (the (s, s) rows would
+  // have to be interleaved with the others).
+  std::vector<uint32_t> kept;
+  const bool q0_final = (qd.final_mask & 1u) != 0;
+  const bool filter = !lane_stats && srcs_in.size() >= SOURCE_FILTER_MIN && !(q0_final && materialize);
+  if (filter) {
+    unsigned long long lmask = 0;
+    for (uint32_t t = qd.out_begin[0]; t < qd.out_begin[1]; t++)
+      if (qd.out_label[t] < 64) lmask |= 1ull << qd.out_label[t];
+    u32 *dsrc = nullptr;
+    unsigned char *dflag = nullptr;
+    int rc2;
+    if ((rc2 = dalloc(ctx, &dsrc, srcs_in.size()))) return rc2;
+    if ((rc2 = dalloc(ctx, &dflag, srcs_in.size()))) {
+      dfree(ctx, dsrc, srcs_in.size());
+      return rc2;
+    }
+    std::vector<unsigned char> flag(srcs_in.size());
+    cudaError_t e = cudaMemcpyAsync(dsrc, srcs_in.data(), srcs_in.size() * 4, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+      e = launch_source_filter(reverse ? g.in_off : g.out_off, g.n, g.L, lmask, dsrc, srcs_in.size(), dflag,
+                               ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(flag.data(), dflag, srcs_in.size(), cudaMemcpyDeviceToHost, ctx->stream);
+    dfree(ctx, dsrc, srcs_in.size());
+    dfree(ctx, dflag, srcs_in.size());
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "source filter");
+    res->stats.launches += 1;
+    kept.reserve(srcs_in.size());
+    uint64_t skipped = 0;
+    for (size_t i = 0; i < srcs_in.size(); i++) {
+      if (flag[i]) {
+        kept.push_back(srcs_in[i]);
+        continue;
+      }
+      skipped++;
+      if (q0_final) {
+        const uint64_t h = splitmix64(((uint64_t)srcs_in[i] << 32) | srcs_in[i]);
+        res->dsum += h;
+        res->dxor ^= h;
+      }
+    }
+    res->stats.product_vertices += skipped;
+    if (q0_final) res->count += skipped;
+  }
+  const std::vector<uint32_t> &srcs = filter ? kept : srcs_in;
   res->stats.lane_words = srcs.size() <= 64 ? 1 : 4;
-  if (Q == 0 || srcs.empty()) return RPQ_OK;
+  if (srcs.empty()) return RPQ_OK;
   const int nw = srcs.size() <= 64 ? 1 : 4;
   const uint32_t K = 64u * nw;
   const uint32_t n = g.n;
   const uint64_t groups_total = (srcs.size() + K - 1) / K;
 
+  const int force = (flags & RPQ_FORCE_PUSH) ? 1 : (flags & RPQ_FORCE_PULL) ? 2 : 0;
+  const int blocks = ctx_bfs_blocks(ctx, nw);
+  if (blocks <= 0) return set_err(ctx, RPQ_ERR_CUDA, "traversal kernel cannot be made resident");
+  // list slots a level can leave unused: every warp may end each of the two
+  // appending phases of a level with part of a reserved segment
+  const uint64_t slack = 2ull * blocks * (BFS_THREADS_HOST / 32) * APPEND_SEG;
+
   // lane groups per launch: bounded by max_groups and by the budget
   uint32_t G = (uint32_t)std::min<uint64_t>(groups_total, ctx->max_groups);
   for (;;) {
     uint64_t words = (uint64_t)G * Q * n * nw;
-    uint64_t need = workspace_bytes(words, (uint64_t)G * Q * n, nw > 1 ? (uint64_t)G * Q * n : 0, G * K);
+    uint64_t need = workspace_bytes(words, (uint64_t)G * Q * n + slack, nw > 1 ? (uint64_t)G * Q * n : 0, G * K);
     uint64_t have = ctx->budget - ctx->used +
                     workspace_bytes(ctx->ws.vis_words, ctx->ws.list_cap, ctx->ws.claim_cap, ctx->ws.lane_cap);
     if (need + (64ull << 20) <= have || G == 1) break;
@@ -258,15 +332,10 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
   }
   {
     uint64_t words = (uint64_t)G * Q * n * nw;
-    int rc = ensure_workspace(ctx, words, (uint64_t)G * Q * n, nw > 1 ? (uint64_t)G * Q * n : 0, G * K);
+    int rc = ensure_workspace(ctx, words, (uint64_t)G * Q * n + slack, nw > 1 ? (uint64_t)G * Q * n : 0, G * K);
     if (rc) return rc;
   }
   Workspace &w = ctx->ws;
-
-
-  const int force = (flags & RPQ_FORCE_PUSH) ? 1 : (flags & RPQ_FORCE_PULL) ? 2 : 0;
-  const int blocks = ctx_bfs_blocks(ctx, nw);
-  if (blocks <= 0) return set_err(ctx, RPQ_ERR_CUDA, "traversal kernel cannot be made resident");
   const uint32_t segs = (n + EMIT_SEG - 1) / EMIT_SEG;
 
   std::vector<uint32_t> lanes;
@@ -310,6 +379,8 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
     p.claim = w.claim;
     p.fbits = w.fbits;
     p.fbits_words = w.fbits_words();
+    p.append_seg = APPEND_SEG;
+    p.list_cap = w.list_cap;
     p.spill = w.spill;
     p.spill_cap = ctx->spill_cap;
     p.list0 = w.list0;
@@ -355,12 +426,7 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
       CK(cudaMemcpyAsync(hls.data(), ls, 24ull * n_lanes, cudaMemcpyDeviceToHost, ctx->stream));
       dfree(ctx, ls, 3ull * n_lanes);
       CK(cudaStreamSynchronize(ctx->stream));
-      if (hctl.err) {
-        cudaMemsetAsync(w.fr0, 0, w.vis_words * 8, ctx->stream);
-        cudaMemsetAsync(w.fr1, 0, w.vis_words * 8, ctx->stream);
-      cudaMemsetAsync(w.fbits, 0, 2 * w.fbits_words() * 4, ctx->stream);
-        return set_err(ctx, RPQ_ERR_TIMEOUT, "traversal grid barrier wait ran out of time");
-      }
+      if (hctl.err) return traversal_error(ctx, hctl.err);
       for (uint32_t i = 0; i < n_lanes; i++) {
         const uint64_t si = g0 * K + i;
         if (si >= srcs.size()) break;
@@ -431,11 +497,7 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
       dfree(ctx, cnt, ncnt);
       dfree(ctx, off, ncnt);
       dfree(ctx, tmp, tmpw);
-      // an interrupted search may leave frontier words set: clear them
-      cudaMemsetAsync(w.fr0, 0, w.vis_words * 8, ctx->stream);
-      cudaMemsetAsync(w.fr1, 0, w.vis_words * 8, ctx->stream);
-      cudaMemsetAsync(w.fbits, 0, 2 * w.fbits_words() * 4, ctx->stream);
-      return set_err(ctx, RPQ_ERR_TIMEOUT, "traversal grid barrier wait ran out of time");
+      return traversal_error(ctx, hctl.err);
     }
     const uint64_t total = hsmall[2];
     res->count += total;

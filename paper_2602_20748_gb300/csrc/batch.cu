@@ -64,6 +64,7 @@ struct BatchParams {
   unsigned long long *qw;  // product edges per query (W)
   u32 *evicted;            // 1 = query left the batch (too large)
   u64 evict_at;            // evict a query once qn exceeds this (0: never)
+  u32 append_seg;          // list slots a warp reserves at a time (0: one atomic per append)
 };
 
 __device__ __forceinline__ u64 bentry(u32 i, u32 q, u32 v) { return ((u64)i << 37) | ((u64)q << 32) | v; }
@@ -129,22 +130,53 @@ __device__ __forceinline__ u32 bdegsum(const BatchParams &p, const QueryDesc &qd
   return s;
 }
 
-// Appends with a capacity check; a full list stops the search with an error
-// the host answers by splitting the batch.
-__device__ __forceinline__ void bappend(const BatchParams &p, bool take, u64 entry, unsigned long long *count,
-                                        u64 *list) {
-  u32 b = __ballot_sync(FULL_MASK, take);
+// A warp's current run of reserved list slots [pos, end) (warp-uniform).
+struct BAppender {
+  u64 pos = 0, end = 0;
+};
+
+// Warp-aggregated append with a capacity check; a full list stops the search
+// with an error the host answers by splitting the batch.  The warp reserves
+// append_seg slots at a time with one atomic add (the list counter would
+// otherwise take one atomic per append from every warp); slots it does not
+// use hold NO_ENTRY (bappend_close).  Small lists use one atomic per append.
+__device__ __forceinline__ void bappend(const BatchParams &p, BAppender &a, bool take, u64 entry,
+                                        unsigned long long *count, u64 *list) {
+  const u32 b = __ballot_sync(FULL_MASK, take);
   if (!b) return;
-  u64 base = 0;
-  if (lane_id() == __ffs(b) - 1) base = atomicAdd(count, (unsigned long long)__popc(b));
-  base = __shfl_sync(FULL_MASK, base, __ffs(b) - 1);
-  u64 at = base + __popc(b & lanemask_lt());
+  const u32 k = __popc(b), r = __popc(b & lanemask_lt());
+  u64 at;
+  if (p.append_seg == 0) {
+    u64 base = 0;
+    if (lane_id() == __ffs(b) - 1) base = atomicAdd(count, (unsigned long long)k);
+    at = __shfl_sync(FULL_MASK, base, __ffs(b) - 1) + r;
+  } else {
+    const u64 room = a.end - a.pos;
+    u64 nb = 0;
+    if (k > room) {
+      if (lane_id() == 0) nb = atomicAdd(count, (unsigned long long)p.append_seg);
+      nb = __shfl_sync(FULL_MASK, nb, 0);
+    }
+    at = r < room ? a.pos + r : nb + (r - room);
+    if (k > room) {
+      a.pos = nb + (k - room);
+      a.end = nb + p.append_seg;
+    } else {
+      a.pos += k;
+    }
+  }
   if (take) {
     if (at < p.list_cap)
       list[at] = entry;
     else
       atomicCAS(&p.ctl->err, 0u, ERR_LIST_FULL);
   }
+}
+
+__device__ __forceinline__ void bappend_close(const BatchParams &p, BAppender &a, u64 *list) {
+  for (u64 i = a.pos + lane_id(); i < a.end; i += 32)
+    if (i < p.list_cap) list[i] = NO_ENTRY;
+  a.pos = a.end = 0;
 }
 
 // Test-and-set of (query i, state q2, vertex w); true when this thread set it.
@@ -160,6 +192,7 @@ __device__ __forceinline__ bool bvisit(const BatchParams &p, u32 i, u32 q2, u32 
 
 __device__ void bseed(const BatchParams &p, u64 *W, u64 *N) {
   const u64 stride = (u64)gridDim.x * blockDim.x;
+  BAppender app;
   for (u64 base = (u64)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < p.nq; base += stride) {
     u64 i = base + lane_id();
     bool take = false;
@@ -177,23 +210,27 @@ __device__ void bseed(const BatchParams &p, u64 *W, u64 *N) {
         }
       }
     }
-    bappend(p, take, bentry((u32)i, 0, s), &p.ctl->n_list[0], p.list0);
+    bappend(p, app, take, bentry((u32)i, 0, s), &p.ctl->n_list[0], p.list0);
   }
+  bappend_close(p, app, p.list0);
 }
 
 __device__ void bpush(const BatchParams &p, int lp, u32 cur, u32 nxt, u64 n_cur, u64 *edges) {
   const u64 *list = lp ? p.list1 : p.list0;
   u64 *nlist = lp ? p.list0 : p.list1;
   const u32 lane = lane_id();
+  BAppender app;
   for (;;) {
     u64 base = 0;
     if (lane == 0) base = atomicAdd(&p.ctl->cursor[cur], 32ull);
     base = __shfl_sync(FULL_MASK, base, 0);
     if (base >= n_cur) break;
     const u64 idx = base + lane;
-    const u64 e = idx < n_cur ? __ldcg(&list[idx]) : 0;
+    u64 e = idx < n_cur ? __ldcg(&list[idx]) : NO_ENTRY;
+    const bool present = e != NO_ENTRY;
+    if (!present) e = 0;
     const u32 i = (u32)(e >> 37), q = (u32)(e >> 32) & 31u, v = (u32)e;
-    bool valid = idx < n_cur && !bad(p, i >= p.nq || v >= p.n, 10);
+    bool valid = present && !bad(p, i >= p.nq || v >= p.n, 10);
     if (valid && p.evict_at && __ldcg(&p.evicted[i])) valid = false;
     const QueryDesc *qd = p.qd + (valid ? i : 0);
     const u32 t_beg = valid ? qd->out_begin[q] : 0;
@@ -253,16 +290,18 @@ __device__ void bpush(const BatchParams &p, int lp, u32 cur, u32 nxt, u64 n_cur,
           w = __ldg(p.out_col + o_beg + (k - o_pre));
           take = bvisit(p, o_i, o_q2, w);
         }
-        bappend(p, take, bentry(o_i, o_q2, w), &p.ctl->n_list[nxt], nlist);
+        bappend(p, app, take, bentry(o_i, o_q2, w), &p.ctl->n_list[nxt], nlist);
       }
     }
   }
+  bappend_close(p, app, nlist);
 }
 
 __device__ void bspill(const BatchParams &p, int lp, u32 cur, u32 nxt, u64 *edges) {
   u64 *nlist = lp ? p.list0 : p.list1;
   const u32 lane = lane_id();
   const u64 count = min(*(volatile unsigned long long *)&p.ctl->spill_count[cur], (unsigned long long)p.spill_cap);
+  BAppender app;
   for (;;) {
     u64 r = 0;
     if (lane == 0) r = atomicAdd(&p.ctl->spill_cursor[cur], 1ull);
@@ -281,9 +320,10 @@ __device__ void bspill(const BatchParams &p, int lp, u32 cur, u32 nxt, u64 *edge
         w = __ldg(p.out_col + b + k);
         take = bvisit(p, i, q2, w);
       }
-      bappend(p, take, bentry(i, q2, w), &p.ctl->n_list[nxt], nlist);
+      bappend(p, app, take, bentry(i, q2, w), &p.ctl->n_list[nxt], nlist);
     }
   }
+  bappend_close(p, app, nlist);
 }
 
 __device__ void bcommit(const BatchParams &p, int lp, u32 nxt, u64 *W, u64 *N) {
@@ -296,6 +336,10 @@ __device__ void bcommit(const BatchParams &p, int lp, u32 nxt, u64 *W, u64 *N) {
     bool ok = j < n_next;
     u32 i = 0;
     u64 d = 0;
+    if (ok) {
+      const u64 e = __ldcg(&nlist[j]);
+      ok = e != NO_ENTRY;
+    }
     if (ok) {
       const u64 e = __ldcg(&nlist[j]);
       i = (u32)(e >> 37);
@@ -559,6 +603,10 @@ static int batch_launch(rpq_ctx *ctx, const rpq_graph *g, uint32_t qbase, uint32
     return berr(ctx, e, "occupancy");
   const int blocks = std::max(1, std::min(sms, ctx_sm_share(ctx))) * bpsm;
   p.nblocks = (unsigned)blocks;
+  // segments only when the unused tails (at most three appending phases per
+  // level, one segment per warp each) stay a small part of the list
+  const u64 nwarps = (u64)blocks * tun.threads / 32;
+  p.append_seg = tun.list_cap >= 16 * 3 * nwarps * APPEND_SEG ? APPEND_SEG : 0;
   void *args[] = {(void *)&p};
   cudaEvent_t ev0, ev1;
   cudaEventCreate(&ev0);

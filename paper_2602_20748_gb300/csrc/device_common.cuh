@@ -28,7 +28,7 @@ __device__ __forceinline__ u64 globaltimer_ns() {
 
 // SplitMix64 output for state x (Steele, Lea and Flood, OOPSLA 2014): add the
 // golden-ratio increment, then the variant-13 64-bit finalizer.
-__device__ __forceinline__ u64 splitmix64(u64 x) {
+__host__ __device__ __forceinline__ u64 splitmix64(u64 x) {
   u64 z = x + 0x9E3779B97F4A7C15ull;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;

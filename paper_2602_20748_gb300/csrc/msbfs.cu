@@ -155,15 +155,54 @@ __device__ __forceinline__ unsigned spill_reserve(unsigned long long *count, uns
   return (unsigned)min((unsigned long long)chunks, cap - first);
 }
 
+// A warp's current run of reserved list slots [pos, end) (warp-uniform).
+struct Appender {
+  u64 pos = 0, end = 0;
+};
+
 // Warp-aggregated append of `entry` for the lanes with `take` set.  All 32
-// lanes must call it.
-__device__ __forceinline__ void warp_append(bool take, u64 entry, unsigned long long *count, u64 *list) {
-  u32 b = __ballot_sync(FULL_MASK, take);
+// lanes must call it.  With segments, the warp fills its reserved slots and
+// reserves APPEND_SEG more with one atomic add when they run out, so the
+// list counter sees one atomic per segment instead of one per append.
+__device__ __forceinline__ void warp_append(const BfsParams &p, Appender &a, bool take, u64 entry,
+                                            unsigned long long *count, u64 *list) {
+  const u32 b = __ballot_sync(FULL_MASK, take);
   if (!b) return;
-  u64 base = 0;
-  if (lane_id() == __ffs(b) - 1) base = atomicAdd(count, (unsigned long long)__popc(b));
-  base = __shfl_sync(FULL_MASK, base, __ffs(b) - 1);
-  if (take) list[base + __popc(b & lanemask_lt())] = entry;
+  const u32 k = __popc(b), r = __popc(b & lanemask_lt());
+  u64 at;
+  if (p.append_seg == 0) {
+    u64 base = 0;
+    if (lane_id() == __ffs(b) - 1) base = atomicAdd(count, (unsigned long long)k);
+    base = __shfl_sync(FULL_MASK, base, __ffs(b) - 1);
+    at = base + r;
+  } else {
+    const u64 room = a.end - a.pos;
+    u64 nb = 0;
+    if (k > room) {
+      if (lane_id() == 0) nb = atomicAdd(count, (unsigned long long)p.append_seg);
+      nb = __shfl_sync(FULL_MASK, nb, 0);
+    }
+    at = r < room ? a.pos + r : nb + (r - room);
+    if (k > room) {
+      a.pos = nb + (k - room);
+      a.end = nb + p.append_seg;
+    } else {
+      a.pos += k;
+    }
+  }
+  if (take) {
+    if (at < p.list_cap)
+      list[at] = entry;
+    else
+      atomicCAS(&p.ctl->err, 0u, ERR_LIST_OVERFLOW);
+  }
+}
+
+// End of a phase: the warp's reserved slots not used hold NO_ENTRY.
+__device__ __forceinline__ void append_close(const BfsParams &p, Appender &a, u64 *list) {
+  for (u64 i = a.pos + lane_id(); i < a.end; i += 32)
+    if (i < p.list_cap) list[i] = NO_ENTRY;
+  a.pos = a.end = 0;
 }
 
 template <int NW>
@@ -172,6 +211,7 @@ __device__ void seed_phase(const BfsParams &p, u64 *stat) {
   const u64 total = (u64)p.G * K;
   const u64 stride = (u64)gridDim.x * blockDim.x;
   u64 W = 0, N = 0, mf = 0;
+  Appender app;
   for (u64 base = (u64)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
     u64 i = base + lane_id();
     bool take = false;
@@ -198,8 +238,9 @@ __device__ void seed_phase(const BfsParams &p, u64 *stat) {
         if (take) mf += d;
       }
     }
-    warp_append(take, entry, &p.ctl->n_list[0], p.list0);
+    warp_append(p, app, take, entry, &p.ctl->n_list[0], p.list0);
   }
+  append_close(p, app, p.list0);
   W = warp_sum(W);
   N = warp_sum(N);
   mf = warp_sum(mf);
@@ -249,14 +290,16 @@ __device__ void push_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u64 n_c
   const u32 Q = p.Q, n1 = p.n + 1;
   const u32 lane = lane_id();
   u64 edges = 0, rows = 0, entries = 0;
+  Appender app;
   for (;;) {
     u64 base = 0;
     if (lane == 0) base = atomicAdd(&p.ctl->cursor[cur], 32ull);
     base = __shfl_sync(FULL_MASK, base, 0);
     if (base >= n_cur) break;
     u64 idx = base + lane;
-    bool valid = idx < n_cur;
-    u64 e = valid ? __ldcg(&list[idx]) : 0;
+    u64 e = idx < n_cur ? __ldcg(&list[idx]) : NO_ENTRY;
+    bool valid = e != NO_ENTRY;
+    if (!valid) e = 0;
     u32 gq = (u32)(e >> 32), v = (u32)e;
     u32 g = gq / Q, q = gq - g * Q;
     Word<NW> fm;
@@ -327,10 +370,11 @@ __device__ void push_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u64 n_c
           w = __ldg(p.out_col + o_beg + (k - o_pre));
           take = relax<NW>(p, FB, o_gq, w, ofm, stamp);
         }
-        warp_append(take, ((u64)o_gq << 32) | w, &p.ctl->n_list[nxt], nlist);
+        warp_append(p, app, take, ((u64)o_gq << 32) | w, &p.ctl->n_list[nxt], nlist);
       }
     }
   }
+  append_close(p, app, nlist);
   edges = warp_sum(edges);
   rows = warp_sum(rows);
   entries = warp_sum(entries);
@@ -350,6 +394,7 @@ __device__ void spill_phase(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 st
   const u32 lane = lane_id();
   const u64 count = min(*(volatile unsigned long long *)&p.ctl->spill_count[cur], (unsigned long long)p.spill_cap);
   u64 edges = 0;
+  Appender app;
   for (;;) {
     u64 r = 0;
     if (lane == 0) r = atomicAdd(&p.ctl->spill_cursor[cur], 1ull);
@@ -371,9 +416,10 @@ __device__ void spill_phase(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 st
         w = __ldg(p.out_col + b + k);
         take = relax<NW>(p, FB, tgq, w, fm, stamp);
       }
-      warp_append(take, ((u64)tgq << 32) | w, &p.ctl->n_list[nxt], nlist);
+      warp_append(p, app, take, ((u64)tgq << 32) | w, &p.ctl->n_list[nxt], nlist);
     }
   }
+  append_close(p, app, nlist);
   edges = warp_sum(edges);
   stat[ST_GROUP_EDGES] += edges;
   stat[ST_ALG_BYTES] += edges * (4 + 8 * NW);
@@ -381,11 +427,12 @@ __device__ void spill_phase(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 st
 
 // Bottom-up work for target (q2, w) over in-edges [beg, end) of one
 // transition group with active source states `from`: every lane ORs the
-// gathered frontier words of its PER words into acc.  A lane stops gathering
-// once acc covers all its lanes not yet visited (nothing more can be found);
-// the sub-warp (lanes sg_mask) leaves the row when all its lanes have.
-// Returns the in-edges examined.
-template <int NW, int PER>
+// gathered frontier words of its PER words into acc.  With EARLY (one lane
+// group: few enough lanes that a vertex can run out of unvisited ones) a lane
+// stops gathering once acc covers all its lanes not yet visited, and the
+// sub-warp (lanes sg_mask) leaves the row when all its lanes have.  Returns
+// the in-edges examined.
+template <int NW, int PER, bool EARLY>
 __device__ __forceinline__ u32 gather_row(const BfsParams &p, const u64 *F, const u32 *bits, u32 from, u32 beg,
                                           u32 end, u32 lane_off, bool lane_on, u32 sg_mask,
                                           const u64 (&vis)[PER], u64 (&acc)[PER], u32 &gathers) {
@@ -397,8 +444,8 @@ __device__ __forceinline__ u32 gather_row(const BfsParams &p, const u64 *F, cons
     for (int k = 0; k < PER; k++) d &= (acc[k] | vis[k]) == ~0ull;
     return d;
   };
-  bool fin = !lane_on || done();
-  if ((__ballot_sync(sg_mask, !fin) & sg_mask) == 0) return 0;
+  bool fin = !lane_on || (EARLY && done());
+  if (EARLY && (__ballot_sync(sg_mask, !fin) & sg_mask) == 0) return 0;
   u32 i = beg;
   // four in-edges per step keep four gathers in flight
   for (; i + 4 <= end; i += 4) {
@@ -431,9 +478,9 @@ __device__ __forceinline__ u32 gather_row(const BfsParams &p, const u64 *F, cons
                     (h3 ? __ldcg(f3) : 0ull);
         }
       }
-      fin = done();
+      if (EARLY) fin = done();
     }
-    if ((__ballot_sync(sg_mask, !fin) & sg_mask) == 0) return i + 4 - beg;
+    if (EARLY && (__ballot_sync(sg_mask, !fin) & sg_mask) == 0) return i + 4 - beg;
   }
   for (; i < end; i++) {
     u32 v = __ldg(p.in_col + i);
@@ -454,9 +501,9 @@ __device__ __forceinline__ u32 gather_row(const BfsParams &p, const u64 *F, cons
 // frontier word (atomically: chunks of long rows of the same vertex may run
 // concurrently); one lane per group claims the list entry.
 template <int NW, int PER>
-__device__ __forceinline__ void pull_finish(const BfsParams &p, u64 *FB, u64 *nlist, u32 nxt, u32 q2, u32 w, u32 stamp,
-                                            u32 lane, bool lane_on, u32 my_g, const u64 (&vis)[PER],
-                                            const u64 (&acc)[PER]) {
+__device__ __forceinline__ void pull_finish(const BfsParams &p, Appender &app, u64 *FB, u64 *nlist, u32 nxt, u32 q2,
+                                            u32 w, u32 stamp, u32 lane, bool lane_on, u32 my_g,
+                                            const u64 (&vis)[PER], const u64 (&acc)[PER]) {
   const u64 base = ((u64)q2 * p.n + w) * p.G * NW + (u64)lane * PER;
   bool take = false;
   bool nz = false;
@@ -479,7 +526,7 @@ __device__ __forceinline__ void pull_finish(const BfsParams &p, u64 *FB, u64 *nl
     if (gnz && lane_on && (lane % (NW / PER)) == 0)
       take = atomicMax(p.claim + (((u64)q2 * p.n + w) * p.G + my_g), stamp) < stamp;
   }
-  warp_append(take, ((u64)(my_g * p.Q + q2) << 32) | w, &p.ctl->n_list[nxt], nlist);
+  warp_append(p, app, take, ((u64)(my_g * p.Q + q2) << 32) | w, &p.ctl->n_list[nxt], nlist);
 }
 
 // Bottom-up expansion.  Light rows: one vertex per sub-warp of SW lanes (the
@@ -489,7 +536,7 @@ __device__ __forceinline__ void pull_finish(const BfsParams &p, u64 *FB, u64 *nl
 // chunk taken dynamically over the (target state, transition group) pairs
 // whose source states are active; the sub-warps split the chunk's edges and
 // OR their gathers together.
-template <int NW>
+template <int NW, bool EARLY>
 __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 active, u32 stamp, const u32 *bits,
                            u64 *stat) {
   constexpr int PER = (NW >= 2) ? 2 : 1;
@@ -513,6 +560,7 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
   const bool chunked = p.hchunk != nullptr;
   const u64 gword = 8ull * NW * p.G;  // bytes of the G words of one (state, vertex)
   u64 edges = 0, words = 0, bytes = 0;
+  Appender app;
 
   for (u64 b64 = warp * VPW; b64 < n; b64 += n_warps * VPW) {
     const u64 w64 = b64 + sg;
@@ -527,6 +575,29 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
         const u32 *off = p.in_off + (u64)l * n1 + w;
         const u32 len = __ldg(off + 1) - __ldg(off);
         any = len > 0 && (len < HEAVY_ROW || !chunked);
+      }
+      if (bits) {
+        // sparse frontier: a vertex none of whose in-neighbours is in it is
+        // skipped before its visited words are read (the sub-warp's lanes
+        // test the in-edges in turn: a column id and a bitmap word each)
+        bool hit = false;
+        for (u32 j = gb; j < ge && !hit && any; j++) {
+          const u32 l = p.q.in_label[j];
+          const u32 from = p.q.in_from[j] & active;
+          if (!from || l >= p.L) continue;
+          const u32 *off = p.in_off + (u64)l * n1 + w;
+          const u32 beg = __ldg(off), end = __ldg(off + 1);
+          if (end - beg >= HEAVY_ROW && chunked) continue;
+          for (u32 i = beg + li; i < end && !hit; i += SW) {
+            const u32 u = __ldg(p.in_col + i);
+            bytes += 4 + 4 * __popc(from);
+            for (u32 fb = from; fb && !hit; fb &= fb - 1) {
+              const u64 bi = (u64)(__ffs(fb) - 1) * n + u;
+              hit = (__ldcg(bits + (bi >> 5)) >> (bi & 31)) & 1u;
+            }
+          }
+        }
+        any = (__ballot_sync(FULL_MASK, hit) & sg_mask) != 0;
       }
       const u64 base = ((u64)q2 * n + w) * wpv + lane_off;
       u64 vis[PER];
@@ -551,7 +622,7 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
           const u32 beg = __ldg(off), end = __ldg(off + 1);
           if (end - beg >= HEAVY_ROW && chunked) continue;
           u32 gat = 0;
-          const u32 ex = gather_row<NW, PER>(p, F, bits, from, beg, end, lane_off, lane_on, sg_mask, vis, acc, gat);
+          const u32 ex = gather_row<NW, PER, EARLY>(p, F, bits, from, beg, end, lane_off, lane_on, sg_mask, vis, acc, gat);
           edges += (li == 0) ? ex : 0;
           // column ids, frontier-bit words when tested, gathered frontier words
           bytes += (li == 0) ? 8 + (u64)ex * (4 + (bits ? 4 * __popc(from) : 0)) + (u64)gat * gword : 0;
@@ -559,7 +630,7 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
         words += (li == 0);
         bytes += (li == 0) ? gword : 0;
       }
-      pull_finish<NW, PER>(p, FB, nlist, nxt, q2, w, stamp, li, lane_on && work, my_g, vis, acc);
+      pull_finish<NW, PER>(p, app, FB, nlist, nxt, q2, w, stamp, li, lane_on && work, my_g, vis, acc);
     }
   }
 
@@ -605,7 +676,7 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
       const u32 len = end - beg, per = (len + VPW - 1) / VPW;
       const u32 sb = beg + min(len, sg * per), se = beg + min(len, (sg + 1) * per);
       u32 gat = 0;
-      const u32 ex = gather_row<NW, PER>(p, F, bits, from, sb, se, lane_off, lane_on, sg_mask, vis, acc, gat);
+      const u32 ex = gather_row<NW, PER, EARLY>(p, F, bits, from, sb, se, lane_off, lane_on, sg_mask, vis, acc, gat);
       for (u32 o = SW; o < 32; o <<= 1) {
 #pragma unroll
         for (int k = 0; k < PER; k++) acc[k] |= __shfl_xor_sync(FULL_MASK, acc[k], o);
@@ -615,9 +686,10 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
       edges += (lane == 0) ? ex_all : 0;
       bytes += (lane == 0) ? 12 + gword + ex_all * (4 + (bits ? 4 * __popc(from) : 0)) + gat_all * gword : 0;
       words += (lane == 0);
-      pull_finish<NW, PER>(p, FB, nlist, nxt, q2s, w, stamp, li, lane_on && sg == 0, my_g, vis, acc);
+      pull_finish<NW, PER>(p, app, FB, nlist, nxt, q2s, w, stamp, li, lane_on && sg == 0, my_g, vis, acc);
     }
   }
+  append_close(p, app, nlist);
   stat[ST_PULL_EDGES] += warp_sum(edges);
   stat[ST_PULL_VERTICES] += warp_sum(words);
   stat[ST_ALG_BYTES] += warp_sum(bytes);
@@ -625,8 +697,11 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
 
 // Commit of a level: fold the new frontier words into VIS, count work, note
 // the DFA states present in the new frontier, clear the old frontier words.
+// set_bits: the next frontier may be sparse enough for bottom-up levels to
+// test its bitmap, so its bits are set; clear_bits: this level's bits were set.
 template <int NW>
-__device__ void commit_phase(const BfsParams &p, int lp, u32 nxt, u64 n_cur, u64 *stat) {
+__device__ void commit_phase(const BfsParams &p, int lp, u32 nxt, u64 n_cur, bool set_bits, bool clear_bits,
+                             u64 *stat) {
   const u64 *list = lp ? p.list1 : p.list0;
   const u64 *nlist = lp ? p.list0 : p.list1;
   u64 *F = lp ? p.fr1 : p.fr0;
@@ -639,6 +714,7 @@ __device__ void commit_phase(const BfsParams &p, int lp, u32 nxt, u64 n_cur, u64
   u32 states = 0;
   for (u64 j = tid; j < n_next; j += stride) {
     u64 e = __ldcg(&nlist[j]);
+    if (e == NO_ENTRY) continue;
     u32 gq = (u32)(e >> 32), w = (u32)e;
     u32 g = gq / Q, q = gq - g * Q;
     u64 wi = widx<NW>(p, g, q, w);
@@ -647,7 +723,7 @@ __device__ void commit_phase(const BfsParams &p, int lp, u32 nxt, u64 n_cur, u64
 #pragma unroll
     for (int t = 0; t < NW; t++) v.w[t] |= m.w[t];
     store_w<NW>(p.vis + wi, v);
-    if (p.fbits) {
+    if (set_bits) {
       const u64 bi = (u64)q * p.n + w;
       atomicOr(p.fbits + (lp ? 0 : p.fbits_words) + (bi >> 5), 1u << (bi & 31));
     }
@@ -664,10 +740,11 @@ __device__ void commit_phase(const BfsParams &p, int lp, u32 nxt, u64 n_cur, u64
   for (int t = 0; t < NW; t++) zero.w[t] = 0;
   for (u64 j = tid; j < n_cur; j += stride) {
     u64 e = __ldcg(&list[j]);
+    if (e == NO_ENTRY) continue;
     u32 gq = (u32)(e >> 32);
     u32 g = gq / Q;
     store_w<NW>(F + widx<NW>(p, g, gq - g * Q, (u32)e), zero);
-    if (p.fbits) {
+    if (clear_bits) {
       // the retired frontier's bitmap: every set bit belongs to one of these entries
       const u64 bi = (u64)(gq - g * Q) * p.n + (u32)e;
       p.fbits[(lp ? p.fbits_words : 0) + (bi >> 5)] = 0u;
@@ -764,12 +841,24 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) msbfs_kernel(const __grid_cons
       }
     } else {
       // a sparse frontier: test the frontier bitmap before each gather
+      // (implies n_cur * 4 < n * Q, so the commit that built this frontier set its bits)
       const bool sparse = p.fbits && n_cur * 4 < (u64)p.n * __popc(active);
       const u32 *bits = sparse ? p.fbits + (lp ? p.fbits_words : 0) : nullptr;
-      pull_level<NW>(p, lp, cur, nxt, active, stamp, bits, stat);
+      if (p.G == 1)
+        pull_level<NW, true>(p, lp, cur, nxt, active, stamp, bits, stat);
+      else
+        pull_level<NW, false>(p, lp, cur, nxt, active, stamp, bits, stat);
       if (!grid_barrier(c, p.nblocks, p.time_limit_ns)) return;
     }
-    commit_phase<NW>(p, lp, nxt, n_cur, stat);
+    {
+      // bitmaps only where a bottom-up level may test them: a frontier with
+      // fewer than n * Q / 4 entries (the seeds always set theirs)
+      const u64 n_next = *(volatile unsigned long long *)&c->n_list[nxt];
+      const u64 sparse_cap = (u64)p.n * p.Q;
+      const bool set_bits = p.fbits && n_next * 4 < sparse_cap;
+      const bool clear_bits = p.fbits && (level == 0 || n_cur * 4 < sparse_cap);
+      commit_phase<NW>(p, lp, nxt, n_cur, set_bits, clear_bits, stat);
+    }
     if (!grid_barrier(c, p.nblocks, p.time_limit_ns)) return;
   }
   if (lane_id() == 0) {
@@ -802,6 +891,33 @@ cudaError_t launch_vis_init(int nw, const BfsParams &p, const unsigned long long
     vis_init_kernel<1><<<(unsigned)blocks, 256, 0, st>>>(p.vis, total, p.G, empty);
   else
     vis_init_kernel<4><<<(unsigned)blocks, 256, 0, st>>>(p.vis, total, p.G, empty);
+  return cudaGetLastError();
+}
+
+// flag[i] = 1 when start vertex srcs[i] has an edge on a label of label_mask
+// in the traversal's forward direction (off = the forward offsets).
+__global__ void source_filter_kernel(const u32 *__restrict__ off, u32 n, u32 L, unsigned long long label_mask,
+                                     const u32 *__restrict__ srcs, u64 count, unsigned char *__restrict__ flag) {
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (u64)gridDim.x * blockDim.x) {
+    const u32 s = srcs[i];
+    unsigned char f = 0;
+    for (unsigned long long m = label_mask; m && !f; m &= m - 1) {
+      const u32 l = __ffsll(m) - 1;
+      if (l >= L) break;
+      const u32 *o = off + (u64)l * (n + 1) + s;
+      f = __ldg(o + 1) > __ldg(o);
+    }
+    flag[i] = f;
+  }
+}
+
+cudaError_t launch_source_filter(const uint32_t *off, uint32_t n, uint32_t L, unsigned long long label_mask,
+                                 const uint32_t *srcs, unsigned long long count, unsigned char *flag,
+                                 cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  u64 blocks = (count + 255) / 256;
+  if (blocks > 152ull * 16) blocks = 152ull * 16;
+  source_filter_kernel<<<(unsigned)blocks, 256, 0, st>>>(off, n, L, label_mask, srcs, count, flag);
   return cudaGetLastError();
 }
 

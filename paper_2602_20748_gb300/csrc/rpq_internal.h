@@ -92,6 +92,9 @@ enum StatIdx {
 };
 
 constexpr int TRACE_LEVELS = 64;
+constexpr unsigned long long NO_ENTRY = ~0ull;      // a reserved list slot left empty
+constexpr unsigned int ERR_LIST_OVERFLOW = 1000u;   // BfsCtl::err: an append ran past list_cap
+constexpr unsigned int APPEND_SEG = 128;             // list slots a warp reserves at a time
 
 struct BfsCtl {
   unsigned int bar_count;
@@ -150,6 +153,10 @@ struct BfsParams {
   // gathering a neighbour's frontier words.  Zero between searches.
   unsigned int *fbits;
   unsigned long long fbits_words;
+  // List appends: a warp reserves append_seg slots at a time (0: one atomic
+  // add per warp-aggregated append); unused reserved slots hold NO_ENTRY.
+  unsigned int append_seg;
+  unsigned long long list_cap;  // entries per list (overflow sets ERR_LIST_OVERFLOW)
   BfsCtl *ctl;
   unsigned int stamp_base;     // claim stamps continue across launches
   unsigned int nblocks;
@@ -162,6 +169,10 @@ struct BfsParams {
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_vis_init(int nw, const BfsParams &p, const unsigned long long *empty, cudaStream_t st);
 cudaError_t launch_msbfs(int nw, const BfsParams &p, int blocks, int threads, cudaStream_t st);
+// flag[i] = whether srcs[i] has an edge (offsets `off`, per label) on a label of label_mask.
+cudaError_t launch_source_filter(const uint32_t *off, uint32_t n, uint32_t L, unsigned long long label_mask,
+                                 const uint32_t *srcs, unsigned long long count, unsigned char *flag,
+                                 cudaStream_t st);
 int msbfs_max_blocks(int nw, int threads, int *blocks_per_sm, int *sms);
 
 struct EmitParams {

@@ -162,6 +162,8 @@ extern "C" int run_rpq_static(rpq_ctx *ctx, const rpq_graph *g, const rpq_query 
   p.claim = nullptr;  // one 64-bit word per lane group: claims come from the OR itself
   p.list0 = list0;
   p.list1 = list1;
+  p.list_cap = words;  // one append per (state, vertex) per level (no segments here)
+  p.append_seg = 0;
   p.ctl = ctl;
   p.stamp_base = 0;
   const int blocks = ctx_bfs_blocks(ctx, 1);

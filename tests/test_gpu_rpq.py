@@ -319,3 +319,25 @@ def test_spill_capacity_overflow_falls_back_in_place():
         want = oracle.rpq(og, regex, sources=sources)
         for mode in (0, rpq.RPQ_FORCE_PUSH):
             check(c3, g, og, regex, sources=sources, mode=mode, want=want)
+
+
+@pytest.mark.parametrize("regex", ["a*", "a.b*", "(a|b)+", "b?"])
+@pytest.mark.parametrize("flags", ["count", "rows"])
+def test_edgeless_start_vertices_skipped(ctx, regex, flags):
+    """Long source lists drop start vertices without an edge on the start
+    state's labels; their (s, s) rows (when the start state accepts) are still
+    counted and digested, and rows, digests, W and N stay exact."""
+    n = 9000
+    src, dst, lab = synth.random_graph(n, 3000, 3, seed=77)  # most vertices have no out-edge
+    g = rpq.load_graph(ctx, n, 3, src, dst, lab)
+    og = oracle.Graph(n, 3, src, dst, lab)
+    want = oracle.rpq(og, regex)
+    q = rpq.compile_rpq(ctx, regex)
+    f = rpq.RPQ_COUNT_ONLY if flags == "count" else rpq.RPQ_MATERIALIZE
+    r = rpq.run_rpq(ctx, g, q, None, flags=f)
+    cnt, s, x = oracle.pair_digest(want.rows)
+    assert rpq.result_info(r) == (cnt, 2, s, x)
+    st = rpq.result_stats(r)
+    assert st["product_edges"] == want.W and st["product_vertices"] == want.N
+    if flags == "rows":
+        assert np.array_equal(rpq.fetch_pairs(r), want.rows)
