@@ -395,6 +395,7 @@ def bench_batch(args):
     t0 = time.perf_counter()
     threads, per_launch = rpq.rpq_autotune_batch(ctx, g, qs, sources)
     tune_s = time.perf_counter() - t0
+    evict_at = rpq.rpq_get_option(ctx, "batch_evict")
     for _ in range(args.warmup):
         rpq.run_rpq_batch(ctx, g, qs, sources, flags=rpq.RPQ_PER_QUERY).free()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -402,7 +403,7 @@ def bench_batch(args):
     sampler.start()
     torch.cuda.synchronize()
     ev0.record()
-    W = rows = launches = 0
+    W = rows = launches = evicted = 0
     r = None
     for k in range(args.steps):
         if r is not None:
@@ -411,6 +412,7 @@ def bench_batch(args):
         st = rpq.result_stats(r)
         W += st["product_edges"]
         launches += st["launches"]
+        evicted += st["evicted"]
         rows += rpq.result_info(r)[0]
     ev1.record()
     torch.cuda.synchronize()
@@ -438,7 +440,8 @@ def bench_batch(args):
         "config": {"workload": "rmat22-batched-single-source", "queries": 4096, "vertices": n,
                    "generated_edges": 1 << 26, "labels": 8, "zipf_s": 1.2, "mode": "per-query count + digest",
                    "autotuned_threads": threads, "autotuned_queries_per_launch": per_launch,
-                   "autotune_s": round(tune_s, 3)},
+                   "autotuned_evict_at": evict_at, "autotune_s": round(tune_s, 3)},
+        "evicted_per_step": evicted // max(1, args.steps),
         "batched_latency_ms": ms, "product_edges_per_s": W / (ms * args.steps / 1000.0),
         "rows_per_step": rows // args.steps,
         "plain": {"queries_per_s": plain_qps, "p50_ms": 1000 * float(np.percentile(lat, 50)),

@@ -119,6 +119,9 @@ int rpq_set_stream(rpq_ctx *ctx, void *cuda_stream);
  *   "batch_evict"  run_rpq_batch with RPQ_PER_QUERY: product vertices after
  *                  which a query leaves the shared launch (0: never) */
 int rpq_set_option(rpq_ctx *ctx, const char *name, double value);
+/* Reads a tunable set by rpq_set_option or chosen by rpq_autotune_batch
+ * (same names, plus "batch_threads" and "batch_queries_per_launch"). */
+int rpq_get_option(const rpq_ctx *ctx, const char *name, double *value);
 
 /* ---- graph store (Section 2.1 data graph; Section 2.4 keeps one grid per
  *      edge label -- here one CSR per edge label) ----------------------------- */
@@ -210,7 +213,7 @@ int run_rpq_batch(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_queries, const rp
 
 /* Times run_rpq_batch (RPQ_PER_QUERY) on a sample of the given batch (its
  * first 512 queries) for each candidate block size (256, 512 threads) and
- * eviction threshold (2^12, 2^14, 2^16, 2^18 product vertices), keeps the
+ * eviction threshold (2^14, 2^16, 2^18, 2^20, 2^22 product vertices, never), keeps the
  * fastest on the context for later run_rpq_batch calls and reports it (out
  * pointers may be NULL; queries per launch is reported as set).
  * Errors: as run_rpq_batch. */
@@ -276,9 +279,9 @@ int run_crpq(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_vars, const int32_t *v
  * waiting single-source request it can admit (up to max_batch, and only while
  * the admitted queries' visited bitmaps fit its memory share) into one launch,
  * so requests that arrive while a batch runs join the next one; the other
- * runs all-pairs requests (in slices of start vertices) and CRPQs, oldest
- * first.  Replies carry the row count and digest the standalone call would
- * report (results are counted, not kept) and the request's latencies.  The
+ * runs all-pairs requests and CRPQs, oldest first.  Replies carry the row
+ * count and digest the standalone call would report (results are counted,
+ * not kept) and the request's latencies.  The
  * graph, queries and atom queries must stay alive until their requests have
  * been waited for.  mem_budget_bytes = 0 uses 80% of the free device memory. */
 typedef struct rpq_server rpq_server;
@@ -364,6 +367,8 @@ typedef struct {
   uint64_t alg_bytes;        /* bytes the traversal kernels must move for the
                                 work they did (column ids, offsets, visited and
                                 frontier words, list entries)                 */
+  uint64_t evicted;          /* run_rpq_batch RPQ_PER_QUERY: queries that left
+                                the shared launch                            */
 } rpq_stats;
 
 int result_stats(const rpq_result *r, rpq_stats *out);

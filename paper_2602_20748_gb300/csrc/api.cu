@@ -735,6 +735,28 @@ int rpq_set_option(rpq_ctx *ctx, const char *name, double value) {
   return RPQ_OK;
 }
 
+int rpq_get_option(const rpq_ctx *ctx, const char *name, double *value) {
+  if (!ctx || !name || !value) return RPQ_ERR_INVALID_ARG;
+  const std::string n(name);
+  if (n == "alpha")
+    *value = ctx->alpha;
+  else if (n == "grid_share")
+    *value = ctx->grid_share;
+  else if (n == "max_groups")
+    *value = ctx->max_groups;
+  else if (n == "time_limit_s")
+    *value = ctx->time_limit_ns * 1e-9;
+  else if (n == "batch_evict")
+    *value = (double)ctx->batch.evict_at;
+  else if (n == "batch_threads")
+    *value = ctx->batch.threads;
+  else if (n == "batch_queries_per_launch")
+    *value = ctx->batch.queries_per_launch;
+  else
+    return RPQ_ERR_INVALID_ARG;
+  return RPQ_OK;
+}
+
 int load_graph(rpq_ctx *ctx, uint32_t n_vertices, uint32_t n_labels, uint64_t n_edges, const uint32_t *src,
                const uint32_t *dst, const uint16_t *label, const uint8_t *vertex_label, rpq_graph **out) {
   if (!ctx || !out) return set_err(ctx, RPQ_ERR_INVALID_ARG, "null argument");
@@ -986,7 +1008,7 @@ int rpq_autotune_batch(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_queries, con
   BatchTuning best = ctx->batch;
   double best_s = -1;
   const int threads[] = {256, 512};
-  const uint64_t evicts[] = {1ull << 12, 1ull << 14, 1ull << 16, 1ull << 18};
+  const uint64_t evicts[] = {1ull << 14, 1ull << 16, 1ull << 18, 1ull << 20, 1ull << 22, 0};
   for (int t : threads)
     for (uint64_t ev : evicts) {
       BatchTuning cand = ctx->batch;

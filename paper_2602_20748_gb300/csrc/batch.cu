@@ -815,6 +815,7 @@ int batch_run(rpq_ctx *ctx, const rpq_graph *g, uint32_t nq, const rpq_query *co
     out->regroup_launches += launches[h];
   }
   out->evicted += out->evicted_idx.size();
+  out->stats.evicted += out->evicted_idx.size();
   // with per-query summaries the totals are theirs: rows and digests of the
   // (source, y) rows every query would report alone
   out->count = out->dsum = out->dxor = 0;

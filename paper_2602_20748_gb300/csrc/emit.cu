@@ -34,7 +34,7 @@ __global__ void emit_kernel(const EmitParams p) {
   u64 cnt = 0, hsum = 0, hxor = 0;
   // count pass: per-lane counts of this thread's vertices as bit planes
   // (EMIT_TILES <= 2^CNT_PLANES - 1 vertices per thread)
-  constexpr int CNT_PLANES = 6;
+  constexpr int CNT_PLANES = 8;
   static_assert(EMIT_TILES < (1 << CNT_PLANES), "count planes too narrow");
   u32 planes[CNT_PLANES];
 #pragma unroll

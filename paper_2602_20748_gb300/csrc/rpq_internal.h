@@ -188,7 +188,7 @@ struct EmitParams {
   uint32_t *dst;                 // output destinations (write pass)
   unsigned long long *digest;    // [2]: sum, xor
 };
-constexpr int EMIT_TILES = 32;  // 32-vertex tiles per segment
+constexpr int EMIT_TILES = 128;  // 32-vertex tiles per segment
 constexpr int EMIT_SEG = 32 * EMIT_TILES;
 cudaError_t launch_emit(int nw, bool write, bool digest, const EmitParams &p, cudaStream_t st);
 // Digest (sum, xor of splitmix64(src << 32 | dst)) of a materialized chunk's

@@ -11,7 +11,8 @@
 //     that arrive while a batch is on the device join the next batch: a slot
 //     opens as soon as the running batch finishes.
 //   * the bulk worker takes all-pairs and CRPQ requests one at a time, oldest
-//     first, and evaluates all-pairs requests in slices of start vertices.
+//     first; an all-pairs request is one evaluation over every start vertex
+//     (launches of 4,096), which a cancel stops before its next launch.
 // Every request gets its row count and row digest, as the standalone call
 // would report them, and its queueing / service / total latency.
 #include <algorithm>
@@ -62,7 +63,6 @@ struct rpq_server {
   const rpq_graph *g = nullptr;
   uint64_t single_budget = 0;
   uint32_t max_batch = 4096;
-  uint32_t slice = 4096;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Req *> singles, bulk;
@@ -130,7 +130,6 @@ void single_worker(rpq_server *s) {
 }
 
 void bulk_worker(rpq_server *s) {
-  const rpq::DevGraph &dg = rpq::graph_dev(s->g);
   for (;;) {
     Req *r = nullptr;
     {
@@ -145,21 +144,14 @@ void bulk_worker(rpq_server *s) {
     int rc = RPQ_OK;
     uint64_t count = 0, dsum = 0, dxor = 0;
     if (r->kind == RPQ_REQ_ALLPAIRS) {
-      for (uint32_t b = 0; b < dg.n && rc == RPQ_OK; b += s->slice) {
-        if (r->ticket <= s->cancel_upto.load()) {
-          rc = RPQ_ERR_CANCELLED;
-          break;
-        }
-        rpq_result *res = nullptr;
-        rc = run_rpq_range(s->ctx_bulk, s->g, r->q, b, std::min<uint32_t>(dg.n, b + s->slice), RPQ_COUNT_ONLY, &res);
-        if (rc == RPQ_OK) {
-          uint64_t c, hs, hx;
-          result_info(res, &c, nullptr, &hs, &hx);
-          count += c;
-          dsum += hs;
-          dxor ^= hx;
-          free_result(res);
-        }
+      // one all-pairs evaluation (start vertices without a usable edge are
+      // dropped up front; the rest run in full launches); a cancel stops it
+      // before its next launch
+      rpq_result *res = nullptr;
+      rc = run_rpq(s->ctx_bulk, s->g, r->q, nullptr, 0, RPQ_COUNT_ONLY, &res);
+      if (rc == RPQ_OK) {
+        result_info(res, &count, nullptr, &dsum, &dxor);
+        free_result(res);
       }
     } else {
       rpq_result *res = nullptr;

@@ -65,7 +65,7 @@ class rpq_stats(ctypes.Structure):
         "product_edges", "product_vertices", "levels", "push_levels", "pull_levels", "group_edges", "group_rows",
         "group_vertices", "pull_edges", "pull_vertices", "lane_words", "lane_groups")] + [
         ("bfs_ms", ctypes.c_double), ("emit_ms", ctypes.c_double), ("bfs_launches", ctypes.c_uint64),
-        ("launches", ctypes.c_uint64), ("alg_bytes", ctypes.c_uint64)]
+        ("launches", ctypes.c_uint64), ("alg_bytes", ctypes.c_uint64), ("evicted", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -352,6 +352,16 @@ EXPORTED += ["rpq_set_option", "rpq_server_create", "rpq_server_submit", "rpq_se
 
 def rpq_set_option(ctx: Context, name: str, value: float):
     ctx.check(_lib.rpq_set_option(ctx.h, name.encode(), float(value)))
+
+
+_lib.rpq_get_option.argtypes = [c_void_p, ctypes.c_char_p, P(ctypes.c_double)]
+EXPORTED += ["rpq_get_option"]
+
+
+def rpq_get_option(ctx: Context, name: str) -> float:
+    v = ctypes.c_double()
+    ctx.check(_lib.rpq_get_option(ctx.h, name.encode(), ctypes.byref(v)))
+    return v.value
 
 
 class Server:

@@ -108,3 +108,14 @@ def test_device_context_fails_loudly_without_gpu():
     with pytest.raises(rpq.RPQError) as e:
         rpq.Context(device=0)
     assert e.value.code == rpq.RPQ_ERR_CUDA
+
+
+def test_options_round_trip(hctx):
+    rpq.rpq_set_option(hctx, "alpha", 8)
+    assert rpq.rpq_get_option(hctx, "alpha") == 8
+    rpq.rpq_set_option(hctx, "batch_evict", 4096)
+    assert rpq.rpq_get_option(hctx, "batch_evict") == 4096
+    assert rpq.rpq_get_option(hctx, "batch_threads") in (128, 256, 512)
+    with pytest.raises(rpq.RPQError):
+        rpq.rpq_get_option(hctx, "no_such_option")
+    rpq.rpq_set_option(hctx, "alpha", 16)
