@@ -54,6 +54,7 @@ struct rpq_ctx {
   uint32_t stamp = 0;
   int sms = 0;
   int bpsm[2] = {0, 0};  // resident traversal blocks per SM for NW = 1, 4
+  int bpsm_multi = 0;    // the same for the per-group-automata kernel (set on first use)
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   float alpha = 16.0f;
   uint64_t time_limit_ns = 20ull * 1000 * 1000 * 1000;
@@ -406,7 +407,7 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
       u64 *ls = nullptr;
       int rc2 = dalloc(ctx, &ls, 3ull * n_lanes);
       if (rc2) return rc2;
-      EmitParams ep;
+      EmitParams ep{};
       std::memset(&ep, 0, sizeof(ep));
       ep.vis = w.vis;
       ep.n = n;
@@ -471,7 +472,7 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
       dfree(ctx, tmp, tmpw);
       return rc;
     }
-    EmitParams ep;
+    EmitParams ep{};
     ep.vis = w.vis;
     ep.n = n;
     ep.G = Gb;
@@ -1236,6 +1237,192 @@ int rpq_lane_stats_for_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query
     stats->alg_bytes += r.stats.alg_bytes;
   }
   return rc;
+}
+
+// Count-only evaluation of up to 16 units in one launch, each unit a lane
+// group of its own (one 64-lane word, at most 64 start vertices, repeats
+// allowed) running its own automaton.  Per lane (rows, digest sum, digest
+// xor) in lane_stats, unit by unit in the units' source order; counters
+// added to *stats.  TOO_COMPLEX when the union of the automata needs more
+// transition entries than a descriptor holds (the caller then runs the units
+// apart).
+int rpq_lane_stats_multi(rpq_ctx *ctx, const rpq_graph *gr, const std::vector<MultiUnit> &units,
+                         std::vector<uint64_t> *lane_stats, rpq_stats *stats) {
+  const DevGraph &g = gr->g;
+  const uint32_t G = (uint32_t)units.size();
+  size_t total_lanes = 0;
+  for (const MultiUnit &u : units) {
+    if (u.srcs.size() > 64) return set_err(ctx, RPQ_ERR_INVALID_ARG, "a unit holds at most 64 start vertices");
+    total_lanes += u.srcs.size();
+  }
+  lane_stats->assign(3 * total_lanes, 0);
+  if (G == 0 || total_lanes == 0) return RPQ_OK;
+  if (G > 16) return set_err(ctx, RPQ_ERR_INVALID_ARG, "at most 16 units per launch");
+  const uint32_t n = g.n, L = g.L;
+  uint32_t Q = 0;
+  for (const MultiUnit &u : units) Q = std::max(Q, query_host(u.q).d.n_states);
+  if (Q == 0) return RPQ_OK;
+  // from_tab[(g * Q + q2) * L + l]: states of unit g reaching q2 on label l
+  std::vector<uint32_t> ft((size_t)G * Q * L, 0);
+  std::vector<QueryDesc> descs(G);
+  std::vector<uint32_t> finals(G);
+  for (uint32_t k = 0; k < G; k++) {
+    const HostQuery &hq = query_host(units[k].q);
+    descs[k] = hq.d;
+    finals[k] = hq.d.final_mask;
+    const uint32_t nl = hq.d.n_labels;
+    for (uint32_t q = 0; q < hq.d.n_states; q++)
+      for (uint32_t l = 0; l < std::min(nl, L); l++) {
+        const int32_t q2 = hq.next[(size_t)q * nl + l];
+        if (q2 >= 0) ft[((size_t)k * Q + q2) * L + l] |= 1u << q;
+      }
+  }
+  // the union automaton: bottom-up iteration order and cost estimates
+  QueryDesc un;
+  std::memset(&un, 0, sizeof(un));
+  un.n_states = Q;
+  un.n_labels = L;
+  uint32_t cnt = 0;
+  for (uint32_t q2 = 0; q2 < Q; q2++) {
+    un.in_begin[q2] = (uint16_t)cnt;
+    for (uint32_t l = 0; l < L; l++) {
+      uint32_t f = 0;
+      for (uint32_t k = 0; k < G; k++) f |= ft[((size_t)k * Q + q2) * L + l];
+      if (!f) continue;
+      if (cnt >= RPQ_MAX_TRANSITIONS) return set_err(ctx, RPQ_ERR_TOO_COMPLEX, "union automaton too large");
+      un.in_label[cnt] = (uint8_t)l;
+      un.in_from[cnt] = f;
+      cnt++;
+    }
+  }
+  un.in_begin[Q] = (uint16_t)cnt;
+  for (uint32_t k = 0; k < G; k++) un.final_mask |= finals[k];
+  if (ctx->bpsm_multi == 0 && msbfs_multi_max_blocks(BFS_THREADS_HOST, &ctx->bpsm_multi))
+    return set_err(ctx, RPQ_ERR_CUDA, "occupancy query failed");
+  const int blocks = ctx_sm_share(ctx) * ctx->bpsm_multi;
+  if (blocks <= 0) return set_err(ctx, RPQ_ERR_CUDA, "traversal kernel cannot be made resident");
+  const uint64_t slack = 2ull * blocks * (BFS_THREADS_HOST / 32) * APPEND_SEG;
+  const uint64_t words = (uint64_t)G * Q * n;
+  int rc = ensure_workspace(ctx, words, words + slack, 0, G * 64);
+  if (rc) return rc;
+  Workspace &w = ctx->ws;
+  // lanes: unit k's start vertices in lanes [64k, 64k + size); a unit with the
+  // empty language keeps its lanes empty (it has no rows and no product vertices)
+  std::vector<uint32_t> lanes((size_t)G * 64, NO_SOURCE);
+  std::vector<uint64_t> empty(G, 0);
+  for (uint32_t k = 0; k < G; k++) {
+    const bool live = query_host(units[k].q).d.n_states > 0;
+    for (uint32_t i = 0; i < 64; i++) {
+      if (live && i < units[k].srcs.size()) {
+        if (units[k].srcs[i] >= n) return set_err(ctx, RPQ_ERR_INVALID_ARG, "source id out of range");
+        lanes[(size_t)k * 64 + i] = units[k].srcs[i];
+      } else {
+        empty[k] |= 1ull << i;
+      }
+    }
+  }
+  QueryDesc *d_desc = nullptr;
+  u32 *d_ft = nullptr, *d_fin = nullptr;
+  u64 *ls = nullptr;
+  auto release = [&]() {
+    dfree(ctx, d_desc, G);
+    dfree(ctx, d_ft, ft.size());
+    dfree(ctx, d_fin, G);
+    dfree(ctx, ls, 3ull * G * 64);
+  };
+  if ((rc = dalloc(ctx, &d_desc, G)) || (rc = dalloc(ctx, &d_ft, ft.size())) || (rc = dalloc(ctx, &d_fin, G)) ||
+      (rc = dalloc(ctx, &ls, 3ull * G * 64))) {
+    release();
+    return rc;
+  }
+  cudaStream_t st = ctx->stream;
+  cudaError_t e = cudaMemcpyAsync(d_desc, descs.data(), G * sizeof(QueryDesc), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_ft, ft.data(), ft.size() * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_fin, finals.data(), G * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w.lanesrc, lanes.data(), lanes.size() * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w.empty, empty.data(), G * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ls, 0, 24ull * G * 64, st);
+  if (e != cudaSuccess) {
+    release();
+    return cuda_err(ctx, e, "multi upload");
+  }
+  BfsParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.out_off = g.out_off;
+  p.out_col = g.out_col;
+  p.in_off = g.in_off;
+  p.in_col = g.in_col;
+  p.hchunk = g.hchunk_in;
+  for (uint32_t l = 0; l <= g.L && l < g.hchunk_in_off.size(); l++) p.hchunk_off[l] = g.hchunk_in_off[l];
+  for (uint32_t l = 0; l < g.L; l++) p.label_edges[l] = g.label_edges[l];
+  p.n = n;
+  p.L = L;
+  p.G = G;
+  p.Q = Q;
+  p.lanesrc = w.lanesrc;
+  p.vis = w.vis;
+  p.fr0 = w.fr0;
+  p.fr1 = w.fr1;
+  p.claim = nullptr;  // one word per group: claims come from the OR itself
+  p.spill = w.spill;
+  p.spill_cap = ctx->spill_cap;
+  p.list0 = w.list0;
+  p.list1 = w.list1;
+  p.fbits = w.fbits;
+  p.fbits_words = w.fbits_words();
+  p.append_seg = APPEND_SEG;
+  p.list_cap = w.list_cap;
+  p.ctl = ctx->ctl;
+  p.stamp_base = ctx->stamp;
+  p.nblocks = (unsigned)blocks;
+  p.force = 0;
+  p.alpha = ctx->alpha;
+  p.time_limit_ns = ctx->time_limit_ns;
+  p.q = un;
+  p.qg = d_desc;
+  p.from_tab = d_ft;
+  EmitParams ep{};
+  ep.vis = w.vis;
+  ep.n = n;
+  ep.G = G;
+  ep.Q = Q;
+  ep.final_mask = un.final_mask;
+  ep.final_g = d_fin;
+  ep.lanesrc = w.lanesrc;
+  ep.segs = (n + EMIT_SEG - 1) / EMIT_SEG;
+  BfsCtl hctl;
+  std::vector<uint64_t> hls(3ull * G * 64);
+  if ((e = launch_vis_init(1, p, w.empty, st)) == cudaSuccess && (e = cudaMemsetAsync(ctx->ctl, 0, sizeof(BfsCtl), st)) == cudaSuccess &&
+      (e = cudaEventRecord(ctx->ev[0], st)) == cudaSuccess && (e = launch_msbfs_multi(p, blocks, BFS_THREADS_HOST, st)) == cudaSuccess &&
+      (e = cudaEventRecord(ctx->ev[1], st)) == cudaSuccess && (e = launch_emit_lane_stats(1, ep, ls, st)) == cudaSuccess &&
+      (e = cudaEventRecord(ctx->ev[2], st)) == cudaSuccess)
+    e = cudaMemcpyAsync(&hctl, ctx->ctl, sizeof(BfsCtl), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hls.data(), ls, hls.size() * 8, cudaMemcpyDeviceToHost, st);
+  release();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "multi-automaton launch");
+  if (hctl.err) return traversal_error(ctx, hctl.err);
+  ctx->stamp += (uint32_t)hctl.levels + 3;
+  size_t at = 0;
+  for (uint32_t k = 0; k < G; k++)
+    for (size_t i = 0; i < units[k].srcs.size(); i++, at++)
+      for (int c = 0; c < 3; c++) (*lane_stats)[3 * at + c] = hls[3 * ((size_t)k * 64 + i) + c];
+  if (stats) {
+    float ms_bfs = 0, ms_emit = 0;
+    cudaEventElapsedTime(&ms_bfs, ctx->ev[0], ctx->ev[1]);
+    cudaEventElapsedTime(&ms_emit, ctx->ev[1], ctx->ev[2]);
+    stats->product_edges += hctl.stats[ST_W];
+    stats->product_vertices += hctl.stats[ST_N];
+    stats->levels += hctl.levels;
+    stats->push_levels += hctl.stats[ST_PUSH_LEVELS];
+    stats->pull_levels += hctl.stats[ST_PULL_LEVELS];
+    stats->alg_bytes += hctl.stats[ST_ALG_BYTES];
+    stats->bfs_ms += ms_bfs;
+    stats->emit_ms += ms_emit;
+    stats->bfs_launches += 1;
+    stats->launches += 4;
+  }
+  return RPQ_OK;
 }
 
 void free_row_chunk(rpq_ctx *ctx, RowChunk &c) {

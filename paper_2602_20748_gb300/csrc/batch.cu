@@ -750,18 +750,46 @@ int batch_run(rpq_ctx *ctx, const rpq_graph *g, uint32_t nq, const rpq_query *co
     b0 += k;
   }
   if (!out->per_query) return RPQ_OK;
-  // Queries that left the batch: one multi-source (bit-sliced) evaluation per
-  // distinct automaton over the start vertices of its queries, with every
-  // lane's own row count and digest.
+  // Queries that left the batch, grouped by automaton, are evaluated by the
+  // direction-optimizing multi-source engine with every lane's own row count
+  // and digest (work items below).
   std::map<std::string, std::vector<uint32_t>> groups;
   for (uint32_t i : out->evicted_idx) {
     const QueryDesc &d = query_host(queries[i]).d;
     groups[std::string(reinterpret_cast<const char *>(&d), sizeof(d))].push_back(i);
   }
-  // the groups run side by side on helper contexts (own streams, a share of
-  // the SMs each), one host thread per helper taking groups in turn
-  std::vector<const std::vector<uint32_t> *> todo;
-  for (auto &kv : groups) todo.push_back(&kv.second);
+  // Work items, run side by side on helper contexts (own streams, a share of
+  // the SMs each), one host thread per helper taking items in turn:
+  //   * an automaton with more than 64 evicted queries: one bit-sliced launch
+  //     over its start vertices (256 lanes per word);
+  //   * smaller ones: units of one automaton and at most 64 start vertices,
+  //     16 units per multi-automaton launch (each unit a lane group running
+  //     its own automaton).
+  // One lane per query, in source order (a repeated start vertex gets a lane
+  // of its own, so the work counter stays the sum over queries).
+  struct Item {
+    std::vector<uint32_t> single;               // query indices, one automaton
+    std::vector<std::vector<uint32_t>> units;   // query indices per unit
+  };
+  std::vector<Item> todo;
+  Item pending;
+  for (auto &kv : groups) {
+    std::vector<uint32_t> members = kv.second;
+    std::sort(members.begin(), members.end(),
+              [&](uint32_t a, uint32_t b) { return sources[a] < sources[b] || (sources[a] == sources[b] && a < b); });
+    if (members.size() > 64) {
+      Item it;
+      it.single = members;
+      todo.push_back(std::move(it));
+      continue;
+    }
+    pending.units.push_back(members);
+    if (pending.units.size() == 16) {
+      todo.push_back(std::move(pending));
+      pending = Item();
+    }
+  }
+  if (!pending.units.empty()) todo.push_back(std::move(pending));
   const int k = (int)std::min<size_t>(REGROUP_STREAMS, todo.size());
   std::vector<rpq_ctx *> helpers;
   int rc = k > 1 ? ctx_helpers(ctx, k, &helpers) : RPQ_OK;
@@ -771,28 +799,55 @@ int batch_run(rpq_ctx *ctx, const rpq_graph *g, uint32_t nq, const rpq_query *co
   std::vector<int> rcs(helpers.size(), RPQ_OK);
   std::vector<rpq_stats> hst(helpers.size());
   std::vector<uint64_t> launches(helpers.size(), 0);
+  auto assign = [&](const std::vector<uint32_t> &tasks, const std::vector<uint64_t> &ls, size_t at) {
+    for (size_t j = 0; j < tasks.size(); j++)
+      for (int c = 0; c < 3; c++) out->qstats[3ull * tasks[j] + c] = ls[3 * (at + j) + c];
+  };
+  auto run_single = [&](size_t h, const std::vector<uint32_t> &tasks) {
+    std::vector<uint32_t> srcs;
+    for (uint32_t i : tasks) srcs.push_back(sources[i]);
+    std::vector<uint64_t> ls;
+    int r = rpq_lane_stats_for_sources(helpers[h], g, queries[tasks[0]], srcs, &ls, &hst[h]);
+    if (r == RPQ_OK) {
+      assign(tasks, ls, 0);
+      launches[h]++;
+    }
+    return r;
+  };
   auto work = [&](size_t h) {
     std::memset(&hst[h], 0, sizeof(rpq_stats));
     cudaSetDevice(ctx_device(ctx));
     for (size_t t; (t = next.fetch_add(1)) < todo.size();) {
-      const std::vector<uint32_t> &members = *todo[t];
-      // one lane per query, in source order (a repeated start vertex gets a
-      // lane of its own, so the work counter stays the sum over queries)
-      std::vector<std::pair<uint32_t, uint32_t>> order;
-      for (uint32_t i : members) order.push_back({sources[i], i});
-      std::sort(order.begin(), order.end());
-      std::vector<uint32_t> srcs;
-      for (auto &o : order) srcs.push_back(o.first);
-      std::vector<uint64_t> ls;
-      int r = rpq_lane_stats_for_sources(helpers[h], g, queries[members[0]], srcs, &ls, &hst[h]);
+      const Item &it = todo[t];
+      int r = RPQ_OK;
+      if (!it.single.empty()) {
+        r = run_single(h, it.single);
+      } else {
+        std::vector<MultiUnit> units(it.units.size());
+        for (size_t u = 0; u < it.units.size(); u++) {
+          units[u].q = queries[it.units[u][0]];
+          for (uint32_t i : it.units[u]) units[u].srcs.push_back(sources[i]);
+        }
+        std::vector<uint64_t> ls;
+        r = rpq_lane_stats_multi(helpers[h], g, units, &ls, &hst[h]);
+        if (r == RPQ_OK) {
+          size_t at = 0;
+          for (const auto &tasks : it.units) {
+            assign(tasks, ls, at);
+            at += tasks.size();
+          }
+          launches[h]++;
+        } else if (r == RPQ_ERR_TOO_COMPLEX) {
+          // the union of these automata does not fit a descriptor: one launch each
+          r = RPQ_OK;
+          for (size_t u = 0; u < it.units.size() && r == RPQ_OK; u++) r = run_single(h, it.units[u]);
+        }
+      }
       if (r) {
         rcs[h] = r;
         next = todo.size();
         return;
       }
-      launches[h]++;
-      for (size_t j = 0; j < order.size(); j++)
-        for (int c = 0; c < 3; c++) out->qstats[3ull * order[j].second + c] = ls[3 * j + c];
     }
   };
   std::vector<std::thread> threads;

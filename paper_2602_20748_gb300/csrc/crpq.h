@@ -45,6 +45,14 @@ int rpq_rows_for_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, s
                          bool reverse, std::vector<RowChunk> *chunks, rpq_stats *stats, uint64_t *dsum = nullptr,
                          uint64_t *dxor = nullptr);
 void free_row_chunk(rpq_ctx *ctx, RowChunk &c);
+// One automaton and at most 64 start vertices: a lane group of a
+// multi-automaton launch.
+struct MultiUnit {
+  const rpq_query *q = nullptr;
+  std::vector<uint32_t> srcs;
+};
+int rpq_lane_stats_multi(rpq_ctx *ctx, const rpq_graph *g, const std::vector<MultiUnit> &units,
+                         std::vector<uint64_t> *lane_stats, rpq_stats *stats);
 int rpq_lane_stats_for_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q,
                                const std::vector<uint32_t> &srcs, std::vector<uint64_t> *lane_stats,
                                rpq_stats *stats);

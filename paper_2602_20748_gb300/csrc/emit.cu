@@ -206,6 +206,7 @@ cudaError_t launch_row_digest(const uint32_t *lanesrc, const unsigned long long 
 template <int NW>
 __global__ void emit_lane_stats_kernel(const EmitParams p, u64 *__restrict__ lane_stats) {
   const u32 g = blockIdx.x % p.G, seg = blockIdx.x / p.G;
+  const u32 final_mask = p.final_g ? p.final_g[g] : p.final_mask;  // per-group automata
   const u32 col = threadIdx.x >> 5, lane = lane_id();
   const u32 K = 64 * NW;
   const u64 glane = (u64)g * K + col * 32 + lane;
@@ -220,7 +221,7 @@ __global__ void emit_lane_stats_kernel(const EmitParams p, u64 *__restrict__ lan
     const u32 w = w0 + lane;
     u32 x = 0;
     if (w < p.n) {
-      for (u32 fm = p.final_mask; fm; fm &= fm - 1) {
+      for (u32 fm = final_mask; fm; fm &= fm - 1) {
         u32 q = __ffs(fm) - 1;
         u64 word = (((u64)q * p.n + w) * p.G + g) * NW;
         x |= __ldcg(vis32 + word * 2 + col);

@@ -129,12 +129,21 @@ __device__ bool grid_barrier(BfsCtl *c, unsigned nblocks, u64 limit_ns) {
   return stop == 0;
 }
 
+// Automaton of group g: its own in multi mode, else the launch's.
+template <bool MULTI>
+__device__ __forceinline__ const QueryDesc &gdesc(const BfsParams &p, u32 g) {
+  if constexpr (MULTI)
+    return p.qg[g];
+  else
+    return p.q;
+}
+
 // Out-degree of v summed over the labels leaving DFA state q.
-__device__ __forceinline__ u32 degsum(const BfsParams &p, u32 q, u32 v) {
+__device__ __forceinline__ u32 degsum(const BfsParams &p, const QueryDesc &qd, u32 q, u32 v) {
   u32 s = 0;
   const u32 n1 = p.n + 1;
-  for (u32 t = p.q.out_begin[q]; t < p.q.out_begin[q + 1]; t++) {
-    u32 l = p.q.out_label[t];
+  for (u32 t = qd.out_begin[q]; t < qd.out_begin[q + 1]; t++) {
+    u32 l = qd.out_label[t];
     if (l >= p.L) continue;
     const u32 *off = p.out_off + (u64)l * n1 + v;
     s += __ldg(off + 1) - __ldg(off);
@@ -205,7 +214,7 @@ __device__ __forceinline__ void append_close(const BfsParams &p, Appender &a, u6
   a.pos = a.end = 0;
 }
 
-template <int NW>
+template <int NW, bool MULTI>
 __device__ void seed_phase(const BfsParams &p, u64 *stat) {
   const u32 K = 64 * NW;
   const u64 total = (u64)p.G * K;
@@ -232,7 +241,7 @@ __device__ void seed_phase(const BfsParams &p, u64 *stat) {
           take = atomicMax(p.claim + ((u64)s * p.G + g), p.stamp_base + 1) < p.stamp_base + 1;
         entry = ((u64)g * p.Q << 32) | s;
         if (take && p.fbits) atomicOr(p.fbits + (s >> 5), 1u << (s & 31));  // state 0, bitmap 0
-        u32 d = degsum(p, 0, s);
+        u32 d = degsum(p, gdesc<MULTI>(p, g), 0, s);
         W += d;
         N += 1;
         if (take) mf += d;
@@ -281,7 +290,7 @@ __device__ __forceinline__ bool relax(const BfsParams &p, u64 *FB, u32 tgq, u32 
 // entries at a time and spreads the edges of their rows evenly over its lanes
 // (prefix sum of row lengths, owner found by binary search); rows longer than
 // SPILL_EDGES are queued in chunks for the spill sub-phase.
-template <int NW>
+template <int NW, bool MULTI>
 __device__ void push_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u64 n_cur, u32 stamp, u64 *stat) {
   const u64 *list = lp ? p.list1 : p.list0;
   u64 *nlist = lp ? p.list0 : p.list1;
@@ -307,15 +316,16 @@ __device__ void push_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u64 n_c
     for (int i = 0; i < NW; i++) fm.w[i] = 0;
     if (valid) fm = load_cg<NW>(F + widx<NW>(p, g, q, v));
     entries += valid;
-    u32 t_beg = valid ? p.q.out_begin[q] : 0;
-    u32 nt = valid ? p.q.out_begin[q + 1] - t_beg : 0;
+    const QueryDesc &qd = gdesc<MULTI>(p, valid ? g : 0);
+    u32 t_beg = valid ? qd.out_begin[q] : 0;
+    u32 nt = valid ? qd.out_begin[q + 1] - t_beg : 0;
     u32 max_nt = __reduce_max_sync(FULL_MASK, nt);
     for (u32 j = 0; j < max_nt; j++) {
       u32 rbeg = 0, rlen = 0, tgq = 0;
       if (j < nt) {
         u32 t = t_beg + j;
-        u32 l = p.q.out_label[t];
-        tgq = g * Q + p.q.out_to[t];
+        u32 l = qd.out_label[t];
+        tgq = g * Q + qd.out_to[t];
         if (l < p.L) {
           const u32 *off = p.out_off + (u64)l * n1 + v;
           rbeg = __ldg(off);
@@ -430,8 +440,9 @@ __device__ void spill_phase(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 st
 // gathered frontier words of its PER words into acc.  With EARLY (one lane
 // group: few enough lanes that a vertex can run out of unvisited ones) a lane
 // stops gathering once acc covers all its lanes not yet visited, and the
-// sub-warp (lanes sg_mask) leaves the row when all its lanes have.  Returns
-// the in-edges examined.
+// sub-warp (lanes sg_mask) leaves the row when all its lanes have (with many
+// groups a vertex practically never runs out, and the test costs more than it
+// saves).  Returns the in-edges examined.
 template <int NW, int PER, bool EARLY>
 __device__ __forceinline__ u32 gather_row(const BfsParams &p, const u64 *F, const u32 *bits, u32 from, u32 beg,
                                           u32 end, u32 lane_off, bool lane_on, u32 sg_mask,
@@ -536,7 +547,7 @@ __device__ __forceinline__ void pull_finish(const BfsParams &p, Appender &app, u
 // chunk taken dynamically over the (target state, transition group) pairs
 // whose source states are active; the sub-warps split the chunk's edges and
 // OR their gathers together.
-template <int NW, bool EARLY>
+template <int NW, bool EARLY, bool MULTI>
 __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 active, u32 stamp, const u32 *bits,
                            u64 *stat) {
   constexpr int PER = (NW >= 2) ? 2 : 1;
@@ -621,8 +632,11 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
           const u32 *off = p.in_off + (u64)l * n1 + w;
           const u32 beg = __ldg(off), end = __ldg(off + 1);
           if (end - beg >= HEAVY_ROW && chunked) continue;
+          // in multi mode each lane gathers through its own group's transitions
+          u32 lfrom = from;
+          if constexpr (MULTI) lfrom = lane_on ? p.from_tab[((u64)my_g * Q + q2) * p.L + l] & active : 0u;
           u32 gat = 0;
-          const u32 ex = gather_row<NW, PER, EARLY>(p, F, bits, from, beg, end, lane_off, lane_on, sg_mask, vis, acc, gat);
+          const u32 ex = gather_row<NW, PER, EARLY>(p, F, bits, lfrom, beg, end, lane_off, lane_on, sg_mask, vis, acc, gat);
           edges += (li == 0) ? ex : 0;
           // column ids, frontier-bit words when tested, gathered frontier words
           bytes += (li == 0) ? 8 + (u64)ex * (4 + (bits ? 4 * __popc(from) : 0)) + (u64)gat * gword : 0;
@@ -641,7 +655,7 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
       it = __shfl_sync(FULL_MASK, it, 0);
       // map the item number to (target state, transition group, chunk)
       u64 acc_base = 0, ci = 0;
-      u32 q2s = 0, from = 0;
+      u32 q2s = 0, from = 0, ls = 0;
       bool found = false;
       for (u32 q2 = 0; q2 < Q && !found; q2++)
         for (u32 j = p.q.in_begin[q2]; j < p.q.in_begin[q2 + 1]; j++) {
@@ -651,6 +665,7 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
           if (it < acc_base + cnt) {
             found = true;
             q2s = q2;
+            ls = l;
             from = p.q.in_from[j] & active;
             ci = p.hchunk_off[l] + (it - acc_base);
             break;
@@ -675,8 +690,10 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
       // the sub-warps take consecutive slices of the chunk's edges
       const u32 len = end - beg, per = (len + VPW - 1) / VPW;
       const u32 sb = beg + min(len, sg * per), se = beg + min(len, (sg + 1) * per);
+      u32 lfrom = from;
+      if constexpr (MULTI) lfrom = lane_on ? p.from_tab[((u64)my_g * Q + q2s) * p.L + ls] & active : 0u;
       u32 gat = 0;
-      const u32 ex = gather_row<NW, PER, EARLY>(p, F, bits, from, sb, se, lane_off, lane_on, sg_mask, vis, acc, gat);
+      const u32 ex = gather_row<NW, PER, EARLY>(p, F, bits, lfrom, sb, se, lane_off, lane_on, sg_mask, vis, acc, gat);
       for (u32 o = SW; o < 32; o <<= 1) {
 #pragma unroll
         for (int k = 0; k < PER; k++) acc[k] |= __shfl_xor_sync(FULL_MASK, acc[k], o);
@@ -699,7 +716,7 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
 // the DFA states present in the new frontier, clear the old frontier words.
 // set_bits: the next frontier may be sparse enough for bottom-up levels to
 // test its bitmap, so its bits are set; clear_bits: this level's bits were set.
-template <int NW>
+template <int NW, bool MULTI>
 __device__ void commit_phase(const BfsParams &p, int lp, u32 nxt, u64 n_cur, bool set_bits, bool clear_bits,
                              u64 *stat) {
   const u64 *list = lp ? p.list1 : p.list0;
@@ -728,7 +745,7 @@ __device__ void commit_phase(const BfsParams &p, int lp, u32 nxt, u64 n_cur, boo
       atomicOr(p.fbits + (lp ? 0 : p.fbits_words) + (bi >> 5), 1u << (bi & 31));
     }
     u32 c = popc_w(m);
-    u32 d = degsum(p, q, w);
+    u32 d = degsum(p, gdesc<MULTI>(p, g), q, w);
     W += (u64)c * d;
     N += c;
     mf += d;
@@ -789,7 +806,7 @@ __device__ double pull_bytes(const BfsParams &p, u32 active) {
   return b;
 }
 
-template <int NW>
+template <int NW, bool MULTI>
 __global__ void __launch_bounds__(BFS_THREADS, 4) msbfs_kernel(const __grid_constant__ BfsParams p) {
   // per-warp statistics, summed into the control block at the end
   u64 stat[ST_COUNT];
@@ -798,7 +815,7 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) msbfs_kernel(const __grid_cons
   BfsCtl *c = p.ctl;
   const bool tracer = blockIdx.x == 0 && threadIdx.x == 0;
 
-  seed_phase<NW>(p, stat);
+  seed_phase<NW, MULTI>(p, stat);
   if (!grid_barrier(c, p.nblocks, p.time_limit_ns)) return;
 
   u32 level = 0;
@@ -833,7 +850,7 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) msbfs_kernel(const __grid_cons
     }
     const u32 stamp = p.stamp_base + level + 2;  // the seeds used stamp_base + 1
     if (push) {
-      push_level<NW>(p, lp, cur, nxt, n_cur, stamp, stat);
+      push_level<NW, MULTI>(p, lp, cur, nxt, n_cur, stamp, stat);
       if (!grid_barrier(c, p.nblocks, p.time_limit_ns)) return;
       if (*(volatile unsigned long long *)&c->spill_count[cur] != 0) {
         spill_phase<NW>(p, lp, cur, nxt, stamp, stat);
@@ -845,9 +862,9 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) msbfs_kernel(const __grid_cons
       const bool sparse = p.fbits && n_cur * 4 < (u64)p.n * __popc(active);
       const u32 *bits = sparse ? p.fbits + (lp ? p.fbits_words : 0) : nullptr;
       if (p.G == 1)
-        pull_level<NW, true>(p, lp, cur, nxt, active, stamp, bits, stat);
+        pull_level<NW, true, MULTI>(p, lp, cur, nxt, active, stamp, bits, stat);
       else
-        pull_level<NW, false>(p, lp, cur, nxt, active, stamp, bits, stat);
+        pull_level<NW, false, MULTI>(p, lp, cur, nxt, active, stamp, bits, stat);
       if (!grid_barrier(c, p.nblocks, p.time_limit_ns)) return;
     }
     {
@@ -857,7 +874,7 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) msbfs_kernel(const __grid_cons
       const u64 sparse_cap = (u64)p.n * p.Q;
       const bool set_bits = p.fbits && n_next * 4 < sparse_cap;
       const bool clear_bits = p.fbits && (level == 0 || n_cur * 4 < sparse_cap);
-      commit_phase<NW>(p, lp, nxt, n_cur, set_bits, clear_bits, stat);
+      commit_phase<NW, MULTI>(p, lp, nxt, n_cur, set_bits, clear_bits, stat);
     }
     if (!grid_barrier(c, p.nblocks, p.time_limit_ns)) return;
   }
@@ -924,8 +941,8 @@ cudaError_t launch_source_filter(const uint32_t *off, uint32_t n, uint32_t L, un
 cudaError_t launch_msbfs(int nw, const BfsParams &p, int blocks, int threads, cudaStream_t st) {
   void *args[] = {(void *)&p};
   if (nw == 1)
-    return cudaLaunchCooperativeKernel((void *)msbfs_kernel<1>, blocks, threads, args, 0, st);
-  return cudaLaunchCooperativeKernel((void *)msbfs_kernel<4>, blocks, threads, args, 0, st);
+    return cudaLaunchCooperativeKernel((void *)msbfs_kernel<1, false>, blocks, threads, args, 0, st);
+  return cudaLaunchCooperativeKernel((void *)msbfs_kernel<4, false>, blocks, threads, args, 0, st);
 }
 
 int msbfs_max_blocks(int nw, int threads, int *blocks_per_sm, int *sms) {
@@ -934,10 +951,22 @@ int msbfs_max_blocks(int nw, int threads, int *blocks_per_sm, int *sms) {
   cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
   cudaError_t e;
   if (nw == 1)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, msbfs_kernel<1>, threads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, msbfs_kernel<1, false>, threads, 0);
   else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, msbfs_kernel<4>, threads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, msbfs_kernel<4, false>, threads, 0);
   return e == cudaSuccess ? 0 : -1;
+}
+
+cudaError_t launch_msbfs_multi(const BfsParams &p, int blocks, int threads, cudaStream_t st) {
+  void *args[] = {(void *)&p};
+  return cudaLaunchCooperativeKernel((void *)msbfs_kernel<1, true>, blocks, threads, args, 0, st);
+}
+
+int msbfs_multi_max_blocks(int threads, int *blocks_per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, msbfs_kernel<1, true>, threads, 0) ==
+                 cudaSuccess
+             ? 0
+             : -1;
 }
 
 }  // namespace rpq

@@ -157,6 +157,13 @@ struct BfsParams {
   // add per warp-aggregated append); unused reserved slots hold NO_ENTRY.
   unsigned int append_seg;
   unsigned long long list_cap;  // entries per list (overflow sets ERR_LIST_OVERFLOW)
+  // Per-group automata (multi mode; nullptr otherwise): group g runs qg[g].
+  // q is then the union of the groups' automata over states 0 .. Q-1: it
+  // drives the bottom-up iteration and the cost estimates, while qg[g] drives
+  // group g's top-down steps and work counters and from_tab[(g * Q + q2) * L
+  // + l] is the set of group g's states that reach q2 on label l.
+  const QueryDesc *qg;
+  const unsigned int *from_tab;
   BfsCtl *ctl;
   unsigned int stamp_base;     // claim stamps continue across launches
   unsigned int nblocks;
@@ -169,6 +176,9 @@ struct BfsParams {
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_vis_init(int nw, const BfsParams &p, const unsigned long long *empty, cudaStream_t st);
 cudaError_t launch_msbfs(int nw, const BfsParams &p, int blocks, int threads, cudaStream_t st);
+// Per-group automata (p.qg set): one lane word per group (NW = 1).
+cudaError_t launch_msbfs_multi(const BfsParams &p, int blocks, int threads, cudaStream_t st);
+int msbfs_multi_max_blocks(int threads, int *blocks_per_sm);
 // flag[i] = whether srcs[i] has an edge (offsets `off`, per label) on a label of label_mask.
 cudaError_t launch_source_filter(const uint32_t *off, uint32_t n, uint32_t L, unsigned long long label_mask,
                                  const uint32_t *srcs, unsigned long long count, unsigned char *flag,
@@ -187,6 +197,7 @@ struct EmitParams {
   const unsigned long long *off; // exclusive offsets of cnt (write pass)
   uint32_t *dst;                 // output destinations (write pass)
   unsigned long long *digest;    // [2]: sum, xor
+  const uint32_t *final_g;       // per-group accepting masks (multi mode), else nullptr
 };
 constexpr int EMIT_TILES = 128;  // 32-vertex tiles per segment
 constexpr int EMIT_SEG = 32 * EMIT_TILES;

@@ -178,7 +178,7 @@ extern "C" int run_rpq_static(rpq_ctx *ctx, const rpq_graph *g, const rpq_query 
   STATIC_CK(launch_vis_init(1, p, empty, st));
   STATIC_CK(launch_msbfs(1, p, blocks, 256, st));
 
-  EmitParams ep;
+  EmitParams ep{};
   ep.vis = vis;
   ep.n = n;
   ep.G = 1;
