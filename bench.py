@@ -63,6 +63,8 @@ def parse_args():
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: mean arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serve: arrival window (s)")
     ap.add_argument("--drain", type=float, default=10.0, help="serve: time after the window before cancelling (s)")
+    ap.add_argument("--batch-multi", type=int, default=1, choices=[0, 1],
+                    help="batch / serve: evicted small automaton groups share multi-automaton launches")
     return ap.parse_args()
 
 
@@ -390,6 +392,7 @@ def bench_batch(args):
     src, dst, lab = synth.rmat_graph(22, 1 << 26, 8, 1.2, seed=synth.BASE_SEED + 4)
     regexes, sources = synth.batch_queries(4096, 8, 1.2, src, n, seed=synth.BASE_SEED + 4)
     ctx = rpq.Context(device=0)
+    rpq.rpq_set_option(ctx, "batch_multi", args.batch_multi)
     g = rpq.load_graph(ctx, n, 8, src, dst, lab)
     qs = [rpq.compile_rpq(ctx, r) for r in regexes]
     t0 = time.perf_counter()
@@ -440,7 +443,8 @@ def bench_batch(args):
         "config": {"workload": "rmat22-batched-single-source", "queries": 4096, "vertices": n,
                    "generated_edges": 1 << 26, "labels": 8, "zipf_s": 1.2, "mode": "per-query count + digest",
                    "autotuned_threads": threads, "autotuned_queries_per_launch": per_launch,
-                   "autotuned_evict_at": evict_at, "autotune_s": round(tune_s, 3)},
+                   "autotuned_evict_at": evict_at, "autotune_s": round(tune_s, 3),
+                   "multi_automaton_launches": bool(args.batch_multi)},
         "evicted_per_step": evicted // max(1, args.steps),
         "batched_latency_ms": ms, "product_edges_per_s": W / (ms * args.steps / 1000.0),
         "rows_per_step": rows // args.steps,
@@ -515,6 +519,7 @@ def _class_summary(kinds, lat, status, wall_s):
         done = [lat[i] for i in idx if status[i] == 0]
         out[name] = {"offered": len(idx), "completed": len(done),
                      "not_completed": len(idx) - len(done),
+                     "errors": sum(1 for i in idx if status[i] not in (0, 1, -9)),
                      "p50_ms": _pct(done, len(idx), 50), "p99_ms": _pct(done, len(idx), 99),
                      "completed_per_s": len(done) / wall_s}
     return out
@@ -544,6 +549,7 @@ def bench_serve(args):
                                             seed=synth.BASE_SEED + 5)
     gen_s = time.perf_counter() - t_gen
     ctx = rpq.Context(device=0)
+    rpq.rpq_set_option(ctx, "batch_multi", args.batch_multi)
     g = rpq.load_graph(ctx, n, L, src, dst, lab)
     del src, dst, lab
     cache = {}
@@ -673,7 +679,8 @@ def bench_serve(args):
         "config": {"workload": f"rmat{scale}-served-mix", "vertices": n, "generated_edges": 16 * n, "labels": L,
                    "zipf_s": 1.2, "rate_per_s": args.rate, "arrival_window_s": args.serve_seconds,
                    "drain_s": args.drain, "mix": {"single": 0.80, "allpairs": 0.15, "crpq": 0.05},
-                   "bulk_labels": "Zipf tail, ranks 9-16", "generation_s": round(gen_s, 1)},
+                   "bulk_labels": "Zipf tail, ranks 9-16", "generation_s": round(gen_s, 1),
+                   "multi_automaton_launches": bool(args.batch_multi)},
         "offered": m, "served": served, "fifo": fifo,
         "fifo_requests_per_s": f_done / horizon,
         "single_p99_fifo_over_served": ratio(fifo["single"]["p99_ms"], served["single"]["p99_ms"]),

@@ -117,7 +117,10 @@ int rpq_set_stream(rpq_ctx *ctx, void *cuda_stream);
  *   "max_groups"   lane groups (256 start vertices each) per launch, 1 .. 16
  *   "time_limit_s" bound on each device-side wait (default 20 s)
  *   "batch_evict"  run_rpq_batch with RPQ_PER_QUERY: product vertices after
- *                  which a query leaves the shared launch (0: never) */
+ *                  which a query leaves the shared launch (0: never)
+ *   "batch_multi"  1 (default): evicted queries of small automaton groups
+ *                  share multi-automaton launches; 0: one launch per automaton
+ * A server's workers take the tunables of the context it was created on. */
 int rpq_set_option(rpq_ctx *ctx, const char *name, double value);
 /* Reads a tunable set by rpq_set_option or chosen by rpq_autotune_batch
  * (same names, plus "batch_threads" and "batch_queries_per_launch"). */
@@ -212,8 +215,8 @@ int run_rpq_batch(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_queries, const rp
                   const uint32_t *sources, uint32_t flags, rpq_result **out);
 
 /* Times run_rpq_batch (RPQ_PER_QUERY) on a sample of the given batch (its
- * first 512 queries) for each candidate block size (256, 512 threads) and
- * eviction threshold (2^14, 2^16, 2^18, 2^20, 2^22 product vertices, never), keeps the
+ * first 1,024 queries) for each candidate block size (256, 512 threads) and
+ * eviction threshold (2^12, 2^14, 2^16, 2^18 product vertices), keeps the
  * fastest on the context for later run_rpq_batch calls and reports it (out
  * pointers may be NULL; queries per launch is reported as set).
  * Errors: as run_rpq_batch. */

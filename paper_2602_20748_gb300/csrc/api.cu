@@ -730,6 +730,8 @@ int rpq_set_option(rpq_ctx *ctx, const char *name, double value) {
     ctx->time_limit_ns = (uint64_t)(value * 1e9);
   } else if (n == "batch_evict" && value >= 0) {
     ctx->batch.evict_at = (uint64_t)value;
+  } else if (n == "batch_multi" && (value == 0 || value == 1)) {
+    ctx->batch.multi = value != 0;
   } else {
     return set_err(ctx, RPQ_ERR_INVALID_ARG, "unknown option or value out of range: " + n);
   }
@@ -753,6 +755,8 @@ int rpq_get_option(const rpq_ctx *ctx, const char *name, double *value) {
     *value = ctx->batch.threads;
   else if (n == "batch_queries_per_launch")
     *value = ctx->batch.queries_per_launch;
+  else if (n == "batch_multi")
+    *value = ctx->batch.multi ? 1 : 0;
   else
     return RPQ_ERR_INVALID_ARG;
   return RPQ_OK;
@@ -1005,11 +1009,13 @@ int rpq_autotune_batch(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_queries, con
   if (!usable(ctx)) return RPQ_ERR_NO_DEVICE;
   for (uint32_t i = 0; i < n_queries; i++)
     if (!queries[i] || sources[i] >= g->g.n) return set_err(ctx, RPQ_ERR_INVALID_ARG, "bad query or source");
-  const uint32_t sample = std::min<uint32_t>(n_queries, 512);
+  const uint32_t sample = std::min<uint32_t>(n_queries, 1024);
   BatchTuning best = ctx->batch;
   double best_s = -1;
   const int threads[] = {256, 512};
-  const uint64_t evicts[] = {1ull << 14, 1ull << 16, 1ull << 18, 1ull << 20, 1ull << 22, 0};
+  // (never evicting is not a candidate: a sample that keeps its heavy queries
+  // in the shared launch says little about a full batch that would not)
+  const uint64_t evicts[] = {1ull << 12, 1ull << 14, 1ull << 16, 1ull << 18};
   for (int t : threads)
     for (uint64_t ev : evicts) {
       BatchTuning cand = ctx->batch;
@@ -1124,13 +1130,20 @@ int ctx_device(rpq_ctx *ctx) { return ctx->device; }
 int ctx_sm_share(rpq_ctx *ctx) { return std::max(1, (int)(ctx->sms * ctx->grid_share)); }
 int ctx_bfs_blocks(rpq_ctx *ctx, int nw) { return ctx_sm_share(ctx) * ctx->bpsm[nw == 1 ? 0 : 1]; }
 bool ctx_trace(rpq_ctx *ctx) { return ctx->trace; }
+BatchTuning ctx_batch_tuning(rpq_ctx *ctx) { return ctx->batch; }
+void ctx_copy_tunables(rpq_ctx *to, const rpq_ctx *from) {
+  to->alpha = from->alpha;
+  to->time_limit_ns = from->time_limit_ns;
+  to->spill_cap = from->spill_cap;
+  to->batch = from->batch;
+}
 int ctx_helpers(rpq_ctx *ctx, int k, std::vector<rpq_ctx *> *out) {
   while ((int)ctx->helpers.size() < k) {
     cudaStream_t hs = nullptr;
     if (cudaStreamCreateWithFlags(&hs, cudaStreamNonBlocking) != cudaSuccess)
       return set_err(ctx, RPQ_ERR_CUDA, "helper stream creation failed");
     rpq_ctx *h = nullptr;
-    int rc = rpq_create(&h, ctx->device, ctx->budget / 8, hs);
+    int rc = rpq_create(&h, ctx->device, ctx->budget / (k + 1), hs);
     if (rc) {
       cudaStreamDestroy(hs);
       return set_err(ctx, rc, "helper context creation failed");
@@ -1141,7 +1154,12 @@ int ctx_helpers(rpq_ctx *ctx, int k, std::vector<rpq_ctx *> *out) {
     ctx->helpers.push_back(h);
     ctx->helper_streams.push_back(hs);
   }
-  for (int i = 0; i < k; i++) ctx->helpers[i]->grid_share = ctx->grid_share / k;
+  for (int i = 0; i < k; i++) {  // follow the parent's current tunables
+    ctx->helpers[i]->grid_share = ctx->grid_share / k;
+    ctx->helpers[i]->alpha = ctx->alpha;
+    ctx->helpers[i]->time_limit_ns = ctx->time_limit_ns;
+    ctx->helpers[i]->spill_cap = ctx->spill_cap;
+  }
   out->assign(ctx->helpers.begin(), ctx->helpers.begin() + k);
   return RPQ_OK;
 }
@@ -1303,6 +1321,24 @@ int rpq_lane_stats_multi(rpq_ctx *ctx, const rpq_graph *gr, const std::vector<Mu
   if (blocks <= 0) return set_err(ctx, RPQ_ERR_CUDA, "traversal kernel cannot be made resident");
   const uint64_t slack = 2ull * blocks * (BFS_THREADS_HOST / 32) * APPEND_SEG;
   const uint64_t words = (uint64_t)G * Q * n;
+  {
+    // traversal state grows with units x states x vertices: halve the launch
+    // while it does not fit the budget
+    const uint64_t need = workspace_bytes(words, words + slack, 0, G * 64);
+    const uint64_t have = ctx->budget - ctx->used +
+                          workspace_bytes(ctx->ws.vis_words, ctx->ws.list_cap, ctx->ws.claim_cap, ctx->ws.lane_cap);
+    if (need + (64ull << 20) > have && G > 1) {
+      const size_t h = G / 2;
+      std::vector<MultiUnit> a(units.begin(), units.begin() + h), b(units.begin() + h, units.end());
+      std::vector<uint64_t> la, lb;
+      int r = rpq_lane_stats_multi(ctx, gr, a, &la, stats);
+      if (r == RPQ_OK) r = rpq_lane_stats_multi(ctx, gr, b, &lb, stats);
+      if (r) return r;
+      std::copy(la.begin(), la.end(), lane_stats->begin());
+      std::copy(lb.begin(), lb.end(), lane_stats->begin() + la.size());
+      return RPQ_OK;
+    }
+  }
   int rc = ensure_workspace(ctx, words, words + slack, 0, G * 64);
   if (rc) return rc;
   Workspace &w = ctx->ws;

@@ -528,7 +528,7 @@ struct DBuf {
 
 }  // namespace
 
-BatchTuning batch_default_tuning() { return BatchTuning{BATCH_THREADS, 4096, 1ull << 28, SPILL_CAP, 1ull << 16}; }
+BatchTuning batch_default_tuning() { return BatchTuning{BATCH_THREADS, 4096, 1ull << 28, SPILL_CAP, 1ull << 16, true}; }
 
 // One launch over queries [0, nq) of the arrays; appends rows to `out`.
 static int batch_launch(rpq_ctx *ctx, const rpq_graph *g, uint32_t qbase, uint32_t nq,
@@ -777,7 +777,7 @@ int batch_run(rpq_ctx *ctx, const rpq_graph *g, uint32_t nq, const rpq_query *co
     std::vector<uint32_t> members = kv.second;
     std::sort(members.begin(), members.end(),
               [&](uint32_t a, uint32_t b) { return sources[a] < sources[b] || (sources[a] == sources[b] && a < b); });
-    if (members.size() > 64) {
+    if (members.size() > 64 || !tun.multi) {
       Item it;
       it.single = members;
       todo.push_back(std::move(it));

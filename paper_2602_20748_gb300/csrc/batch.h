@@ -19,6 +19,7 @@ struct BatchTuning {
   uint64_t spill_cap;           // long-row chunks per level (<= SPILL_CAP)
   uint64_t evict_at;            // per-query mode: a query with more product vertices leaves the
                                 // batch and is evaluated with the multi-source engine (0: never)
+  bool multi;                   // evicted small automaton groups share multi-automaton launches
 };
 
 struct BatchOut {
@@ -33,6 +34,7 @@ struct BatchOut {
 };
 
 BatchTuning batch_default_tuning();
+BatchTuning ctx_batch_tuning(rpq_ctx *ctx);  // the context's current tuning
 
 // Evaluates queries[i] from sources[i] for i < nq; rows (i, y) sorted.
 int batch_run(rpq_ctx *ctx, const rpq_graph *g, uint32_t nq, const rpq_query *const *queries,

@@ -29,8 +29,10 @@ int ctx_bfs_blocks(rpq_ctx *ctx, int nw);
 int ctx_sm_share(rpq_ctx *ctx);  // SMs the context's persistent grids may use
 float ctx_alpha(rpq_ctx *ctx);
 bool ctx_trace(rpq_ctx *ctx);              // per-level trace printing (RPQ_TRACE=1)
-// k helper contexts (created once, kept by ctx): own streams, an eighth of
-// ctx's budget each and ctx->grid_share / k of the SMs, for evaluations that
+// alpha, time limit, spill capacity and batched-engine tuning of `from`
+void ctx_copy_tunables(rpq_ctx *to, const rpq_ctx *from);
+// k helper contexts (created once, kept by ctx): own streams, ctx's budget
+// / (k + 1) each and ctx->grid_share / k of the SMs, for evaluations that
 // run side by side from k host threads.
 int ctx_helpers(rpq_ctx *ctx, int k, std::vector<rpq_ctx *> *out);
 // `count` pinned host buffers of `bytes` each, owned by the context and kept

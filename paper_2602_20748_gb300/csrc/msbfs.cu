@@ -455,7 +455,9 @@ __device__ __forceinline__ u32 gather_row(const BfsParams &p, const u64 *F, cons
     for (int k = 0; k < PER; k++) d &= (acc[k] | vis[k]) == ~0ull;
     return d;
   };
-  bool fin = !lane_on || (EARLY && done());
+  // a lane with no source state on this row (another group's label in a
+  // multi launch) has nothing to gather here
+  bool fin = !lane_on || from == 0 || (EARLY && done());
   if (EARLY && (__ballot_sync(sg_mask, !fin) & sg_mask) == 0) return 0;
   u32 i = beg;
   // four in-edges per step keep four gathers in flight
@@ -861,7 +863,9 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) msbfs_kernel(const __grid_cons
       // (implies n_cur * 4 < n * Q, so the commit that built this frontier set its bits)
       const bool sparse = p.fbits && n_cur * 4 < (u64)p.n * __popc(active);
       const u32 *bits = sparse ? p.fbits + (lp ? p.fbits_words : 0) : nullptr;
-      if (p.G == 1)
+      // early exit pays where few lanes are live: one lane group, or the
+      // per-group automata of a multi launch (typically one start vertex each)
+      if (p.G == 1 || MULTI)
         pull_level<NW, true, MULTI>(p, lp, cur, nxt, active, stamp, bits, stat);
       else
         pull_level<NW, false, MULTI>(p, lp, cur, nxt, active, stamp, bits, stat);

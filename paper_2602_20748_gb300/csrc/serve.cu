@@ -105,7 +105,7 @@ void single_worker(rpq_server *s) {
     }
     rpq::BatchOut bo;
     bo.per_query = true;
-    rpq::BatchTuning tun = rpq::batch_default_tuning();
+    rpq::BatchTuning tun = rpq::ctx_batch_tuning(s->ctx_single);
     tun.queries_per_launch = (uint32_t)take.size();
     int rc = rpq::batch_run(s->ctx_single, s->g, (uint32_t)take.size(), qs.data(), srcs.data(), false, tun, &bo);
     const auto t1 = Clock::now();
@@ -207,7 +207,10 @@ int rpq_server_create(rpq_ctx *ctx, const rpq_graph *g, uint64_t mem_budget_byte
     delete s;
     return rpq::ctx_error(ctx, rc, "worker context creation failed");
   }
-  // the two workers share the device: half of the SMs each for persistent grids
+  // the workers follow the owner's tunables and share the device: half of
+  // the SMs each for persistent grids
+  rpq::ctx_copy_tunables(s->ctx_single, ctx);
+  rpq::ctx_copy_tunables(s->ctx_bulk, ctx);
   rpq_set_option(s->ctx_single, "grid_share", 0.5);
   rpq_set_option(s->ctx_bulk, "grid_share", 0.5);
   // visited bitmaps get a third of the single worker's share; the rest holds
