@@ -63,7 +63,7 @@ def parse_args():
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: mean arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serve: arrival window (s)")
     ap.add_argument("--drain", type=float, default=10.0, help="serve: time after the window before cancelling (s)")
-    ap.add_argument("--batch-multi", type=int, default=1, choices=[0, 1],
+    ap.add_argument("--batch-multi", type=int, default=0, choices=[0, 1],
                     help="batch / serve: evicted small automaton groups share multi-automaton launches")
     return ap.parse_args()
 
@@ -521,6 +521,7 @@ def _class_summary(kinds, lat, status, wall_s):
                      "not_completed": len(idx) - len(done),
                      "errors": sum(1 for i in idx if status[i] not in (0, 1, -9)),
                      "p50_ms": _pct(done, len(idx), 50), "p99_ms": _pct(done, len(idx), 99),
+                     "completed_p50_ms": _pct(done, len(done), 50), "completed_p99_ms": _pct(done, len(done), 99),
                      "completed_per_s": len(done) / wall_s}
     return out
 

@@ -528,7 +528,7 @@ struct DBuf {
 
 }  // namespace
 
-BatchTuning batch_default_tuning() { return BatchTuning{BATCH_THREADS, 4096, 1ull << 28, SPILL_CAP, 1ull << 16, true}; }
+BatchTuning batch_default_tuning() { return BatchTuning{BATCH_THREADS, 4096, 1ull << 28, SPILL_CAP, 1ull << 16, false}; }
 
 // One launch over queries [0, nq) of the arrays; appends rows to `out`.
 static int batch_launch(rpq_ctx *ctx, const rpq_graph *g, uint32_t qbase, uint32_t nq,

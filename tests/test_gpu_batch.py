@@ -98,17 +98,19 @@ def test_batch_autotune_and_edge_cases(ctx, er):
     assert e.value.code == rpq.RPQ_ERR_INVALID_ARG
 
 
-@pytest.mark.parametrize("evict,alpha", [(0, 16), (40, 16), (65536, 16), (40, 1e9), (40, 1e-9)])
-def test_batch_per_query_matches_standalone(evict, alpha):
+@pytest.mark.parametrize("evict,alpha,multi", [(0, 16, 0), (40, 16, 0), (65536, 16, 0), (40, 16, 1), (40, 1e9, 1),
+                                               (40, 1e-9, 1)])
+def test_batch_per_query_matches_standalone(evict, alpha, multi):
     """RPQ_PER_QUERY: every query's row count and digest equal run_rpq's for
     that query alone, whether it stays in the shared launch or is evicted and
     evaluated by the multi-source engine (threshold 40 evicts most queries,
-    0 none; small automaton groups share multi-automaton launches); alpha
-    1e9 / 1e-9 makes every level bottom-up / top-down.  The work counter
-    stays exact."""
+    0 none; with multi = 1 small automaton groups share multi-automaton
+    launches); alpha 1e9 / 1e-9 makes every level bottom-up / top-down.  The
+    work counter stays exact."""
     c = rpq.Context(device=0)
     rpq.rpq_set_option(c, "batch_evict", evict)
     rpq.rpq_set_option(c, "alpha", alpha)
+    rpq.rpq_set_option(c, "batch_multi", multi)
     n = 20000
     src, dst, lab = synth.rmat_graph(15, 8 * n, 4, 1.2, seed=57)
     src %= n
