@@ -399,6 +399,7 @@ def bench_batch(args):
     threads, per_launch = rpq.rpq_autotune_batch(ctx, g, qs, sources)
     tune_s = time.perf_counter() - t0
     evict_at = rpq.rpq_get_option(ctx, "batch_evict")
+    streams = rpq.rpq_get_option(ctx, "batch_streams")
     for _ in range(args.warmup):
         rpq.run_rpq_batch(ctx, g, qs, sources, flags=rpq.RPQ_PER_QUERY).free()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -443,7 +444,7 @@ def bench_batch(args):
         "config": {"workload": "rmat22-batched-single-source", "queries": 4096, "vertices": n,
                    "generated_edges": 1 << 26, "labels": 8, "zipf_s": 1.2, "mode": "per-query count + digest",
                    "autotuned_threads": threads, "autotuned_queries_per_launch": per_launch,
-                   "autotuned_evict_at": evict_at, "autotune_s": round(tune_s, 3),
+                   "autotuned_evict_at": evict_at, "autotuned_streams": streams, "autotune_s": round(tune_s, 3),
                    "multi_automaton_launches": bool(args.batch_multi)},
         "evicted_per_step": evicted // max(1, args.steps),
         "batched_latency_ms": ms, "product_edges_per_s": W / (ms * args.steps / 1000.0),

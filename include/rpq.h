@@ -118,6 +118,8 @@ int rpq_set_stream(rpq_ctx *ctx, void *cuda_stream);
  *   "time_limit_s" bound on each device-side wait (default 20 s)
  *   "batch_evict"  run_rpq_batch with RPQ_PER_QUERY: product vertices after
  *                  which a query leaves the shared launch (0: never)
+ *   "batch_streams" helper contexts evaluating evicted queries side by
+ *                  side, 1 .. 16 (default 4)
  *   "batch_multi"  1: evicted queries of small automaton groups share
  *                  multi-automaton launches; 0 (default): one launch per
  *                  automaton (the same throughput on 4,096 mixed queries,
@@ -217,8 +219,9 @@ int run_rpq_batch(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_queries, const rp
                   const uint32_t *sources, uint32_t flags, rpq_result **out);
 
 /* Times run_rpq_batch (RPQ_PER_QUERY) on a sample of the given batch (its
- * first 1,024 queries) for each candidate block size (256, 512 threads) and
- * eviction threshold (2^12, 2^14, 2^16, 2^18 product vertices), keeps the
+ * first 1,024 queries) for each candidate block size (256, 512 threads),
+ * eviction threshold (2^12, 2^14, 2^16, 2^18 product vertices) and number of
+ * side-by-side evaluations of evicted queries (4, 8), keeps the
  * fastest on the context for later run_rpq_batch calls and reports it (out
  * pointers may be NULL; queries per launch is reported as set).
  * Errors: as run_rpq_batch. */

@@ -732,6 +732,8 @@ int rpq_set_option(rpq_ctx *ctx, const char *name, double value) {
     ctx->batch.evict_at = (uint64_t)value;
   } else if (n == "batch_multi" && (value == 0 || value == 1)) {
     ctx->batch.multi = value != 0;
+  } else if (n == "batch_streams" && value >= 1 && value <= 16) {
+    ctx->batch.streams = (uint32_t)value;
   } else {
     return set_err(ctx, RPQ_ERR_INVALID_ARG, "unknown option or value out of range: " + n);
   }
@@ -757,6 +759,8 @@ int rpq_get_option(const rpq_ctx *ctx, const char *name, double *value) {
     *value = ctx->batch.queries_per_launch;
   else if (n == "batch_multi")
     *value = ctx->batch.multi ? 1 : 0;
+  else if (n == "batch_streams")
+    *value = ctx->batch.streams;
   else
     return RPQ_ERR_INVALID_ARG;
   return RPQ_OK;
@@ -1016,24 +1020,27 @@ int rpq_autotune_batch(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_queries, con
   // (never evicting is not a candidate: a sample that keeps its heavy queries
   // in the shared launch says little about a full batch that would not)
   const uint64_t evicts[] = {1ull << 12, 1ull << 14, 1ull << 16, 1ull << 18};
+  const uint32_t streams[] = {4, 8};
   for (int t : threads)
-    for (uint64_t ev : evicts) {
-      BatchTuning cand = ctx->batch;
-      cand.threads = t;
-      cand.evict_at = ev;
-      BatchOut bo;
-      bo.per_query = true;
-      cudaStreamSynchronize(ctx->stream);
-      auto t0 = std::chrono::steady_clock::now();
-      int rc = sample ? batch_run(ctx, g, sample, queries, sources, false, cand, &bo) : RPQ_OK;
-      cudaStreamSynchronize(ctx->stream);
-      double s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-      if (rc) return rc;
-      if (best_s < 0 || s < best_s) {
-        best_s = s;
-        best = cand;
+    for (uint64_t ev : evicts)
+      for (uint32_t ns : streams) {
+        BatchTuning cand = ctx->batch;
+        cand.threads = t;
+        cand.evict_at = ev;
+        cand.streams = ns;
+        BatchOut bo;
+        bo.per_query = true;
+        cudaStreamSynchronize(ctx->stream);
+        auto t0 = std::chrono::steady_clock::now();
+        int rc = sample ? batch_run(ctx, g, sample, queries, sources, false, cand, &bo) : RPQ_OK;
+        cudaStreamSynchronize(ctx->stream);
+        double s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (rc) return rc;
+        if (best_s < 0 || s < best_s) {
+          best_s = s;
+          best = cand;
+        }
       }
-    }
   ctx->batch = best;
   if (threads_out) *threads_out = (uint32_t)best.threads;
   if (queries_per_launch_out) *queries_per_launch_out = best.queries_per_launch;

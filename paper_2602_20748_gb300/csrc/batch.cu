@@ -36,8 +36,8 @@ constexpr unsigned ERR_LIST_FULL = 100;  // frontier list capacity exceeded
 // Bounds checks: an index outside its array records which check failed (the
 // access is skipped) and stops the search with RPQ_ERR_CUDA on the host.
 constexpr unsigned ERR_BOUNDS = 200;
-// evicted queries' automaton groups evaluated side by side
-constexpr size_t REGROUP_STREAMS = 4;
+// at most this many helper contexts evaluate evicted queries side by side
+constexpr uint32_t MAX_REGROUP_STREAMS = 16;
 
 struct BatchParams {
   const uint32_t *out_off;
@@ -528,7 +528,9 @@ struct DBuf {
 
 }  // namespace
 
-BatchTuning batch_default_tuning() { return BatchTuning{BATCH_THREADS, 4096, 1ull << 28, SPILL_CAP, 1ull << 16, false}; }
+BatchTuning batch_default_tuning() {
+  return BatchTuning{BATCH_THREADS, 4096, 1ull << 28, SPILL_CAP, 1ull << 16, false, 4};
+}
 
 // One launch over queries [0, nq) of the arrays; appends rows to `out`.
 static int batch_launch(rpq_ctx *ctx, const rpq_graph *g, uint32_t qbase, uint32_t nq,
@@ -790,7 +792,7 @@ int batch_run(rpq_ctx *ctx, const rpq_graph *g, uint32_t nq, const rpq_query *co
     }
   }
   if (!pending.units.empty()) todo.push_back(std::move(pending));
-  const int k = (int)std::min<size_t>(REGROUP_STREAMS, todo.size());
+  const int k = (int)std::min<size_t>(std::max(1u, std::min(tun.streams, MAX_REGROUP_STREAMS)), todo.size());
   std::vector<rpq_ctx *> helpers;
   int rc = k > 1 ? ctx_helpers(ctx, k, &helpers) : RPQ_OK;
   if (rc) return rc;

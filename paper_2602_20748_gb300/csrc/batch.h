@@ -20,6 +20,7 @@ struct BatchTuning {
   uint64_t evict_at;            // per-query mode: a query with more product vertices leaves the
                                 // batch and is evaluated with the multi-source engine (0: never)
   bool multi;                   // evicted small automaton groups share multi-automaton launches
+  uint32_t streams;             // helper contexts evaluating evicted queries side by side
 };
 
 struct BatchOut {
