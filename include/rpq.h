@@ -396,8 +396,13 @@ int result_query_stats(const rpq_result *r, uint32_t i, uint64_t *count, uint64_
  * RPQ_REVERSE.  The context serves only this stream until rpq_stream_close
  * (the library runs it from two threads of its own); the graph and query must
  * outlive the stream.  Device memory held by rows not yet copied is bounded by
- * three batches; host memory is three pinned slots of 256 MiB, allocated by
- * the first stream on the context and kept by the context for later ones. */
+ * four batches; host memory is three pinned slots of 256 MiB, allocated by
+ * the first stream on the context and kept by the context for later ones.
+ * rpq_stream_open_multi streams several queries over the same range, one
+ * after the other (all rows of queries[0], then of queries[1], ...), so that
+ * the copies of one query's last batches overlap the next query's first
+ * traversals; each block names its query.  The query array is read at open
+ * time; the queries themselves must outlive the stream. */
 typedef struct rpq_stream rpq_stream;
 
 typedef struct {
@@ -407,10 +412,15 @@ typedef struct {
                                 dst[offsets[i] .. offsets[i + 1])             */
   const uint32_t *dst;       /* destinations, ascending per source            */
   uint64_t n_rows;           /* rows in this block; 0 marks the end           */
+  uint32_t query;            /* index of the block's query (0 for
+                                rpq_stream_open)                              */
 } rpq_row_block;
 
 int rpq_stream_open(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, uint32_t src_begin, uint32_t src_end,
                     uint32_t flags, rpq_stream **out);
+/* n_queries >= 1 queries, none null; INVALID_ARG otherwise. */
+int rpq_stream_open_multi(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *const *queries, uint32_t n_queries,
+                          uint32_t src_begin, uint32_t src_end, uint32_t flags, rpq_stream **out);
 /* Fills *block with the next block of rows.  Its arrays belong to the stream
  * and stay valid until the next rpq_stream_next or rpq_stream_close on it.
  * n_rows = 0 at the end; a failure of the evaluation is returned here (after

@@ -4,140 +4,282 @@
 // set of v with some accepting state q such that s's lane is set in the
 // visited word of (group g, state q, vertex v).  For lane group g, OR the
 // accepting states' words into a K-bit result word per vertex.  A block owns
-// a segment of EMIT_SEG vertices of one group; warp c handles lane column c
-// (32 lanes) and walks the segment in 32-vertex tiles, thread i holding the
-// 32 lane bits of vertex w0 + i.  For every lane j with a bit in the tile, a
-// ballot over bit j gives the tile's members of lane j's row in vertex order:
-// the count pass adds its popcount to lane j's (lane, segment) count, and the
-// write pass stores the members at consecutive positions of lane j's row (one
-// coalesced store per lane and tile).  An exclusive scan over the counts laid
-// out [lane][segment] gives every row its output position directly (lanes
-// are in source order, segments in vertex order).  The row digest is folded
-// by the thread that holds the member.
+// a segment of EMIT_SEG vertices of one group and walks it in batches of
+// EMIT_BATCH 32-vertex tiles.  The block loads a batch cooperatively, whole
+// 32-byte sectors at a time (a vertex's K lane bits of the group are one
+// contiguous run), into shared memory laid out by lane column; warp c then
+// reads lane column c (32 lanes) of each tile, thread i holding the 32 lane
+// bits of vertex w0 + i.
+//
+// Count pass: each thread adds its words into bit-sliced counters (plane k
+// holds bit k of each lane's count over the thread's vertices); at the end
+// each plane is transposed across the warp once and the (lane, segment)
+// counts come out as popcounts.  An exclusive scan over the counts laid out
+// [lane][segment] gives every row its output position directly (lanes are in
+// source order, segments in vertex order).
+//
+// Write pass: a 32 x 32 bit transpose across the warp turns each tile around
+// so that thread j holds lane j's members among the tile's 32 vertices; the
+// thread appends them to a private ring in shared memory indexed by output
+// position.  Whenever a row's current 128-byte-aligned chunk of the output is
+// complete, the warp stores it: four rows per store instruction, eight lanes
+// per row, 16 bytes per lane -- whole sectors, with only the first and last
+// chunk of a row stored word by word where they are partial.
 #include "device_common.cuh"
 #include "rpq_internal.h"
 
 namespace rpq {
 
-template <int NW, bool WRITE, bool DIGEST>
-__global__ void emit_kernel(const EmitParams p) {
+namespace {
+
+constexpr u32 EMIT_BATCH = 8;            // tiles per cooperative load
+constexpr u32 EMIT_BV = EMIT_BATCH * 32;  // vertices per batch
+constexpr u32 EMIT_RING = 64;            // ring words per row (write pass)
+static_assert(EMIT_TILES % EMIT_BATCH == 0, "segments hold whole batches");
+
+// Shared-memory words of the write pass for 2 * NW warps: the batch [2 * NW
+// columns][EMIT_BV], the rings [2 * NW][32 rows][EMIT_RING], the flush slots
+// [2 * NW][32].
+constexpr u32 emit_write_smem_words(int nw) {
+  return 2 * nw * EMIT_BV + 2 * nw * 32 * EMIT_RING + 2 * nw * 32;
+}
+
+// 32 x 32 bit transpose across a warp: on entry lane i holds row i (bit k =
+// element (i, k)), on return lane j holds column j (bit i = element (i, j)).
+// The recursive block transpose: stages of width 16, 8, 4, 2, 1 each swap the
+// off-diagonal blocks between lanes i and i ^ s -- a shuffle, a rotate by s
+// (right for the upper lane, left for the lower one) and a bit select.
+__device__ __forceinline__ u32 warp_transpose32(u32 x) {
+  const u32 lane = lane_id();
+#pragma unroll
+  for (int k = 4; k >= 0; k--) {
+    const u32 s = 1u << k;
+    const u32 M = k == 4 ? 0x0000FFFFu : k == 3 ? 0x00FF00FFu : k == 2 ? 0x0F0F0F0Fu : k == 1 ? 0x33333333u : 0x55555555u;
+    const bool hi = (lane & s) != 0;
+    const u32 y = __shfl_xor_sync(FULL_MASK, x, s);
+    const u32 t = __funnelshift_r(y, y, hi ? s : 32 - s);
+    const u32 keep = hi ? ~M : M;
+    x = (x & keep) | (t & ~keep);
+  }
+  return x;
+}
+
+// Cooperative batch load, in two halves so that the next batch's loads can be
+// in flight while the current one is processed.  fetch: this thread's four
+// 64-bit visited words of the batch starting at vertex w_first (vertices
+// w_first .. w_first + nv - 1 of group g, OR over the accepting states; zero
+// past nv or n); store: put them in s_vis[column][vertex].
+template <int NW>
+__device__ __forceinline__ void batch_fetch(const EmitParams &p, u32 final_mask, u32 g, u32 w_first, u32 nv,
+                                            u64 (&pre)[4]) {
+  static_assert(EMIT_BV * NW == 4 * 64 * NW, "four words per thread");
+#pragma unroll
+  for (u32 r = 0; r < 4; r++) {
+    const u32 k = threadIdx.x + r * (64 * NW);
+    const u32 v = k / NW, h = k % NW;
+    const u32 w = w_first + v;
+    u64 word = 0;
+    if (v < nv && w < p.n)
+      for (u32 fm = final_mask; fm; fm &= fm - 1) {
+        const u32 q = __ffs(fm) - 1;
+        word |= __ldg(p.vis + (((u64)q * p.n + w) * p.G + g) * NW + h);
+      }
+    pre[r] = word;
+  }
+}
+
+template <int NW>
+__device__ __forceinline__ void batch_store(const u64 (&pre)[4], u32 *s_vis) {
+#pragma unroll
+  for (u32 r = 0; r < 4; r++) {
+    const u32 k = threadIdx.x + r * (64 * NW);
+    const u32 v = k / NW, h = k % NW;
+    s_vis[(2 * h) * EMIT_BV + v] = (u32)pre[r];
+    s_vis[(2 * h + 1) * EMIT_BV + v] = (u32)(pre[r] >> 32);
+  }
+}
+
+__device__ __forceinline__ void digest_add(u64 src, u32 y, u64 &hsum, u64 &hxor) {
+  const u64 h = splitmix64(src | (u64)y);
+  hsum += h;
+  hxor ^= h;
+}
+
+__device__ __forceinline__ void digest_flush(u64 hsum, u64 hxor, u64 *digest) {
+  hsum = warp_sum(hsum);
+  hxor = warp_xor(hxor);
+  if (lane_id() == 0 && (hsum | hxor)) {
+    atomicAdd(&digest[0], hsum);
+    atomicXor(&digest[1], hxor);
+  }
+}
+
+// Stores the rows whose lanes are set in R.  Row j's words [rd_j, end_j) sit
+// in its ring at position mod EMIT_RING and go to base_j[rd_j .. end_j); all
+// of them lie in the 32-word chunk that starts at rd_j & ~31 (base_j is
+// 128-byte aligned).  Rows are taken four per round, eight lanes per row,
+// four words per lane.
+__device__ __forceinline__ void ring_flush(u32 R, u32 rd, u32 end, u32 *base, const u32 *ring, u32 *slots) {
+  const u32 lane = lane_id();
+  if (R & (1u << lane)) slots[__popc(R & lanemask_lt())] = lane;
+  __syncwarp();
+  const u32 n_rows = __popc(R);
+  for (u32 r0 = 0; r0 < n_rows; r0 += 4) {
+    const u32 idx = r0 + (lane >> 3);
+    const bool act = idx < n_rows;
+    const u32 j = slots[act ? idx : 0];
+    const u32 rdj = __shfl_sync(FULL_MASK, rd, j);
+    const u32 endj = __shfl_sync(FULL_MASK, end, j);
+    u32 *bj = reinterpret_cast<u32 *>(__shfl_sync(FULL_MASK, reinterpret_cast<u64>(base), j));
+    if (act) {
+      const u32 piece = (rdj & ~31u) + (lane & 7) * 4;
+      u32 *d = bj + piece;
+      const u32 *s = ring + j * EMIT_RING + (piece & (EMIT_RING - 1));
+      if (piece >= rdj && piece + 4 <= endj) {
+        *reinterpret_cast<uint4 *>(d) = *reinterpret_cast<const uint4 *>(s);
+      } else {
+#pragma unroll
+        for (u32 k = 0; k < 4; k++)
+          if (piece + k >= rdj && piece + k < endj) d[k] = s[k];
+      }
+    }
+  }
+  __syncwarp();
+}
+
+}  // namespace
+
+// Count pass: cnt[lane][segment] = the lane's members in the segment; with
+// DIGEST, also the digest of those (source, y) rows (count-only results).
+template <int NW, bool DIGEST>
+__global__ void __launch_bounds__(64 * NW, NW == 1 ? 16 : 4) emit_count_kernel(const EmitParams p) {
+  __shared__ u32 s_vis[2 * NW * EMIT_BV];
   // groups of one segment are adjacent blocks, so they read the same
   // visited lines close together in time
   const u32 g = blockIdx.x % p.G, seg = blockIdx.x / p.G;
   const u32 col = threadIdx.x >> 5, lane = lane_id();
-  const u32 K = 64 * NW;
-  const u64 glane = (u64)g * K + col * 32 + lane;
+  const u64 glane = (u64)g * (64 * NW) + col * 32 + lane;
   const u32 src = p.lanesrc[glane];
   const u32 valid_cols = __ballot_sync(FULL_MASK, src != NO_SOURCE);
-  const u32 *vis32 = reinterpret_cast<const u32 *>(p.vis);
-  const u32 lt = (1u << lane) - 1u;
-  u64 cnt = 0, hsum = 0, hxor = 0;
-  // count pass: per-lane counts of this thread's vertices as bit planes
-  // (EMIT_TILES <= 2^CNT_PLANES - 1 vertices per thread)
-  constexpr int CNT_PLANES = 8;
+  const u64 src_hi = (u64)src << 32;
+  const u32 w_begin = seg * EMIT_SEG;
+  const u32 n_tiles = min((u32)EMIT_TILES, (p.n - w_begin + 31) / 32);
+  constexpr int CNT_PLANES = 8;  // EMIT_TILES <= 2^CNT_PLANES - 1 vertices per thread
   static_assert(EMIT_TILES < (1 << CNT_PLANES), "count planes too narrow");
   u32 planes[CNT_PLANES];
 #pragma unroll
   for (int k = 0; k < CNT_PLANES; k++) planes[k] = 0;
-  u64 pos = 0;  // lane `lane`'s next output position (write pass)
-  if (WRITE) pos = p.off[glane * p.segs + seg];
-  const u32 w_begin = seg * EMIT_SEG;
-  for (u32 t = 0; t < EMIT_TILES; t++) {
-    const u32 w0 = w_begin + t * 32;
-    if (w0 >= p.n) break;
-    const u32 w = w0 + lane;
-    u32 x = 0;
-    if (w < p.n) {
-      for (u32 fm = p.final_mask; fm; fm &= fm - 1) {
-        u32 q = __ffs(fm) - 1;
-        u64 word = (((u64)q * p.n + w) * p.G + g) * NW;
-        x |= __ldcg(vis32 + word * 2 + col);
-      }
-    }
-    x &= valid_cols;
-    if (!WRITE && !DIGEST) {
-      // count only: add x into per-thread bit-sliced counters (plane k holds
-      // bit k of each lane's count over this thread's vertices so far)
-      u32 carry = x;
+  u32 cnt = 0;
+  u64 hsum = 0, hxor = 0;
+  for (u32 tb = 0; tb < n_tiles; tb += EMIT_BATCH) {
+    u64 pre[4];
+    batch_fetch<NW>(p, p.final_mask, g, w_begin + tb * 32, min(EMIT_BATCH, n_tiles - tb) * 32, pre);
+    __syncthreads();  // the previous batch is consumed
+    batch_store<NW>(pre, s_vis);
+    __syncthreads();
 #pragma unroll
-      for (int k = 0; k < CNT_PLANES; k++) {
-        const u32 t = planes[k] & carry;
-        planes[k] ^= carry;
-        carry = t;
-      }
-      continue;
-    }
-    for (u32 rows = __reduce_or_sync(FULL_MASK, x); rows; rows &= rows - 1) {
-      const u32 j = __ffs(rows) - 1;
-      const u32 mine = (x >> j) & 1u;
-      const u32 m = __ballot_sync(FULL_MASK, mine);
-      if (WRITE) {
-        const u64 base = __shfl_sync(FULL_MASK, pos, j);
-        if (mine) p.dst[base + __popc(m & lt)] = w;
-      }
+    for (u32 t = 0; t < EMIT_BATCH; t++) {
+      const u32 x = s_vis[col * EMIT_BV + t * 32 + lane] & valid_cols;  // zero past the segment's end
       if (DIGEST) {
-        const u32 sj = __shfl_sync(FULL_MASK, src, j);
-        if (mine) {
-          u64 h = splitmix64(((u64)sj << 32) | (u64)w);
-          hsum += h;
-          hxor ^= h;
+        u32 m = warp_transpose32(x);
+        cnt += __popc(m);
+        const u32 w0 = w_begin + (tb + t) * 32;
+        for (; m; m &= m - 1) digest_add(src_hi, w0 + __ffs(m) - 1, hsum, hxor);
+      } else {
+        u32 carry = x;
+#pragma unroll
+        for (int k = 0; k < CNT_PLANES; k++) {
+          const u32 c = planes[k] & carry;
+          planes[k] ^= carry;
+          carry = c;
         }
       }
-      if (lane == j) {
-        if (WRITE)
-          pos += __popc(m);
-        else
-          cnt += __popc(m);
-      }
     }
   }
-  if (!WRITE && !DIGEST) {
-    // lane j's count = sum over planes k of 2^k * (threads with bit j set in
-    // plane k): transpose each plane with 32 ballots
+  if (!DIGEST) {
+    // lane j's count = sum over planes k of 2^k * (thread bits j of plane k)
 #pragma unroll
-    for (int k = 0; k < CNT_PLANES; k++) {
-      if (!__any_sync(FULL_MASK, planes[k])) continue;
-      u32 mine = 0;
-#pragma unroll
-      for (int j = 0; j < 32; j++) {
-        const u32 b = __ballot_sync(FULL_MASK, (planes[k] >> j) & 1u);
-        if (lane == (u32)j) mine = b;
-      }
-      cnt += (u64)__popc(mine) << k;
-    }
+    for (int k = 0; k < CNT_PLANES; k++) cnt += (u32)__popc(warp_transpose32(planes[k])) << k;
   }
-  if (!WRITE) p.cnt[glane * p.segs + seg] = (u32)cnt;
-  if (DIGEST) {
-    hsum = warp_sum(hsum);
-    hxor = warp_xor(hxor);
-    if (lane == 0 && (hsum | hxor)) {
-      atomicAdd(&p.digest[0], hsum);
-      atomicXor(&p.digest[1], hxor);
-    }
-  }
+  p.cnt[glane * p.segs + seg] = cnt;
+  if (DIGEST) digest_flush(hsum, hxor, p.digest);
 }
 
-// Pass 1 (write = false) counts per (lane, segment); pass 2 (write = true)
-// writes the destinations.  The row digest is folded in the pass given
-// digest = true (the write pass when rows are kept, else the count pass).
+// Write pass: dst[off[lane][segment] ...] = the lane's members in vertex
+// order, through per-row rings in shared memory (see the head of the file).
+// Positions are kept relative to base = the row's first output word rounded
+// down to a 128-byte boundary; the ring slot of position x is x mod
+// EMIT_RING, so a 32-word aligned chunk of the output is 32 consecutive ring
+// words.
+template <int NW>
+__global__ void __launch_bounds__(64 * NW, NW == 1 ? 16 : 3) emit_write_kernel(const EmitParams p) {
+  extern __shared__ __align__(16) u32 emit_smem[];
+  constexpr u32 COLS = 2 * NW;
+  const u32 g = blockIdx.x % p.G, seg = blockIdx.x / p.G;
+  const u32 col = threadIdx.x >> 5, lane = lane_id();
+  u32 *s_vis = emit_smem;                                           // [COLS][EMIT_BV]
+  u32 *ring = emit_smem + COLS * EMIT_BV + col * 32 * EMIT_RING;    // this warp's [32][EMIT_RING]
+  u32 *slots = emit_smem + COLS * EMIT_BV + COLS * 32 * EMIT_RING + col * 32;
+  u32 *myring = ring + lane * EMIT_RING;
+  const u64 glane = (u64)g * (64 * NW) + col * 32 + lane;
+  const u32 src = p.lanesrc[glane];
+  const u32 valid_cols = __ballot_sync(FULL_MASK, src != NO_SOURCE);
+  const u64 pos0 = p.off[glane * p.segs + seg];
+  u32 *base = p.dst + (pos0 & ~31ull);
+  u32 rd = (u32)pos0 & 31u, wr = rd;  // stored / placed words of this row, relative to base
+  const u32 w_begin = seg * EMIT_SEG;
+  const u32 n_tiles = min((u32)EMIT_TILES, (p.n - w_begin + 31) / 32);
+  u64 pre[4];
+  batch_fetch<NW>(p, p.final_mask, g, w_begin, min(EMIT_BATCH, n_tiles) * 32, pre);
+  for (u32 tb = 0; tb < n_tiles; tb += EMIT_BATCH) {
+    const u32 nt = min(EMIT_BATCH, n_tiles - tb);
+    __syncthreads();  // the previous batch is consumed
+    batch_store<NW>(pre, s_vis);
+    __syncthreads();
+    if (tb + EMIT_BATCH < n_tiles)  // next batch in flight while this one is placed
+      batch_fetch<NW>(p, p.final_mask, g, w_begin + (tb + EMIT_BATCH) * 32,
+                      min(EMIT_BATCH, n_tiles - tb - EMIT_BATCH) * 32, pre);
+    for (u32 t = 0; t < nt; t++) {
+      u32 m = warp_transpose32(s_vis[col * EMIT_BV + t * 32 + lane] & valid_cols);
+      const u32 wb = w_begin + (tb + t) * 32 - 1;
+      // at most 31 words were pending, so the ring (64) holds this tile's 32
+      for (; m; m &= m - 1) myring[wr++ & (EMIT_RING - 1)] = wb + __ffs(m);
+      const bool full = wr > (rd | 31u);  // rd's 32-word chunk is complete
+      const u32 R = __ballot_sync(FULL_MASK, full);
+      if (R) {
+        ring_flush(R, rd, (rd | 31u) + 1u, base, ring, slots);
+        if (full) rd = (rd | 31u) + 1u;
+      }
+    }
+  }
+  const u32 R = __ballot_sync(FULL_MASK, wr > rd);  // the partial last chunks
+  if (R) ring_flush(R, rd, wr, base, ring, slots);
+}
+
+// Pass 1 (write = false) counts per (lane, segment), with the digest folded
+// when digest = true; pass 2 (write = true, digest = false) writes the
+// destinations.
 cudaError_t launch_emit(int nw, bool write, bool digest, const EmitParams &p, cudaStream_t st) {
   const unsigned grid = p.segs * p.G;
   const int threads = nw == 1 ? 64 : 256;
-  if (nw == 1) {
-    if (write)
-      digest ? emit_kernel<1, true, true><<<grid, threads, 0, st>>>(p)
-             : emit_kernel<1, true, false><<<grid, threads, 0, st>>>(p);
+  if (!write) {
+    if (nw == 1)
+      digest ? emit_count_kernel<1, true><<<grid, threads, 0, st>>>(p)
+             : emit_count_kernel<1, false><<<grid, threads, 0, st>>>(p);
     else
-      digest ? emit_kernel<1, false, true><<<grid, threads, 0, st>>>(p)
-             : emit_kernel<1, false, false><<<grid, threads, 0, st>>>(p);
-  } else {
-    if (write)
-      digest ? emit_kernel<4, true, true><<<grid, threads, 0, st>>>(p)
-             : emit_kernel<4, true, false><<<grid, threads, 0, st>>>(p);
-    else
-      digest ? emit_kernel<4, false, true><<<grid, threads, 0, st>>>(p)
-             : emit_kernel<4, false, false><<<grid, threads, 0, st>>>(p);
+      digest ? emit_count_kernel<4, true><<<grid, threads, 0, st>>>(p)
+             : emit_count_kernel<4, false><<<grid, threads, 0, st>>>(p);
+    return cudaGetLastError();
   }
+  if (digest) return cudaErrorInvalidValue;  // the write pass does not fold the digest
+  // the NW = 4 write pass needs more than the default 48 KB: opt in once
+  static const cudaError_t attr_err = cudaFuncSetAttribute(
+      emit_write_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(emit_write_smem_words(4) * 4));
+  if (attr_err != cudaSuccess) return attr_err;
+  if (nw == 1)
+    emit_write_kernel<1><<<grid, threads, emit_write_smem_words(1) * 4, st>>>(p);
+  else
+    emit_write_kernel<4><<<grid, threads, emit_write_smem_words(4) * 4, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -146,12 +288,6 @@ cudaError_t launch_emit(int nw, bool write, bool digest, const EmitParams &p, cu
 // lane_off[i + 1])) and all belong to source lanesrc[i].  The 16-byte aligned
 // middle of a lane's rows is read four rows per load, two loads in flight per
 // thread; the unaligned ends row by row.
-__device__ __forceinline__ void digest_add(u64 src, u32 y, u64 &hsum, u64 &hxor) {
-  const u64 h = splitmix64(src | (u64)y);
-  hsum += h;
-  hxor ^= h;
-}
-
 __global__ void row_digest_kernel(const u32 *__restrict__ lanesrc, const u64 *__restrict__ lane_off, u32 n_lanes,
                                   const u32 *__restrict__ dst, u64 *__restrict__ digest) {
   u64 hsum = 0, hxor = 0;
@@ -204,42 +340,33 @@ cudaError_t launch_row_digest(const uint32_t *lanesrc, const unsigned long long 
 // holds lane 32c + j's members and folds its own digest; one set of atomics
 // per lane and segment.
 template <int NW>
-__global__ void emit_lane_stats_kernel(const EmitParams p, u64 *__restrict__ lane_stats) {
+__global__ void __launch_bounds__(64 * NW, NW == 1 ? 16 : 4) emit_lane_stats_kernel(const EmitParams p,
+                                                                                   u64 *__restrict__ lane_stats) {
+  __shared__ u32 s_vis[2 * NW * EMIT_BV];
   const u32 g = blockIdx.x % p.G, seg = blockIdx.x / p.G;
   const u32 final_mask = p.final_g ? p.final_g[g] : p.final_mask;  // per-group automata
   const u32 col = threadIdx.x >> 5, lane = lane_id();
-  const u32 K = 64 * NW;
-  const u64 glane = (u64)g * K + col * 32 + lane;
+  const u64 glane = (u64)g * (64 * NW) + col * 32 + lane;
   const u32 src = p.lanesrc[glane];
   const u32 valid_cols = __ballot_sync(FULL_MASK, src != NO_SOURCE);
-  const u32 *vis32 = reinterpret_cast<const u32 *>(p.vis);
-  u64 cnt = 0, hsum = 0, hxor = 0;
+  const u64 src_hi = (u64)src << 32;
   const u32 w_begin = seg * EMIT_SEG;
-  for (u32 t = 0; t < EMIT_TILES; t++) {
-    const u32 w0 = w_begin + t * 32;
-    if (w0 >= p.n) break;
-    const u32 w = w0 + lane;
-    u32 x = 0;
-    if (w < p.n) {
-      for (u32 fm = final_mask; fm; fm &= fm - 1) {
-        u32 q = __ffs(fm) - 1;
-        u64 word = (((u64)q * p.n + w) * p.G + g) * NW;
-        x |= __ldcg(vis32 + word * 2 + col);
-      }
-    }
-    x &= valid_cols;
-    if (!__any_sync(FULL_MASK, x)) continue;
-    u32 mine = 0;
-#pragma unroll
-    for (int j = 0; j < 32; j++) {
-      u32 b = __ballot_sync(FULL_MASK, (x >> j) & 1u);
-      if (lane == (u32)j) mine = b;
-    }
-    cnt += __popc(mine);
-    for (u32 b = mine; b; b &= b - 1) {
-      u64 h = splitmix64(((u64)src << 32) | (u64)(w0 + __ffs(b) - 1));
-      hsum += h;
-      hxor ^= h;
+  const u32 n_tiles = min((u32)EMIT_TILES, (p.n - w_begin + 31) / 32);
+  u64 cnt = 0, hsum = 0, hxor = 0;
+  for (u32 tb = 0; tb < n_tiles; tb += EMIT_BATCH) {
+    const u32 nt = min(EMIT_BATCH, n_tiles - tb);
+    u64 pre[4];
+    batch_fetch<NW>(p, final_mask, g, w_begin + tb * 32, nt * 32, pre);
+    __syncthreads();
+    batch_store<NW>(pre, s_vis);
+    __syncthreads();
+    for (u32 t = 0; t < nt; t++) {
+      const u32 x = s_vis[col * EMIT_BV + t * 32 + lane] & valid_cols;
+      if (!__any_sync(FULL_MASK, x)) continue;
+      u32 m = warp_transpose32(x);
+      cnt += __popc(m);
+      const u32 w0 = w_begin + (tb + t) * 32;
+      for (; m; m &= m - 1) digest_add(src_hi, w0 + __ffs(m) - 1, hsum, hxor);
     }
   }
   if (cnt) {
@@ -284,13 +411,7 @@ __global__ void emit_pairs_kernel(const EmitParams p, u32 *__restrict__ out) {
         x |= __ldcg(vis32 + word * 2 + col);
       }
     }
-    x &= valid_cols;
-    u32 mine = 0;
-#pragma unroll
-    for (int j = 0; j < 32; j++) {
-      u32 b = __ballot_sync(FULL_MASK, (x >> j) & 1u);
-      if (lane == (u32)j) mine = b;
-    }
+    const u32 mine = warp_transpose32(x & valid_cols);
     for (u32 b = mine; b; b &= b - 1) {
       out[2 * pos] = src;
       out[2 * pos + 1] = w0 + (__ffs(b) - 1);

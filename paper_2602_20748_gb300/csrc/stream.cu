@@ -1,13 +1,14 @@
-// Streamed materialization: the sorted rows of one RPQ over a range of start
-// vertices, delivered to the host one block at a time while the device keeps
-// exploring (the batch-wise result transfer of the paper's Section 5, with a
-// compact row layout).
+// Streamed materialization: the sorted rows of one or more RPQs over a range
+// of start vertices, delivered to the host one block at a time while the
+// device keeps exploring (the batch-wise result transfer of the paper's
+// Section 5, with a compact row layout).
 //
 // Two host threads drive the device:
-//   * the evaluation thread runs the start vertices in batches of one
-//     traversal launch (eval + emission, the rows stay on the device) and
-//     queues each finished batch; at most MAX_PENDING batches wait, so the
-//     device memory held by rows stays bounded;
+//   * the evaluation thread runs the queries one after another, each over the
+//     start vertices in batches of one traversal launch (eval + emission, the
+//     rows stay on the device), and queues each finished batch; at most
+//     MAX_PENDING batches wait to be copied, so the device memory held by rows
+//     stays bounded;
 //   * the copy thread splits a finished batch into pieces of at most SLOT_ROWS
 //     destinations and copies each into a free pinned host slot on a copy
 //     stream of its own, so the copy of batch k overlaps the traversal of
@@ -15,7 +16,8 @@
 // The caller takes filled slots in order through rpq_stream_next; a slot goes
 // back to the copier when the caller asks for the next block.  Device memory
 // of a copied batch is released by the evaluation thread (the only thread that
-// allocates), after the copy's completion event.
+// allocates) once the copy's completion event has fired; the thread does not
+// wait for copies in flight, so the next traversal starts while they run.
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -34,6 +36,7 @@ constexpr int N_SLOTS = 3;
 constexpr size_t MAX_PENDING = 2;  // evaluated batches not yet copied
 
 struct Batch {
+  uint32_t query = 0;  // index into the stream's queries
   std::vector<rpq::RowChunk> chunks;
   std::vector<std::vector<uint32_t>> lanesrc;  // host copies, per chunk
   std::vector<std::vector<uint64_t>> lane_off;
@@ -46,6 +49,7 @@ struct Slot {
   std::vector<uint32_t> sources;
   std::vector<uint64_t> offsets;
   uint64_t rows = 0;
+  uint32_t query = 0;
 };
 
 }  // namespace
@@ -53,7 +57,7 @@ struct Slot {
 struct rpq_stream {
   rpq_ctx *ctx = nullptr;
   const rpq_graph *g = nullptr;
-  const rpq_query *q = nullptr;
+  std::vector<const rpq_query *> qs;
   uint32_t begin = 0, end = 0, batch = 4096;
   bool reverse = false;
   cudaStream_t copy = nullptr;
@@ -82,83 +86,97 @@ void release_batch(rpq_stream *s, Batch *b) {
   delete b;
 }
 
+// Releases the copied batches whose copies have completed (all of them when
+// wait is set); the others stay queued.
+void release_copied(rpq_stream *s, bool wait) {
+  std::vector<Batch *> done;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto it = s->copied.begin(); it != s->copied.end();) {
+      if (wait || !(*it)->copied || cudaEventQuery((*it)->copied) != cudaErrorNotReady) {
+        done.push_back(*it);
+        it = s->copied.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
+  for (Batch *b : done) release_batch(s, b);
+}
+
 void eval_thread(rpq_stream *s) {
   cudaSetDevice(rpq::ctx_device(s->ctx));
-  for (uint64_t b0 = s->begin; b0 < s->end; b0 += s->batch) {
-    std::vector<Batch *> to_free;
-    {
-      std::unique_lock<std::mutex> lk(s->mu);
-      s->cv.wait(lk, [&] { return s->stop || s->pending.size() < MAX_PENDING || !s->copied.empty(); });
-      to_free.assign(s->copied.begin(), s->copied.end());
-      s->copied.clear();
-      if (s->stop) {
-        lk.unlock();
-        for (Batch *b : to_free) release_batch(s, b);
-        break;
-      }
-    }
-    for (Batch *b : to_free) release_batch(s, b);
-    {
-      std::unique_lock<std::mutex> lk(s->mu);
-      s->cv.wait(lk, [&] { return s->stop || s->pending.size() < MAX_PENDING; });
-      if (s->stop) break;
-    }
-    const uint32_t e = (uint32_t)std::min<uint64_t>(s->end, b0 + s->batch);
-    std::vector<uint32_t> srcs(e - (uint32_t)b0);
-    for (uint32_t i = 0; i < srcs.size(); i++) srcs[i] = (uint32_t)b0 + i;
-    auto *b = new Batch;
-    rpq_stats st;
-    std::memset(&st, 0, sizeof(st));
-    uint64_t hs = 0, hx = 0;
-    int rc = rpq::rpq_rows_for_sources(s->ctx, s->g, s->q, srcs, s->reverse, &b->chunks, &st, &hs, &hx);
-    uint64_t nrows = 0;
-    if (rc == RPQ_OK) {
-      cudaStream_t cs = rpq::ctx_stream(s->ctx);
-      for (const rpq::RowChunk &c : b->chunks) {
-        b->lanesrc.emplace_back(c.n_lanes);
-        b->lane_off.emplace_back((size_t)c.n_lanes + 1);
-        cudaError_t ce = cudaMemcpyAsync(b->lanesrc.back().data(), c.lanesrc, (size_t)c.n_lanes * 4,
-                                         cudaMemcpyDeviceToHost, cs);
-        if (ce == cudaSuccess)
-          ce = cudaMemcpyAsync(b->lane_off.back().data(), c.lane_off, ((size_t)c.n_lanes + 1) * 8,
-                               cudaMemcpyDeviceToHost, cs);
-        if (ce == cudaSuccess) ce = cudaStreamSynchronize(cs);
-        if (ce != cudaSuccess) {
-          rc = rpq::ctx_error(s->ctx, RPQ_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(ce));
+  bool failed = false;
+  for (uint32_t qi = 0; qi < s->qs.size() && !failed; qi++) {
+    for (uint64_t b0 = s->begin; b0 < s->end; b0 += s->batch) {
+      release_copied(s, false);
+      {
+        std::unique_lock<std::mutex> lk(s->mu);
+        s->cv.wait(lk, [&] { return s->stop || s->pending.size() < MAX_PENDING; });
+        if (s->stop) {
+          failed = true;
           break;
         }
-        nrows += c.rows;
       }
+      const uint32_t e = (uint32_t)std::min<uint64_t>(s->end, b0 + s->batch);
+      std::vector<uint32_t> srcs(e - (uint32_t)b0);
+      for (uint32_t i = 0; i < srcs.size(); i++) srcs[i] = (uint32_t)b0 + i;
+      auto *b = new Batch;
+      b->query = qi;
+      rpq_stats st;
+      std::memset(&st, 0, sizeof(st));
+      uint64_t hs = 0, hx = 0;
+      int rc = rpq::rpq_rows_for_sources(s->ctx, s->g, s->qs[qi], srcs, s->reverse, &b->chunks, &st, &hs, &hx);
+      uint64_t nrows = 0;
+      if (rc == RPQ_OK) {
+        cudaStream_t cs = rpq::ctx_stream(s->ctx);
+        for (const rpq::RowChunk &c : b->chunks) {
+          b->lanesrc.emplace_back(c.n_lanes);
+          b->lane_off.emplace_back((size_t)c.n_lanes + 1);
+          cudaError_t ce = cudaMemcpyAsync(b->lanesrc.back().data(), c.lanesrc, (size_t)c.n_lanes * 4,
+                                           cudaMemcpyDeviceToHost, cs);
+          if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(b->lane_off.back().data(), c.lane_off, ((size_t)c.n_lanes + 1) * 8,
+                                 cudaMemcpyDeviceToHost, cs);
+          if (ce == cudaSuccess) ce = cudaStreamSynchronize(cs);
+          if (ce != cudaSuccess) {
+            rc = rpq::ctx_error(s->ctx, RPQ_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(ce));
+            break;
+          }
+          nrows += c.rows;
+        }
+      }
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (rc != RPQ_OK) {
+        s->rc = rc;
+        s->copied.push_back(b);  // released below
+        failed = true;
+        break;
+      }
+      s->rows += nrows;
+      s->dsum += hs;
+      s->dxor ^= hx;
+      rpq_stats &a = s->stats;
+      a.product_edges += st.product_edges;
+      a.product_vertices += st.product_vertices;
+      a.levels += st.levels;
+      a.push_levels += st.push_levels;
+      a.pull_levels += st.pull_levels;
+      a.group_edges += st.group_edges;
+      a.group_rows += st.group_rows;
+      a.group_vertices += st.group_vertices;
+      a.pull_edges += st.pull_edges;
+      a.pull_vertices += st.pull_vertices;
+      a.lane_words = st.lane_words ? st.lane_words : a.lane_words;
+      a.lane_groups += st.lane_groups;
+      a.bfs_ms += st.bfs_ms;
+      a.emit_ms += st.emit_ms;
+      a.bfs_launches += st.bfs_launches;
+      a.launches += st.launches;
+      a.alg_bytes += st.alg_bytes;
+      s->pending.push_back(b);
+      s->cv.notify_all();
     }
-    std::lock_guard<std::mutex> lk(s->mu);
-    if (rc != RPQ_OK) {
-      s->rc = rc;
-      s->copied.push_back(b);  // released below, after the loop
-      break;
-    }
-    s->rows += nrows;
-    s->dsum += hs;
-    s->dxor ^= hx;
-    rpq_stats &a = s->stats;
-    a.product_edges += st.product_edges;
-    a.product_vertices += st.product_vertices;
-    a.levels += st.levels;
-    a.push_levels += st.push_levels;
-    a.pull_levels += st.pull_levels;
-    a.group_edges += st.group_edges;
-    a.group_rows += st.group_rows;
-    a.group_vertices += st.group_vertices;
-    a.pull_edges += st.pull_edges;
-    a.pull_vertices += st.pull_vertices;
-    a.lane_words = st.lane_words ? st.lane_words : a.lane_words;
-    a.lane_groups += st.lane_groups;
-    a.bfs_ms += st.bfs_ms;
-    a.emit_ms += st.emit_ms;
-    a.bfs_launches += st.bfs_launches;
-    a.launches += st.launches;
-    a.alg_bytes += st.alg_bytes;
-    s->pending.push_back(b);
-    s->cv.notify_all();
   }
   std::lock_guard<std::mutex> lk(s->mu);
   s->eval_done = true;
@@ -212,6 +230,7 @@ void copy_thread(rpq_stream *s) {
         }
         sl.offsets.push_back(k);
         sl.rows = k;
+        sl.query = b->query;
         std::lock_guard<std::mutex> lk(s->mu);
         if (ce != cudaSuccess) {
           s->rc = rpq::ctx_error(s->ctx, RPQ_ERR_CUDA, std::string("stream copy: ") + cudaGetErrorString(ce));
@@ -260,22 +279,28 @@ void destroy_stream(rpq_stream *s) {
 
 extern "C" {
 
-int rpq_stream_open(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, uint32_t src_begin, uint32_t src_end,
-                    uint32_t flags, rpq_stream **out) {
-  if (!ctx || !g || !q || !out) return rpq::ctx_error(ctx, RPQ_ERR_INVALID_ARG, "null argument");
+int rpq_stream_open_multi(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *const *queries, uint32_t n_queries,
+                          uint32_t src_begin, uint32_t src_end, uint32_t flags, rpq_stream **out) {
+  if (!ctx || !g || !queries || !out) return rpq::ctx_error(ctx, RPQ_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
+  if (n_queries == 0) return rpq::ctx_error(ctx, RPQ_ERR_INVALID_ARG, "no queries");
+  for (uint32_t i = 0; i < n_queries; i++)
+    if (!queries[i]) return rpq::ctx_error(ctx, RPQ_ERR_INVALID_ARG, "null query");
   const int dev = rpq::ctx_device(ctx);
   if (dev < 0) return rpq::ctx_error(ctx, RPQ_ERR_NO_DEVICE, "host-only context has no GPU");
   if (flags & ~(uint32_t)RPQ_REVERSE) return rpq::ctx_error(ctx, RPQ_ERR_INVALID_ARG, "flags: only RPQ_REVERSE");
   if (src_begin > src_end || src_end > rpq::graph_dev(g).n)
     return rpq::ctx_error(ctx, RPQ_ERR_INVALID_ARG, "bad source range");
-  if ((flags & RPQ_REVERSE) && !rpq::query_host(q).has_rev)
-    return rpq::ctx_error(ctx, RPQ_ERR_TOO_COMPLEX, "the reversed language needs more than RPQ_MAX_STATES states");
+  if (flags & RPQ_REVERSE)
+    for (uint32_t i = 0; i < n_queries; i++)
+      if (!rpq::query_host(queries[i]).has_rev)
+        return rpq::ctx_error(ctx, RPQ_ERR_TOO_COMPLEX,
+                              "the reversed language needs more than RPQ_MAX_STATES states");
   cudaSetDevice(dev);
   auto *s = new rpq_stream;
   s->ctx = ctx;
   s->g = g;
-  s->q = q;
+  s->qs.assign(queries, queries + n_queries);
   s->begin = src_begin;
   s->end = src_end;
   s->reverse = (flags & RPQ_REVERSE) != 0;
@@ -300,6 +325,15 @@ int rpq_stream_open(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, uint32
   s->t_copy = std::thread(copy_thread, s);
   *out = s;
   return RPQ_OK;
+}
+
+int rpq_stream_open(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, uint32_t src_begin, uint32_t src_end,
+                    uint32_t flags, rpq_stream **out) {
+  if (!q) {
+    if (out) *out = nullptr;
+    return rpq::ctx_error(ctx, RPQ_ERR_INVALID_ARG, "null argument");
+  }
+  return rpq_stream_open_multi(ctx, g, &q, 1, src_begin, src_end, flags, out);
 }
 
 int rpq_stream_next(rpq_stream *s, rpq_row_block *block) {
@@ -327,6 +361,7 @@ int rpq_stream_next(rpq_stream *s, rpq_row_block *block) {
   block->offsets = sl.offsets.data();
   block->dst = sl.host;
   block->n_rows = sl.rows;
+  block->query = sl.query;
   return RPQ_OK;
 }
 

@@ -423,26 +423,35 @@ class Server:
 
 class rpq_row_block(ctypes.Structure):
     _fields_ = [("n_sources", c_u32), ("sources", P(c_u32)), ("offsets", P(c_u64)), ("dst", P(c_u32)),
-                ("n_rows", c_u64)]
+                ("n_rows", c_u64), ("query", c_u32)]
 
 
 _lib.rpq_stream_open.argtypes = [c_void_p, c_void_p, c_void_p, c_u32, c_u32, c_u32, P(c_void_p)]
+_lib.rpq_stream_open_multi.argtypes = [c_void_p, c_void_p, P(c_void_p), c_u32, c_u32, c_u32, c_u32, P(c_void_p)]
 _lib.rpq_stream_next.argtypes = [c_void_p, P(rpq_row_block)]
 _lib.rpq_stream_info.argtypes = [c_void_p, P(c_u64), P(c_u64), P(c_u64), P(rpq_stats)]
 _lib.rpq_stream_close.argtypes = [c_void_p]
 _lib.rpq_stream_close.restype = None
-EXPORTED += ["rpq_stream_open", "rpq_stream_next", "rpq_stream_info", "rpq_stream_close"]
+EXPORTED += ["rpq_stream_open", "rpq_stream_open_multi", "rpq_stream_next", "rpq_stream_info", "rpq_stream_close"]
 
 
 class Stream:
     """rpq_stream_*: rows of rho from start vertices [begin, end), block by
-    block, copied to the host while the device keeps exploring."""
+    block, copied to the host while the device keeps exploring.  q is one
+    Query or a sequence of them (rpq_stream_open_multi: the queries run one
+    after another; ``block_query`` is the index of the last block's query)."""
 
-    def __init__(self, ctx: Context, g: Graph, q: Query, begin: int, end: int, flags: int = 0):
+    def __init__(self, ctx: Context, g: Graph, q, begin: int, end: int, flags: int = 0):
         h = c_void_p()
-        ctx.check(_lib.rpq_stream_open(ctx.h, g.h, q.h, begin, end, flags, ctypes.byref(h)))
+        if isinstance(q, Query):
+            ctx.check(_lib.rpq_stream_open(ctx.h, g.h, q.h, begin, end, flags, ctypes.byref(h)))
+        else:
+            qs = list(q)
+            arr = (c_void_p * max(1, len(qs)))(*[x.h for x in qs])
+            ctx.check(_lib.rpq_stream_open_multi(ctx.h, g.h, arr, len(qs), begin, end, flags, ctypes.byref(h)))
         self.ctx, self.g, self.q, self.h = ctx, g, q, h
         self._blk = rpq_row_block()
+        self.block_query = 0
 
     def next_block(self):
         """(sources, offsets, dst) as numpy views of the library's pinned slot
@@ -451,6 +460,7 @@ class Stream:
         b = self._blk
         if b.n_rows == 0:
             return None
+        self.block_query = b.query
         src = np.ctypeslib.as_array(b.sources, shape=(b.n_sources,))
         off = np.ctypeslib.as_array(b.offsets, shape=(b.n_sources + 1,))
         dst = np.ctypeslib.as_array(b.dst, shape=(b.n_rows,))

@@ -96,3 +96,38 @@ def test_stream_row_split_across_slots(ctx):
     assert blocks[0][0][-1] == cut and blocks[1][0][0] == cut
     assert np.array_equal(rows[:, 0], np.repeat(np.arange(4096, dtype=np.uint32), n))
     assert np.array_equal(rows[:, 1], np.tile(np.arange(n, dtype=np.uint32), 4096))
+
+
+def test_stream_multi_query_equals_single(ctx):
+    """rpq_stream_open_multi: the blocks of each query, in order, give exactly
+    that query's single-query stream rows; totals are the sums."""
+    n = 9000
+    src, dst, lab = synth.rmat_graph(14, 6 * n, 4, 1.2, seed=73)
+    src %= n
+    dst %= n
+    g = rpq.load_graph(ctx, n, 4, src, dst, lab)
+    regexes = ["a*", "d", "(a|b)+.c", "a.b*.c"]
+    qs = [rpq.compile_rpq(ctx, r) for r in regexes]
+    lo, hi = 300, 8900  # three launches per query, the last one ragged
+    st = rpq.Stream(ctx, g, qs, lo, hi)
+    per_q = [[] for _ in qs]
+    last = 0
+    while (b := st.next_block()) is not None:
+        s_, o_, d_ = (x.copy() for x in b)
+        assert st.block_query >= last  # queries arrive one after another
+        last = st.block_query
+        per_q[st.block_query].append(np.stack([np.repeat(s_, np.diff(o_).astype(np.int64)), d_], axis=1))
+    rows_m, hs_m, hx_m, stats_m = st.info()
+    st.close()
+    tot, hs, hx, w = 0, 0, 0, 0
+    for i, q in enumerate(qs):
+        got = np.concatenate(per_q[i]).astype(np.uint32) if per_q[i] else np.zeros((0, 2), dtype=np.uint32)
+        want, info, _ = streamed(ctx, g, q, lo, hi)
+        assert np.array_equal(got, want), regexes[i]
+        tot += info[0]
+        hs = (hs + info[1]) % (1 << 64)
+        hx ^= info[2]
+        w += info[3]["product_edges"]
+    assert rows_m == tot and hs_m == hs and hx_m == hx and stats_m["product_edges"] == w
+    with pytest.raises(rpq.RPQError):
+        rpq.Stream(ctx, g, [], lo, hi)
