@@ -65,6 +65,8 @@ struct rpq_ctx {
   rpq::BatchTuning batch = rpq::batch_default_tuning();  // run_rpq_batch tunables
   std::atomic<int> cancel{0};  // set by a server to stop the request in service
   std::vector<void *> pinned;  // pinned host slots lent to streams (kept for reuse)
+  unsigned char *rb_host = nullptr;  // mapped pinned read-back buffer (RB_CAP bytes)
+  void *rb_dev = nullptr;            // its device address
   std::vector<rpq_ctx *> helpers;  // contexts for concurrent sub-evaluations (own streams)
   std::vector<cudaStream_t> helper_streams;
   size_t pinned_bytes = 0;
@@ -158,6 +160,41 @@ void dfree(rpq_ctx *ctx, T *&p, uint64_t count) {
   dev_free(ctx, (void *)p, count * sizeof(T));
   p = nullptr;
 }
+
+// Small device -> host reads (the traversal's control block, totals, source
+// flags) go through a kernel into a mapped pinned buffer instead of the copy
+// engines: a stream's bulk row copies queued there would otherwise hold every
+// such read back until they drain.
+constexpr size_t RB_CAP = 1u << 20;
+
+__global__ void rb_copy_kernel(unsigned char *__restrict__ dst, const unsigned char *__restrict__ src, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+// Queues the copy of `bytes` (off + bytes <= RB_CAP) from device memory src to
+// read-back offset off; the bytes are at ctx->rb_host + off once the stream is
+// synchronized.
+cudaError_t rb_queue(rpq_ctx *ctx, size_t off, const void *src, size_t bytes) {
+  if (!ctx->rb_host) {
+    void *h = nullptr;
+    cudaError_t e = cudaHostAlloc(&h, RB_CAP, cudaHostAllocMapped);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaHostGetDevicePointer(&ctx->rb_dev, h, 0)) != cudaSuccess) {
+      cudaFreeHost(h);
+      return e;
+    }
+    ctx->rb_host = static_cast<unsigned char *>(h);
+  }
+  if (bytes == 0) return cudaSuccess;
+  if (off + bytes > RB_CAP) return cudaErrorInvalidValue;
+  const unsigned blocks = (unsigned)std::min<size_t>((bytes + 255) / 256, 1024);
+  rb_copy_kernel<<<blocks, 256, 0, ctx->stream>>>(static_cast<unsigned char *>(ctx->rb_dev) + off,
+                                                  static_cast<const unsigned char *>(src), bytes);
+  return cudaGetLastError();
+}
+
+constexpr size_t RB_SMALL = (sizeof(BfsCtl) + 15) & ~(size_t)15;  // read-back offset after the control block
 
 bool usable(rpq_ctx *ctx) {
   if (!ctx) return false;
@@ -282,12 +319,15 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
     if (e == cudaSuccess)
       e = launch_source_filter(reverse ? g.in_off : g.out_off, g.n, g.L, lmask, dsrc, srcs_in.size(), dflag,
                                ctx->stream);
+    const bool rb = srcs_in.size() <= RB_CAP;
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(flag.data(), dflag, srcs_in.size(), cudaMemcpyDeviceToHost, ctx->stream);
+      e = rb ? rb_queue(ctx, 0, dflag, srcs_in.size())
+             : cudaMemcpyAsync(flag.data(), dflag, srcs_in.size(), cudaMemcpyDeviceToHost, ctx->stream);
     dfree(ctx, dsrc, srcs_in.size());
     dfree(ctx, dflag, srcs_in.size());
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_err(ctx, e, "source filter");
+    if (rb) std::memcpy(flag.data(), ctx->rb_host, srcs_in.size());
     res->stats.launches += 1;
     kept.reserve(srcs_in.size());
     uint64_t skipped = 0;
@@ -491,9 +531,11 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
     res->stats.launches += 2;
     BfsCtl hctl;
     u64 hsmall[3];
-    CK(cudaMemcpyAsync(&hctl, ctx->ctl, sizeof(BfsCtl), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(hsmall, ctx->small, 3 * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(rb_queue(ctx, 0, ctx->ctl, sizeof(BfsCtl)));
+    CK(rb_queue(ctx, RB_SMALL, ctx->small, 3 * 8));
     CK(cudaStreamSynchronize(ctx->stream));
+    std::memcpy(&hctl, ctx->rb_host, sizeof(BfsCtl));
+    std::memcpy(hsmall, ctx->rb_host + RB_SMALL, 3 * 8);
     if (hctl.err) {
       dfree(ctx, cnt, ncnt);
       dfree(ctx, off, ncnt);
@@ -551,7 +593,7 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
       CK(launch_row_digest(w.lanesrc, c.lane_off, n_lanes, c.dst, ctx->small, ctx->stream));
       res->stats.launches += 3;
       res->chunks.push_back(c);
-      CK(cudaMemcpyAsync(hdig, ctx->small, 16, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(rb_queue(ctx, RB_SMALL, ctx->small, 16));
     }
     CK(cudaEventRecord(ctx->ev[3], ctx->stream));
     dfree(ctx, cnt, ncnt);
@@ -559,6 +601,7 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
     dfree(ctx, tmp, tmpw);
     CK(cudaEventSynchronize(ctx->ev[3]));
     CK(cudaStreamSynchronize(ctx->stream));
+    if (materialize) std::memcpy(hdig, ctx->rb_host + RB_SMALL, 16);
     res->dsum += hdig[0];
     res->dxor ^= hdig[1];
     float ms_bfs = 0, ms_emit = 0;
@@ -687,6 +730,7 @@ void destroy_now(rpq_ctx *c) {
     for (cudaStream_t hs : c->helper_streams) cudaStreamDestroy(hs);
     if (c->pool) cudaMemPoolDestroy(c->pool);
     for (void *h : c->pinned) cudaFreeHost(h);
+    if (c->rb_host) cudaFreeHost(c->rb_host);
   }
   delete c;
 }

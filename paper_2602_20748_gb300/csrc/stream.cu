@@ -35,11 +35,21 @@ constexpr uint64_t SLOT_ROWS = 1ull << 26;  // destinations per pinned slot (256
 constexpr int N_SLOTS = 3;
 constexpr size_t MAX_PENDING = 2;  // evaluated batches not yet copied
 
+// Pinned, device-mapped host buffer for a batch's lane metadata.
+struct MetaBuf {
+  void *h = nullptr;
+  size_t bytes = 0;
+};
+
 struct Batch {
   uint32_t query = 0;  // index into the stream's queries
   std::vector<rpq::RowChunk> chunks;
-  std::vector<std::vector<uint32_t>> lanesrc;  // host copies, per chunk
-  std::vector<std::vector<uint64_t>> lane_off;
+  // host views of each chunk's lane sources and offsets, in `meta`: written
+  // there by a kernel, so that they do not queue behind the bulk row copies
+  // on the copy engine
+  std::vector<const uint32_t *> lanesrc;
+  std::vector<const uint64_t *> lane_off;
+  MetaBuf meta;
   cudaEvent_t copied = nullptr;  // recorded after the batch's last copy
 };
 
@@ -67,6 +77,7 @@ struct rpq_stream {
   std::deque<int> free_slots, ready;
   std::deque<Batch *> pending;  // evaluated, being or to be copied
   std::deque<Batch *> copied;   // copies issued; device rows to release
+  std::vector<MetaBuf> meta_free;  // recycled metadata buffers
   int handed = -1;              // slot the caller holds
   bool eval_done = false, copy_done = false, stop = false;
   int rc = RPQ_OK;
@@ -77,13 +88,80 @@ struct rpq_stream {
 
 namespace {
 
+// Lane metadata of the chunks [lanesrc | lane_off]: copied from the device
+// into mapped pinned memory by this kernel (one word per thread).
+__global__ void meta_to_host(const uint32_t *__restrict__ lanesrc, const unsigned long long *__restrict__ lane_off,
+                             uint32_t n_lanes, uint32_t *h_lanesrc, unsigned long long *h_lane_off) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= n_lanes; i += gridDim.x * blockDim.x) {
+    if (i < n_lanes) h_lanesrc[i] = lanesrc[i];
+    h_lane_off[i] = lane_off[i];
+  }
+}
+
+int meta_get(rpq_stream *s, size_t bytes, MetaBuf *out) {
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (size_t i = 0; i < s->meta_free.size(); i++)
+      if (s->meta_free[i].bytes >= bytes) {
+        *out = s->meta_free[i];
+        s->meta_free.erase(s->meta_free.begin() + i);
+        return RPQ_OK;
+      }
+  }
+  const size_t want = (bytes + 65535) & ~(size_t)65535;
+  cudaError_t e = cudaHostAlloc(&out->h, want, cudaHostAllocMapped);
+  if (e != cudaSuccess) {
+    out->h = nullptr;
+    return rpq::ctx_error(s->ctx, RPQ_ERR_CUDA, std::string("stream metadata buffer: ") + cudaGetErrorString(e));
+  }
+  out->bytes = want;
+  return RPQ_OK;
+}
+
+void meta_put(rpq_stream *s, MetaBuf m) {
+  if (!m.h) return;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->meta_free.push_back(m);
+}
+
 void release_batch(rpq_stream *s, Batch *b) {
   if (b->copied) {
     cudaEventSynchronize(b->copied);
     cudaEventDestroy(b->copied);
   }
   for (rpq::RowChunk &c : b->chunks) rpq::free_row_chunk(s->ctx, c);
+  meta_put(s, b->meta);
   delete b;
+}
+
+// Brings the lane sources and offsets of b's chunks to the host (see Batch).
+int fetch_meta(rpq_stream *s, Batch *b) {
+  size_t bytes = 0;
+  for (const rpq::RowChunk &c : b->chunks) bytes += ((size_t)c.n_lanes + 1) * 8 + (size_t)c.n_lanes * 4 + 8;
+  if (bytes == 0) return RPQ_OK;
+  int rc = meta_get(s, bytes, &b->meta);
+  if (rc != RPQ_OK) return rc;
+  cudaStream_t cs = rpq::ctx_stream(s->ctx);
+  char *h = static_cast<char *>(b->meta.h);
+  cudaError_t e = cudaSuccess;
+  for (const rpq::RowChunk &c : b->chunks) {
+    auto *h_off = reinterpret_cast<uint64_t *>(h);  // 8-byte aligned: each chunk's part is rounded up to 8
+    auto *h_src = reinterpret_cast<uint32_t *>(h + ((size_t)c.n_lanes + 1) * 8);
+    void *d_off = nullptr, *d_src = nullptr;
+    if ((e = cudaHostGetDevicePointer(&d_off, h_off, 0)) != cudaSuccess ||
+        (e = cudaHostGetDevicePointer(&d_src, h_src, 0)) != cudaSuccess)
+      break;
+    meta_to_host<<<(c.n_lanes + 256) / 256, 256, 0, cs>>>(c.lanesrc, c.lane_off, c.n_lanes,
+                                                          static_cast<uint32_t *>(d_src),
+                                                          static_cast<unsigned long long *>(d_off));
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    b->lane_off.push_back(h_off);
+    b->lanesrc.push_back(h_src);
+    h += (((size_t)c.n_lanes + 1) * 8 + (size_t)c.n_lanes * 4 + 7) & ~(size_t)7;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e != cudaSuccess) return rpq::ctx_error(s->ctx, RPQ_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+  return RPQ_OK;
 }
 
 // Releases the copied batches whose copies have completed (all of them when
@@ -128,24 +206,9 @@ void eval_thread(rpq_stream *s) {
       uint64_t hs = 0, hx = 0;
       int rc = rpq::rpq_rows_for_sources(s->ctx, s->g, s->qs[qi], srcs, s->reverse, &b->chunks, &st, &hs, &hx);
       uint64_t nrows = 0;
-      if (rc == RPQ_OK) {
-        cudaStream_t cs = rpq::ctx_stream(s->ctx);
-        for (const rpq::RowChunk &c : b->chunks) {
-          b->lanesrc.emplace_back(c.n_lanes);
-          b->lane_off.emplace_back((size_t)c.n_lanes + 1);
-          cudaError_t ce = cudaMemcpyAsync(b->lanesrc.back().data(), c.lanesrc, (size_t)c.n_lanes * 4,
-                                           cudaMemcpyDeviceToHost, cs);
-          if (ce == cudaSuccess)
-            ce = cudaMemcpyAsync(b->lane_off.back().data(), c.lane_off, ((size_t)c.n_lanes + 1) * 8,
-                                 cudaMemcpyDeviceToHost, cs);
-          if (ce == cudaSuccess) ce = cudaStreamSynchronize(cs);
-          if (ce != cudaSuccess) {
-            rc = rpq::ctx_error(s->ctx, RPQ_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(ce));
-            break;
-          }
-          nrows += c.rows;
-        }
-      }
+      if (rc == RPQ_OK) rc = fetch_meta(s, b);
+      if (rc == RPQ_OK)
+        for (const rpq::RowChunk &c : b->chunks) nrows += c.rows;
       std::lock_guard<std::mutex> lk(s->mu);
       if (rc != RPQ_OK) {
         s->rc = rc;
@@ -200,8 +263,8 @@ void copy_thread(rpq_stream *s) {
     bool ok = true;
     for (size_t ci = 0; ci < b->chunks.size() && ok; ci++) {
       const rpq::RowChunk &c = b->chunks[ci];
-      const std::vector<uint64_t> &off = b->lane_off[ci];
-      const std::vector<uint32_t> &lsrc = b->lanesrc[ci];
+      const uint64_t *off = b->lane_off[ci];
+      const uint32_t *lsrc = b->lanesrc[ci];
       uint32_t lane = 0;
       for (uint64_t r0 = 0; r0 < c.rows && ok;) {
         int si;
@@ -269,6 +332,7 @@ void destroy_stream(rpq_stream *s) {
   if (s->copy) cudaStreamSynchronize(s->copy);
   for (Batch *b : s->pending) release_batch(s, b);
   for (Batch *b : s->copied) release_batch(s, b);
+  for (MetaBuf &m : s->meta_free) cudaFreeHost(m.h);
   for (Slot &sl : s->slots)
     if (sl.done) cudaEventDestroy(sl.done);  // the pinned slots stay with the context
   if (s->copy) cudaStreamDestroy(s->copy);
