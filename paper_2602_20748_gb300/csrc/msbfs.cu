@@ -61,6 +61,23 @@ __device__ __forceinline__ Word<NW> load_cg(const u64 *p) {
   return x;
 }
 
+// PER consecutive words at p (16-byte aligned when PER is even), or all ones
+// when !on.
+template <int PER>
+__device__ __forceinline__ void load_vis(const u64 *p, bool on, u64 (&v)[PER]) {
+  if constexpr (PER % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < PER; k += 2) {
+      const ulonglong2 a = on ? __ldcg(reinterpret_cast<const ulonglong2 *>(p + k)) : make_ulonglong2(~0ull, ~0ull);
+      v[k] = a.x;
+      v[k + 1] = a.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < PER; k++) v[k] = on ? __ldcg(p + k) : ~0ull;
+  }
+}
+
 template <int NW>
 __device__ __forceinline__ void store_w(u64 *p, const Word<NW> &x) {
   if constexpr (NW % 2 == 0) {
@@ -614,12 +631,10 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
       }
       const u64 base = ((u64)q2 * n + w) * wpv + lane_off;
       u64 vis[PER];
+      load_vis<PER>(p.vis + base, lane_on && any, vis);
       bool full = true;
 #pragma unroll
-      for (int k = 0; k < PER; k++) {
-        vis[k] = (lane_on && any) ? __ldcg(p.vis + base + k) : ~0ull;
-        full &= vis[k] == ~0ull;
-      }
+      for (int k = 0; k < PER; k++) full &= vis[k] == ~0ull;
       const u32 fb = __ballot_sync(FULL_MASK, full);
       const bool work = any && (fb & sg_mask) != sg_mask;
       if (!__any_sync(FULL_MASK, work)) continue;
@@ -679,12 +694,10 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
       const u32 w = __ldg(rec), beg = __ldg(rec + 1), end = __ldg(rec + 2);
       const u64 base = ((u64)q2s * n + w) * wpv + lane_off;
       u64 vis[PER];
+      load_vis<PER>(p.vis + base, lane_on, vis);
       bool full = true;
 #pragma unroll
-      for (int k = 0; k < PER; k++) {
-        vis[k] = lane_on ? __ldcg(p.vis + base + k) : ~0ull;
-        full &= vis[k] == ~0ull;
-      }
+      for (int k = 0; k < PER; k++) full &= vis[k] == ~0ull;
       if (__all_sync(FULL_MASK, full)) continue;
       u64 acc[PER];
 #pragma unroll
