@@ -592,20 +592,34 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
   u64 edges = 0, words = 0, bytes = 0;
   Appender app;
 
-  for (u64 b64 = warp * VPW; b64 < n; b64 += n_warps * VPW) {
-    const u64 w64 = b64 + sg;
-    const bool wv = w64 < n;
-    const u32 w = wv ? (u32)w64 : 0;
+  // A warp takes 32 consecutive vertices at a time: lane i first finds, with
+  // coalesced reads of the in-row offsets, the target states into which
+  // vertex c0 + i has a light in-row on an active transition; only those
+  // (vertex, state) pairs are then visited, VPW vertices at a time (their
+  // offsets are in L1 by then).
+  for (u64 c0 = warp * 32; c0 < n; c0 += n_warps * 32) {
+    u32 qmask = 0;
+    if (c0 + lane < n) {
+      const u32 v = (u32)(c0 + lane);
+      for (u32 q2 = 0; q2 < Q; q2++)
+        for (u32 j = p.q.in_begin[q2]; j < p.q.in_begin[q2 + 1]; j++) {
+          const u32 l = p.q.in_label[j];
+          if (!(p.q.in_from[j] & active) || l >= p.L) continue;
+          const u32 *off = p.in_off + (u64)l * n1 + v;
+          const u32 len = __ldg(off + 1) - __ldg(off);
+          if (len > 0 && (len < HEAVY_ROW || !chunked)) qmask |= 1u << q2;
+        }
+    }
+    const u32 M = __ballot_sync(FULL_MASK, qmask != 0);
+    for (u32 s0 = 0; s0 < 32 && (M >> s0); s0 += VPW) {
+      if (VPW < 32 && ((M >> s0) & ((1u << VPW) - 1u)) == 0) continue;
+      const u32 s = s0 + sg;
+      const u32 vq = __shfl_sync(FULL_MASK, qmask, s);
+      const bool wv = vq != 0;
+      const u32 w = wv ? (u32)(c0 + s) : 0;
     for (u32 q2 = 0; q2 < Q; q2++) {
       const u32 gb = p.q.in_begin[q2], ge = p.q.in_begin[q2 + 1];
-      bool any = false;
-      for (u32 j = gb; j < ge && !any && wv; j++) {
-        const u32 l = p.q.in_label[j];
-        if (!(p.q.in_from[j] & active) || l >= p.L) continue;
-        const u32 *off = p.in_off + (u64)l * n1 + w;
-        const u32 len = __ldg(off + 1) - __ldg(off);
-        any = len > 0 && (len < HEAVY_ROW || !chunked);
-      }
+      bool any = wv && ((vq >> q2) & 1u);
       if (bits) {
         // sparse frontier: a vertex none of whose in-neighbours is in it is
         // skipped before its visited words are read (the sub-warp's lanes
@@ -662,6 +676,7 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
         bytes += (li == 0) ? gword : 0;
       }
       pull_finish<NW, PER>(p, app, FB, nlist, nxt, q2, w, stamp, li, lane_on && work, my_g, vis, acc);
+    }
     }
   }
 
