@@ -528,11 +528,14 @@ __device__ __forceinline__ u32 gather_row(const BfsParams &p, const u64 *F, cons
 }
 
 // Bottom-up target (q2, w), all groups: new lanes = acc & ~VIS go to the next
-// frontier word (atomically: chunks of long rows of the same vertex may run
-// concurrently); one lane per group claims the list entry.
+// frontier word, and one lane per group appends the list entry.  When chunks
+// of long in-rows of the same vertex may also produce (q2, w) in this level
+// (shared), the word is or-ed atomically and the entry is claimed (the first
+// producer appends); otherwise this sub-warp is the only producer, the word
+// was zero, and no atomic result has to be waited for.
 template <int NW, int PER>
 __device__ __forceinline__ void pull_finish(const BfsParams &p, Appender &app, u64 *FB, u64 *nlist, u32 nxt, u32 q2,
-                                            u32 w, u32 stamp, u32 lane, bool lane_on, u32 my_g,
+                                            u32 w, u32 stamp, u32 lane, bool lane_on, u32 my_g, bool shared,
                                             const u64 (&vis)[PER], const u64 (&acc)[PER]) {
   const u64 base = ((u64)q2 * p.n + w) * p.G * NW + (u64)lane * PER;
   bool take = false;
@@ -544,17 +547,29 @@ __device__ __forceinline__ void pull_finish(const BfsParams &p, Appender &app, u
     nz |= nw[k] != 0;
   }
   if constexpr (NW == 1) {
-    if (nz) take = atomicOr((unsigned long long *)(FB + base), nw[0]) == 0;
+    if (nz) {
+      if (shared) {
+        take = atomicOr((unsigned long long *)(FB + base), nw[0]) == 0;
+      } else {
+        FB[base] = nw[0];
+        take = true;
+      }
+    }
   } else {
 #pragma unroll
     for (int k = 0; k < PER; k++)
-      if (nw[k]) atomicOr((unsigned long long *)(FB + base + k), nw[k]);
+      if (nw[k]) {
+        if (shared)
+          atomicOr((unsigned long long *)(FB + base + k), nw[k]);
+        else
+          FB[base + k] = nw[k];
+      }
     // NW / PER lanes hold one group's word
     bool gnz = nz;
 #pragma unroll
     for (int o = 1; o < NW / PER; o <<= 1) gnz |= __shfl_xor_sync(FULL_MASK, gnz, o);
     if (gnz && lane_on && (lane % (NW / PER)) == 0)
-      take = atomicMax(p.claim + (((u64)q2 * p.n + w) * p.G + my_g), stamp) < stamp;
+      take = !shared || atomicMax(p.claim + (((u64)q2 * p.n + w) * p.G + my_g), stamp) < stamp;
   }
   warp_append(p, app, take, ((u64)(my_g * p.Q + q2) << 32) | w, &p.ctl->n_list[nxt], nlist);
 }
@@ -598,7 +613,7 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
   // (vertex, state) pairs are then visited, VPW vertices at a time (their
   // offsets are in L1 by then).
   for (u64 c0 = warp * 32; c0 < n; c0 += n_warps * 32) {
-    u32 qmask = 0;
+    u32 qmask = 0, hmask = 0;  // hmask: states with a long in-row (its chunks also produce)
     if (c0 + lane < n) {
       const u32 v = (u32)(c0 + lane);
       for (u32 q2 = 0; q2 < Q; q2++)
@@ -608,6 +623,7 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
           const u32 *off = p.in_off + (u64)l * n1 + v;
           const u32 len = __ldg(off + 1) - __ldg(off);
           if (len > 0 && (len < HEAVY_ROW || !chunked)) qmask |= 1u << q2;
+          if (len >= HEAVY_ROW && chunked) hmask |= 1u << q2;
         }
     }
     const u32 M = __ballot_sync(FULL_MASK, qmask != 0);
@@ -615,6 +631,7 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
       if (VPW < 32 && ((M >> s0) & ((1u << VPW) - 1u)) == 0) continue;
       const u32 s = s0 + sg;
       const u32 vq = __shfl_sync(FULL_MASK, qmask, s);
+      const u32 vh = __shfl_sync(FULL_MASK, hmask, s);
       const bool wv = vq != 0;
       const u32 w = wv ? (u32)(c0 + s) : 0;
     for (u32 q2 = 0; q2 < Q; q2++) {
@@ -675,7 +692,8 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
         words += (li == 0);
         bytes += (li == 0) ? gword : 0;
       }
-      pull_finish<NW, PER>(p, app, FB, nlist, nxt, q2, w, stamp, li, lane_on && work, my_g, vis, acc);
+      pull_finish<NW, PER>(p, app, FB, nlist, nxt, q2, w, stamp, li, lane_on && work, my_g, ((vh >> q2) & 1u) != 0,
+                           vis, acc);
     }
     }
   }
@@ -733,7 +751,7 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
       edges += (lane == 0) ? ex_all : 0;
       bytes += (lane == 0) ? 12 + gword + ex_all * (4 + (bits ? 4 * __popc(from) : 0)) + gat_all * gword : 0;
       words += (lane == 0);
-      pull_finish<NW, PER>(p, app, FB, nlist, nxt, q2s, w, stamp, li, lane_on && sg == 0, my_g, vis, acc);
+      pull_finish<NW, PER>(p, app, FB, nlist, nxt, q2s, w, stamp, li, lane_on && sg == 0, my_g, true, vis, acc);
     }
   }
   append_close(p, app, nlist);
