@@ -855,7 +855,7 @@ __device__ double pull_bytes(const BfsParams &p, u32 active) {
 }
 
 template <int NW, bool MULTI>
-__global__ void __launch_bounds__(BFS_THREADS, 5) msbfs_kernel(const __grid_constant__ BfsParams p) {
+__global__ void __launch_bounds__(BFS_THREADS, 4) msbfs_kernel(const __grid_constant__ BfsParams p) {
   // per-warp statistics, summed into the control block at the end
   u64 stat[ST_COUNT];
 #pragma unroll
