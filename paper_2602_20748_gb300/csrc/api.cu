@@ -328,7 +328,7 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_err(ctx, e, "source filter");
     if (rb) std::memcpy(flag.data(), ctx->rb_host, srcs_in.size());
-    res->stats.launches += 1;
+    res->stats.launches += rb ? 2 : 1;
     kept.reserve(srcs_in.size());
     uint64_t skipped = 0;
     for (size_t i = 0; i < srcs_in.size(); i++) {
@@ -533,6 +533,7 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
     u64 hsmall[3];
     CK(rb_queue(ctx, 0, ctx->ctl, sizeof(BfsCtl)));
     CK(rb_queue(ctx, RB_SMALL, ctx->small, 3 * 8));
+    res->stats.launches += 2;
     CK(cudaStreamSynchronize(ctx->stream));
     std::memcpy(&hctl, ctx->rb_host, sizeof(BfsCtl));
     std::memcpy(hsmall, ctx->rb_host + RB_SMALL, 3 * 8);
@@ -589,11 +590,11 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
       CK(launch_emit(nw, true, false, ep, ctx->stream));
       CK(launch_gather_lane_off(off, segs, n_lanes, ctx->small + 2, c.lane_off, ctx->stream));
       CK(cudaMemcpyAsync(c.lanesrc, w.lanesrc, n_lanes * 4, cudaMemcpyDeviceToDevice, ctx->stream));
-      // digest of the written rows, thread per row
+      // digest of the written rows (a block per source lane)
       CK(launch_row_digest(w.lanesrc, c.lane_off, n_lanes, c.dst, ctx->small, ctx->stream));
-      res->stats.launches += 3;
       res->chunks.push_back(c);
       CK(rb_queue(ctx, RB_SMALL, ctx->small, 16));
+      res->stats.launches += 4;
     }
     CK(cudaEventRecord(ctx->ev[3], ctx->stream));
     dfree(ctx, cnt, ncnt);

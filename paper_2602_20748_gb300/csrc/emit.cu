@@ -386,8 +386,9 @@ cudaError_t launch_emit_lane_stats(int nw, const EmitParams &p, unsigned long lo
 }
 
 // Second pass that writes interleaved (src, dst) rows straight into a
-// caller's buffer (used by the entry point that allocates nothing): same walk
-// as emit_kernel's write pass, row k at out[2k], out[2k + 1].
+// caller's buffer (used by the entry point that allocates nothing, at most 64
+// start vertices): tile by tile, the warp transpose gives each lane its
+// members in vertex order; row k goes to out[2k], out[2k + 1].
 template <int NW>
 __global__ void emit_pairs_kernel(const EmitParams p, u32 *__restrict__ out) {
   const u32 seg = blockIdx.x, g = blockIdx.y;
