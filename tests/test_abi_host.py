@@ -119,3 +119,22 @@ def test_options_round_trip(hctx):
     with pytest.raises(rpq.RPQError):
         rpq.rpq_get_option(hctx, "no_such_option")
     rpq.rpq_set_option(hctx, "alpha", 16)
+
+
+def test_stream_open_multi_argument_checks(hctx):
+    """rpq_stream_open_multi validates its arguments before touching the graph
+    or the device: no queries or a null query is INVALID_ARG, a host-only
+    context is NO_DEVICE (the graph handle is never read on these paths)."""
+    import ctypes
+
+    q = rpq.compile_rpq(hctx, "a*")
+    out = ctypes.c_void_p()
+    fake_graph = ctypes.c_void_p(1)  # never dereferenced on the paths below
+    one = (ctypes.c_void_p * 1)(q.h)
+    none = (ctypes.c_void_p * 1)(None)
+    f = rpq._lib.rpq_stream_open_multi
+    assert f(hctx.h, None, one, 1, 0, 0, 0, ctypes.byref(out)) == rpq.RPQ_ERR_INVALID_ARG
+    assert f(hctx.h, fake_graph, one, 0, 0, 0, 0, ctypes.byref(out)) == rpq.RPQ_ERR_INVALID_ARG
+    assert f(hctx.h, fake_graph, none, 1, 0, 0, 0, ctypes.byref(out)) == rpq.RPQ_ERR_INVALID_ARG
+    assert f(hctx.h, fake_graph, one, 1, 0, 0, 0, ctypes.byref(out)) == rpq.RPQ_ERR_NO_DEVICE
+    assert out.value is None
