@@ -272,10 +272,13 @@ cudaError_t launch_emit(int nw, bool write, bool digest, const EmitParams &p, cu
     return cudaGetLastError();
   }
   if (digest) return cudaErrorInvalidValue;  // the write pass does not fold the digest
-  // the NW = 4 write pass needs more than the default 48 KB: opt in once
-  static const cudaError_t attr_err = cudaFuncSetAttribute(
-      emit_write_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(emit_write_smem_words(4) * 4));
-  if (attr_err != cudaSuccess) return attr_err;
+  if (nw != 1) {
+    // the NW = 4 write pass needs more than the default 48 KB; the opt-in is
+    // per device, so it is repeated on every launch (an inexpensive call)
+    const cudaError_t e = cudaFuncSetAttribute(emit_write_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(emit_write_smem_words(4) * 4));
+    if (e != cudaSuccess) return e;
+  }
   if (nw == 1)
     emit_write_kernel<1><<<grid, threads, emit_write_smem_words(1) * 4, st>>>(p);
   else
