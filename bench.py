@@ -132,6 +132,7 @@ class ClockSampler:
 
 
 KERNEL_SOURCES = ("msbfs.cu", "rpq_internal.h", "device_common.cuh")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "msbfs_traffic_rmat18.json")
 
 
 def kernel_source_sha1() -> str:
@@ -144,43 +145,47 @@ def kernel_source_sha1() -> str:
     return h.hexdigest()
 
 
-def measured_traffic():
-    """DRAM bytes per traversal launch from the committed ncu summary
-    (profiles/msbfs_traffic.json), or None when the kernel's sources changed
-    since those counters were taken."""
-    path = os.path.join(ROOT, "profiles", "msbfs_traffic.json")
+def measured_traffic_ratio():
+    """DRAM bytes per algorithmic byte of the traversal kernel, from the
+    committed small-case ncu capture (R-MAT scale 18, the bench's launch
+    configuration): its DRAM read + write bytes per launch divided by the
+    same launches' algorithmic bytes (formula below).  None when the kernel's
+    sources changed since the counters were taken."""
     try:
-        with open(path) as f:
+        with open(TRAFFIC_FILE) as f:
             t = json.load(f)
     except (OSError, ValueError):
-        return None
-    return t.get("bytes_per_launch") if t.get("source_sha1") == kernel_source_sha1() else None
+        return None, None
+    if t.get("source_sha1") != kernel_source_sha1():
+        return None, t
+    return float(t["dram_bytes_per_alg_byte"]), t
 
 
-def algorithmic_bytes(st: dict) -> float:
-    """Bytes the traversal kernel must move for the work it did, counted by the
-    kernel itself (rpq_stats.alg_bytes): per top-down relaxation a 4-byte
-    column id and the target's visited word (8 * NW bytes); per adjacency row
-    its two offsets; per frontier entry the 8-byte entry and its frontier word;
-    per bottom-up (state, vertex) examined the visited words of all G groups;
-    per bottom-up in-edge a column id and the G frontier words of each active
-    source state; per new entry its entry, new frontier word and visited word
-    read and written; per old entry its entry and cleared frontier word."""
-    return float(st["alg_bytes"])
+def algorithmic_bytes_s8d(st: dict, nw: int) -> float:
+    """Algorithmic bytes of the bit-sliced traversal for the work one launch
+    did, counted per lane group (a group of 64 * nw start vertices shares one
+    visited word per product vertex): for every lane-group product vertex
+    (v, q) discovered, its label rows (two 4-byte offsets each, X_g rows), its
+    out-edges on those labels (a 4-byte column id and the target's visited
+    word of 8 * nw bytes each, W_g edges) and its list entry pushed and popped
+    (8 bytes, N_g entries): 4 W_g + 8 X_g + 8 nw W_g + 8 N_g.  These counts do
+    not depend on the kernel's direction choices or on how many bytes it
+    actually touches (that is alg_bytes, reported as touched)."""
+    return (4.0 + 8.0 * nw) * st["group_product_edges"] + 8.0 * st["group_label_rows"] + 8.0 * st["group_vertices"]
 
 
-def cpu_oracle_sample(n, src, dst, lab, seconds: float, batch0: int):
-    """Times the CPU oracle (as it stands) on start vertices of the workload,
-    in chunks of one source per host core, until `seconds` have passed."""
+def cpu_oracle_sample(n, src, dst, lab, seconds: float, batch0: int, threads: int = 0):
+    """Times the CPU oracle (as it stands) on random start vertices of the
+    workload, in chunks of one source per thread, until `seconds` have passed
+    (threads = 0: every host core)."""
     import oracle
 
     og = oracle.Graph(n, N_LABELS, src, dst, lab)
-    cores = os.cpu_count() or 1
+    cores = threads or os.cpu_count() or 1
     W = 0
     used = 0
     t_total = 0.0
     done = 0
-    per_query = []
     rng = np.random.Generator(np.random.PCG64(batch0))
     for regex in QUERIES:
         t_q = 0.0
@@ -193,9 +198,23 @@ def cpu_oracle_sample(n, src, dst, lab, seconds: float, batch0: int):
             W += r.W
             done += len(srcs)
             used = max(used, r.threads)
-        per_query.append(regex)
         t_total += t_q
     return W, t_total, used, done
+
+
+def workload_config(n: int, m_unique, batch: int, world: int) -> dict:
+    """The config object both arms print."""
+    return {"workload": WORKLOAD if n == 1 << SCALE else f"rmat{n.bit_length() - 1}-allpairs",
+            "queries": QUERIES, "vertices": n, "generated_edges": 16 * n, "distinct_edges": m_unique,
+            "labels": N_LABELS, "zipf_s": ZIPF_S, "batch_sources_per_step": batch,
+            "parallelism": f"sources/{world}",
+            "l2": "inputs larger than L2 (graph CSR ~200 MB, traversal state ~4.6 GB per launch)"}
+
+
+def distinct_edges(n: int, src, dst, lab) -> int:
+    """Distinct (src, dst, label) triples (what load_graph keeps)."""
+    key = (src.astype(np.uint64) * np.uint64(n) + dst.astype(np.uint64)) * np.uint64(N_LABELS) + lab.astype(np.uint64)
+    return int(np.unique(key).size)
 
 
 def reference_arm(args, rank: int, world: int):
@@ -217,8 +236,7 @@ def reference_arm(args, rank: int, world: int):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * ts / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "queries": QUERIES, "vertices": n, "generated_edges": N_EDGES,
-                   "labels": N_LABELS, "zipf_s": ZIPF_S},
+        "config": workload_config(n, distinct_edges(n, src, dst, lab), args.batch, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{srcs} random start vertices over the 4 queries, {ts:.1f} s of CPU oracle time"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -267,7 +285,11 @@ def ours(args, rank: int, world: int, local_rank: int):
             acc["bfs_ms"] += st["bfs_ms"]
             acc["bfs_launches"] += st["bfs_launches"]
             acc["launches"] += st["launches"]
-            acc["alg_bytes"] += algorithmic_bytes(st)
+            acc["alg_bytes"] += st["alg_bytes"]
+            acc["s8d_bytes"] += algorithmic_bytes_s8d(st, 4)
+            acc["gw"] += st["group_product_edges"]
+            acc["gx"] += st["group_label_rows"]
+            acc["gn"] += st["group_vertices"]
             acc["emit_ms"] += st["emit_ms"]
             for k in ("push_levels", "pull_levels", "levels"):
                 acc[k] += st[k]
@@ -275,7 +297,7 @@ def ours(args, rank: int, world: int, local_rank: int):
 
     def new_acc():
         return dict(W=0, pairs=0, bfs_ms=0.0, emit_ms=0.0, bfs_launches=0, launches=0, alg_bytes=0.0,
-                    push_levels=0, pull_levels=0, levels=0)
+                    s8d_bytes=0.0, gw=0, gx=0, gn=0, push_levels=0, pull_levels=0, levels=0)
 
     for i in range(args.warmup):
         run_step(i, new_acc())
@@ -343,31 +365,50 @@ def ours(args, rank: int, world: int, local_rank: int):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         Wc, tc, cores, k = cpu_oracle_sample(n, src, dst, lab, args.cpu_seconds, 7)
+        W1, t1, _, k1 = cpu_oracle_sample(n, src, dst, lab, max(2.0, args.cpu_seconds / 3), 8, threads=1)
         cpu = {"value": Wc / tc, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{k} random start vertices over the 4 queries ({tc:.1f} s of oracle time)"}
+               "sample": f"{k} random start vertices over the 4 queries ({tc:.1f} s of oracle time)",
+               "single_thread": {"value": W1 / t1, "unit": UNIT, "cores": 1,
+                                 "sample": f"{k1} random start vertices over the 4 queries ({t1:.1f} s)"}}
 
     peak, peak_kind = peaks()
-    achieved = acc["alg_bytes"] / max(1, acc["bfs_launches"]) / (acc["bfs_ms"] / max(1, acc["bfs_launches"]) / 1e3) / 1e9
-    traffic = measured_traffic()
+    L = max(1, acc["bfs_launches"])
+    ms_launch = acc["bfs_ms"] / L
+    s8d = acc["s8d_bytes"] / L
+    touched = acc["alg_bytes"] / L
+    achieved = s8d / (ms_launch / 1e3) / 1e9
+    touched_gbs = touched / (ms_launch / 1e3) / 1e9
+    ratio, tinfo = measured_traffic_ratio()
+    traffic = ratio * s8d if ratio is not None else None
+    roofline = {
+        "bound": "hbm", "kernel": "msbfs_kernel<4>", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+        "alg_bytes_per_launch": s8d,
+        "alg_formula": "4*W_g + 8*X_g + 8*NW*W_g + 8*N_g per launch (NW = 4 u64 per lane word; "
+                       "W_g, X_g, N_g = lane-group relaxations, label rows, product vertices)",
+        "W_g_per_launch": acc["gw"] / L, "X_g_per_launch": acc["gx"] / L, "N_g_per_launch": acc["gn"] / L,
+        "touched_bytes_per_launch": touched, "touched_gbs": touched_gbs, "touched_frac": touched_gbs / peak,
+        "dram_gbs": traffic / (ms_launch / 1e3) / 1e9 if traffic is not None else None,
+        "dram_frac": traffic / (ms_launch / 1e3) / 1e9 / peak if traffic is not None else None,
+        "traffic_source": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of msbfs_kernel<4> on R-MAT scale "
+                           f"{tinfo.get('scale')}, {tinfo.get('dram_bytes_per_alg_byte'):.3f} DRAM bytes per "
+                           f"algorithmic byte, scaled to this launch's algorithmic bytes"
+                           if ratio is not None else "stale or missing (kernel sources changed)"),
+        "bfs_ms": acc["bfs_ms"], "bfs_launches": acc["bfs_launches"], "ms_per_launch": ms_launch,
+        "emit_ms": acc["emit_ms"]}
     if rank == 0:
+        cfg = workload_config(n, m_unique, B, world)
+        cfg["graph_load_s"] = round(load_s, 3)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.scale == SCALE else f"rmat{args.scale}-allpairs",
-                       "queries": QUERIES, "vertices": n, "generated_edges": 16 * n,
-                       "distinct_edges": m_unique, "labels": N_LABELS, "zipf_s": ZIPF_S,
-                       "batch_sources_per_step": B, "parallelism": f"sources/{world}",
-                       "l2": "inputs larger than L2 (graph CSR ~200 MB, traversal state ~4.6 GB per launch)",
-                       "graph_load_s": round(load_s, 3)},
+            "config": cfg,
             "result_pairs_per_s": pairs_all / (ms_max / 1000.0),
             "result_pairs": pairs_all,
             "product_edges": W_all,
             "levels": {"push": acc["push_levels"], "pull": acc["pull_levels"]},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "kernel": "msbfs_kernel<4>",
-                         "peak_kind": peak_kind, "bfs_ms": acc["bfs_ms"], "bfs_launches": acc["bfs_launches"],
-                         "emit_ms": acc["emit_ms"]},
+            "roofline": roofline,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clocks,

@@ -237,9 +237,12 @@ int rpq_autotune_batch(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_queries, con
  * an allocation may imply, or code hosted inside another runtime that
  * forbids allocating on its device.  It evaluates the same RPQ as run_rpq for
  * 1 .. 64 start vertices, but every byte of scratch it uses lives in one
- * 64 MiB array that the library reserves on each device when it is loaded
- * and keeps until the process exits; the call itself calls no cudaMalloc,
- * cudaFree or other allocating routine.
+ * 64 MiB array per device that the library reserves when the first context on
+ * that device is created (rpq_create looks up the array's device address with
+ * cudaGetSymbolAddress, which loads it, and loads the kernels this call
+ * launches) and keeps until the process exits; the call itself calls no
+ * cudaMalloc, cudaFree or other allocating routine.  A context created after
+ * a cudaDeviceReset looks the address up again.
  *   sources    host array of n_sources start vertices (duplicates ignored).
  *   out_pairs  caller-owned DEVICE buffer of 2 * max_rows uint32 values; row
  *              k is written as (src, dst) at out_pairs[2k], out_pairs[2k+1],
@@ -249,13 +252,14 @@ int rpq_autotune_batch(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_queries, con
  * (plus a little per 1,024 vertices); larger ones are rejected with
  * OUT_OF_BUDGET and a message naming both sizes.  If the result has more than
  * max_rows rows, nothing is written, *n_rows holds the row count and the call
- * returns OUT_OF_BUDGET.  The first call on a device finds the array's device
- * address (cudaGetSymbolAddress) and must therefore come before any stream
- * capture on that device.  All calls share the array, and each keeps the
+ * returns OUT_OF_BUDGET.  All calls share the array, and each keeps the
  * previous call's contents until it clears what it needs: calls whose GPU
  * work overlaps (from several threads or streams on one device) race and
  * must be serialized by the caller.  The call waits for its work to finish.
- * Errors: INVALID_ARG, NO_DEVICE, OUT_OF_BUDGET, CUDA, TIMEOUT. */
+ * Errors: INVALID_ARG (NULL pointer, n_sources not in 1 .. 64, a source out of
+ * range), NO_DEVICE, OUT_OF_BUDGET, CUDA (a CUDA call failed, or the
+ * traversal's entry list overflowed -- an internal error), TIMEOUT (a
+ * traversal barrier wait ran out of time). */
 int run_rpq_static(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, const uint32_t *sources,
                    uint32_t n_sources, uint32_t *out_pairs, uint64_t max_rows, uint64_t *n_rows);
 
@@ -377,6 +381,12 @@ typedef struct {
                                 frontier words, list entries)                 */
   uint64_t evicted;          /* run_rpq_batch RPQ_PER_QUERY: queries that left
                                 the shared launch                            */
+  uint64_t group_product_edges; /* W_g: for every lane-group product vertex
+                                   (group, v, q) discovered, deg_l(v) summed
+                                   over the labels l leaving q -- the
+                                   relaxations one bit-sliced word serves    */
+  uint64_t group_label_rows;    /* X_g: adjacency rows (v, l) of those
+                                   product vertices (labels present)         */
 } rpq_stats;
 
 int result_stats(const rpq_result *r, rpq_stats *out);

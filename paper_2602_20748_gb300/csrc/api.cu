@@ -72,6 +72,7 @@ struct rpq_ctx {
   size_t pinned_bytes = 0;
   int live = 0;          // graphs and results not yet freed
   bool closing = false;  // rpq_destroy was called while handles were live
+  void *static_scratch = nullptr;  // device address of run_rpq_static's array
 };
 
 struct rpq_graph {
@@ -490,6 +491,8 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
       s.pull_edges += hctl.stats[ST_PULL_EDGES];
       s.pull_vertices += hctl.stats[ST_PULL_VERTICES];
       s.alg_bytes += hctl.stats[ST_ALG_BYTES];
+      s.group_product_edges += hctl.stats[ST_GROUP_W];
+      s.group_label_rows += hctl.stats[ST_GROUP_X];
       s.lane_groups += Gb;
       ctx->stamp += (uint32_t)hctl.levels + 3;
       float ms_bfs = 0, ms_emit = 0;
@@ -562,6 +565,8 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
     s.pull_edges += hctl.stats[ST_PULL_EDGES];
     s.pull_vertices += hctl.stats[ST_PULL_VERTICES];
     s.alg_bytes += hctl.stats[ST_ALG_BYTES];
+      s.group_product_edges += hctl.stats[ST_GROUP_W];
+      s.group_label_rows += hctl.stats[ST_GROUP_X];
     s.lane_groups += Gb;
     if (ctx->trace) {
       uint32_t nl = (uint32_t)std::min<uint64_t>(hctl.levels, TRACE_LEVELS);
@@ -709,6 +714,15 @@ int rpq_create(rpq_ctx **out, int device, uint64_t mem_budget_bytes, void *cuda_
     g_create_error = c->err;
     rpq_destroy(c);
     return RPQ_ERR_CUDA;
+  }
+  {
+    // run_rpq_static's array is reserved here, not at its first call
+    std::string msg;
+    if (static_scratch_prepare(&c->static_scratch, &msg) != RPQ_OK) {
+      g_create_error = msg;
+      rpq_destroy(c);
+      return RPQ_ERR_CUDA;
+    }
   }
   *out = c;
   return RPQ_OK;
@@ -1234,6 +1248,7 @@ bool ctx_cancelled(rpq_ctx *ctx) { return ctx->cancel.load(std::memory_order_rel
 void ctx_set_cancel(rpq_ctx *ctx, bool on) { ctx->cancel.store(on ? 1 : 0); }
 float ctx_alpha(rpq_ctx *ctx) { return ctx->alpha; }
 uint64_t ctx_time_limit_ns(rpq_ctx *ctx) { return ctx->time_limit_ns; }
+void *ctx_static_scratch(rpq_ctx *ctx) { return ctx->static_scratch; }
 const DevGraph &graph_dev(const rpq_graph *g) { return g->g; }
 const HostQuery &query_host(const rpq_query *q) { return q->hq; }
 
@@ -1261,6 +1276,8 @@ int rpq_rows_for_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, s
     stats->pull_edges += r.stats.pull_edges;
     stats->pull_vertices += r.stats.pull_vertices;
     stats->alg_bytes += r.stats.alg_bytes;
+    stats->group_product_edges += r.stats.group_product_edges;
+    stats->group_label_rows += r.stats.group_label_rows;
     stats->lane_groups += r.stats.lane_groups;
     stats->bfs_ms += r.stats.bfs_ms;
     stats->emit_ms += r.stats.emit_ms;
@@ -1305,6 +1322,8 @@ int rpq_lane_stats_for_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query
     stats->bfs_launches += r.stats.bfs_launches;
     stats->launches += r.stats.launches;
     stats->alg_bytes += r.stats.alg_bytes;
+    stats->group_product_edges += r.stats.group_product_edges;
+    stats->group_label_rows += r.stats.group_label_rows;
   }
   return rc;
 }
@@ -1505,6 +1524,8 @@ int rpq_lane_stats_multi(rpq_ctx *ctx, const rpq_graph *gr, const std::vector<Mu
     stats->push_levels += hctl.stats[ST_PUSH_LEVELS];
     stats->pull_levels += hctl.stats[ST_PULL_LEVELS];
     stats->alg_bytes += hctl.stats[ST_ALG_BYTES];
+    stats->group_product_edges += hctl.stats[ST_GROUP_W];
+    stats->group_label_rows += hctl.stats[ST_GROUP_X];
     stats->bfs_ms += ms_bfs;
     stats->emit_ms += ms_emit;
     stats->bfs_launches += 1;

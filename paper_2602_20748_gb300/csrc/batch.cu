@@ -869,6 +869,8 @@ int batch_run(rpq_ctx *ctx, const rpq_graph *g, uint32_t nq, const rpq_query *co
     a.bfs_launches += b.bfs_launches;
     a.launches += b.launches;
     a.alg_bytes += b.alg_bytes;
+    a.group_product_edges += b.group_product_edges;
+    a.group_label_rows += b.group_label_rows;
     out->regroup_launches += launches[h];
   }
   out->evicted += out->evicted_idx.size();

@@ -41,6 +41,10 @@ int ctx_pinned(rpq_ctx *ctx, int count, size_t bytes, void **out);
 bool ctx_cancelled(rpq_ctx *ctx);          // a server asked the request in service to stop
 void ctx_set_cancel(rpq_ctx *ctx, bool on);
 uint64_t ctx_time_limit_ns(rpq_ctx *ctx);
+// Device address of the static scratch array of run_rpq_static on the
+// context's device (looked up by rpq_create).
+void *ctx_static_scratch(rpq_ctx *ctx);
+int static_scratch_prepare(void **addr, std::string *msg);
 const DevGraph &graph_dev(const rpq_graph *g);
 const HostQuery &query_host(const rpq_query *q);
 int rpq_rows_for_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, std::vector<uint32_t> &srcs,

@@ -430,6 +430,13 @@ cudaError_t launch_emit_pairs(const EmitParams &p, uint32_t *out, cudaStream_t s
   return cudaGetLastError();
 }
 
+cudaError_t preload_static_emit_kernels() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, emit_count_kernel<1, false>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, emit_pairs_kernel<1>);
+  return e;
+}
+
 // lane_off[i] = off[i * segs] for every lane; lane_off[n_lanes] = total.
 __global__ void gather_lane_off(const u64 *__restrict__ off, u32 segs, u32 n_lanes, const u64 *__restrict__ total,
                                 u64 *__restrict__ lane_off) {

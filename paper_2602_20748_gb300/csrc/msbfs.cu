@@ -155,16 +155,19 @@ __device__ __forceinline__ const QueryDesc &gdesc(const BfsParams &p, u32 g) {
     return p.q;
 }
 
-// Out-degree of v summed over the labels leaving DFA state q.
-__device__ __forceinline__ u32 degsum(const BfsParams &p, const QueryDesc &qd, u32 q, u32 v) {
-  u32 s = 0;
+// Out-degree of v summed over the labels leaving DFA state q; *rows (if
+// given) gets the number of those labels present in the graph.
+__device__ __forceinline__ u32 degsum(const BfsParams &p, const QueryDesc &qd, u32 q, u32 v, u32 *rows = nullptr) {
+  u32 s = 0, r = 0;
   const u32 n1 = p.n + 1;
   for (u32 t = qd.out_begin[q]; t < qd.out_begin[q + 1]; t++) {
     u32 l = qd.out_label[t];
     if (l >= p.L) continue;
     const u32 *off = p.out_off + (u64)l * n1 + v;
     s += __ldg(off + 1) - __ldg(off);
+    r++;
   }
+  if (rows) *rows = r;
   return s;
 }
 
@@ -236,7 +239,7 @@ __device__ void seed_phase(const BfsParams &p, u64 *stat) {
   const u32 K = 64 * NW;
   const u64 total = (u64)p.G * K;
   const u64 stride = (u64)gridDim.x * blockDim.x;
-  u64 W = 0, N = 0, mf = 0;
+  u64 W = 0, N = 0, mf = 0, gx = 0, gn = 0;
   Appender app;
   for (u64 base = (u64)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
     u64 i = base + lane_id();
@@ -258,10 +261,15 @@ __device__ void seed_phase(const BfsParams &p, u64 *stat) {
           take = atomicMax(p.claim + ((u64)s * p.G + g), p.stamp_base + 1) < p.stamp_base + 1;
         entry = ((u64)g * p.Q << 32) | s;
         if (take && p.fbits) atomicOr(p.fbits + (s >> 5), 1u << (s & 31));  // state 0, bitmap 0
-        u32 d = degsum(p, gdesc<MULTI>(p, g), 0, s);
+        u32 rows = 0;
+        u32 d = degsum(p, gdesc<MULTI>(p, g), 0, s, &rows);
         W += d;
         N += 1;
-        if (take) mf += d;
+        if (take) {
+          mf += d;
+          gx += rows;
+          gn += 1;
+        }
       }
     }
     warp_append(p, app, take, entry, &p.ctl->n_list[0], p.list0);
@@ -270,10 +278,15 @@ __device__ void seed_phase(const BfsParams &p, u64 *stat) {
   W = warp_sum(W);
   N = warp_sum(N);
   mf = warp_sum(mf);
+  gx = warp_sum(gx);
+  gn = warp_sum(gn);
   if (lane_id() == 0) {
     stat[ST_W] += W;
     stat[ST_N] += N;
-    stat[ST_GROUP_VERTICES] += N;
+    stat[ST_GROUP_VERTICES] += gn;
+    // counted once per warp and phase: straight into the control block
+    if (mf) atomicAdd(&p.ctl->stats[ST_GROUP_W], mf);
+    if (gx) atomicAdd(&p.ctl->stats[ST_GROUP_X], gx);
     if (mf) atomicAdd(&p.ctl->mf[0], mf);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&p.ctl->smask[0], 1u);
@@ -775,7 +788,7 @@ __device__ void commit_phase(const BfsParams &p, int lp, u32 nxt, u64 n_cur, boo
   const u64 n_next = *(volatile unsigned long long *)&p.ctl->n_list[nxt];
   const u64 stride = (u64)gridDim.x * blockDim.x;
   const u64 tid = (u64)blockIdx.x * blockDim.x + threadIdx.x;
-  u64 W = 0, N = 0, mf = 0, gv = 0;
+  u64 W = 0, N = 0, mf = 0, gv = 0, gx = 0;
   u32 states = 0;
   for (u64 j = tid; j < n_next; j += stride) {
     u64 e = __ldcg(&nlist[j]);
@@ -793,10 +806,12 @@ __device__ void commit_phase(const BfsParams &p, int lp, u32 nxt, u64 n_cur, boo
       atomicOr(p.fbits + (lp ? 0 : p.fbits_words) + (bi >> 5), 1u << (bi & 31));
     }
     u32 c = popc_w(m);
-    u32 d = degsum(p, gdesc<MULTI>(p, g), q, w);
+    u32 rows = 0;
+    u32 d = degsum(p, gdesc<MULTI>(p, g), q, w, &rows);
     W += (u64)c * d;
     N += c;
     mf += d;
+    gx += rows;
     gv += 1;
     states |= 1u << q;
   }
@@ -820,6 +835,7 @@ __device__ void commit_phase(const BfsParams &p, int lp, u32 nxt, u64 n_cur, boo
   N = warp_sum(N);
   mf = warp_sum(mf);
   gv = warp_sum(gv);
+  gx = warp_sum(gx);
   states = __reduce_or_sync(FULL_MASK, states);
   // per new entry: the entry, its new frontier word, its visited word read and
   // written; per old entry: the entry and its frontier word cleared
@@ -828,6 +844,8 @@ __device__ void commit_phase(const BfsParams &p, int lp, u32 nxt, u64 n_cur, boo
     stat[ST_W] += W;
     stat[ST_N] += N;
     stat[ST_GROUP_VERTICES] += gv;
+    if (mf) atomicAdd(&p.ctl->stats[ST_GROUP_W], mf);
+    if (gx) atomicAdd(&p.ctl->stats[ST_GROUP_X], gx);
     if (mf) atomicAdd(&p.ctl->mf[nxt], mf);
     if (states) atomicOr(&p.ctl->smask[nxt], states);
   }
@@ -1005,6 +1023,13 @@ int msbfs_max_blocks(int nw, int threads, int *blocks_per_sm, int *sms) {
   else
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, msbfs_kernel<4, false>, threads, 0);
   return e == cudaSuccess ? 0 : -1;
+}
+
+cudaError_t preload_static_msbfs_kernels() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, msbfs_kernel<1, false>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, vis_init_kernel<1>);
+  return e;
 }
 
 cudaError_t launch_msbfs_multi(const BfsParams &p, int blocks, int threads, cudaStream_t st) {

@@ -88,6 +88,8 @@ enum StatIdx {
   ST_PULL_EDGES,     // in-edges read by bottom-up levels
   ST_PULL_VERTICES,  // (vertex, state) words examined bottom-up
   ST_ALG_BYTES,      // algorithmic bytes of the traversal (see the kernel)
+  ST_GROUP_W,        // W_g: out-degree over the state's labels, summed over lane-group product vertices
+  ST_GROUP_X,        // X_g: (label) adjacency rows of lane-group product vertices
   ST_COUNT
 };
 
@@ -213,6 +215,12 @@ cudaError_t launch_emit_lane_stats(int nw, const EmitParams &p, unsigned long lo
 
 // Write pass into interleaved (src, dst) rows of a caller's buffer (NW = 1).
 cudaError_t launch_emit_pairs(const EmitParams &p, uint32_t *out, cudaStream_t st);
+
+// Load (under the runtime's lazy module loading) the kernels the entry point
+// that allocates nothing launches, so that their first use allocates nothing.
+cudaError_t preload_static_msbfs_kernels();
+cudaError_t preload_static_emit_kernels();
+cudaError_t preload_scan_kernels();
 
 cudaError_t launch_gather_lane_off(const unsigned long long *off, uint32_t segs, uint32_t n_lanes,
                                    const unsigned long long *total, unsigned long long *lane_off, cudaStream_t st);

@@ -119,4 +119,13 @@ cudaError_t exclusive_scan_u64(const u64 *in, u64 *out, size_t n, u64 *total, u6
   return scan_impl<u64>(in, out, n, total, tmp, st);
 }
 
+cudaError_t preload_scan_kernels() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, scan_tile_sums<uint32_t>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, scan_tile_apply<uint32_t>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, scan_tile_sums<u64>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, scan_tile_apply<u64>);
+  return e;
+}
+
 }  // namespace rpq

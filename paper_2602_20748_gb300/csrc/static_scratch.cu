@@ -6,10 +6,17 @@
 // the device-wide synchronization an allocation can imply, or a plug-in that
 // runs inside another runtime which forbids allocating on its device.  For
 // them this file keeps the traversal's scratch memory in one file-scope
-// device array, reserved when the library is loaded, and runs the same
-// traversal and emission kernels as run_rpq (one lane group of up to 64 start
-// vertices) on it.  The caller passes the inputs (a loaded graph, a compiled
-// query, start vertices) and the output buffer.
+// device array and runs the same traversal and emission kernels as run_rpq
+// (one lane group of up to 64 start vertices) on it.  The caller passes the
+// inputs (a loaded graph, a compiled query, start vertices) and the output
+// buffer.
+//
+// The array belongs to this file's device module.  Under the runtime's lazy
+// module loading that module, and with it the array, is loaded the first time
+// the host asks for the array's address; rpq_create does that (with the
+// context's device current) and also loads the kernels this entry point
+// launches, so the array is reserved when the first context on a device is
+// created and a later call has nothing left to reserve.
 //
 // Every call shares the one array, so calls whose GPU work overlaps (other
 // threads, other streams of the same device) race with each other; callers
@@ -25,13 +32,8 @@ namespace rpq {
 namespace {
 
 constexpr size_t STATIC_SCRATCH_BYTES = 64ull << 20;  // 64 MiB per device
-constexpr int MAX_DEVICES = 64;
 
 static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
-
-// Device addresses of g_static_scratch, one per device, filled by the first
-// call on that device (cudaGetSymbolAddress with the device current).
-unsigned char *g_scratch_addr[MAX_DEVICES] = {nullptr};
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -52,6 +54,29 @@ static size_t static_scratch_need(uint32_t Q, uint32_t n, uint32_t segs) {
   return need;
 }
 
+// Set-up for one context, with its device current: the host-side name of the
+// array is not a device address, so the runtime is asked for the address
+// (which also loads the array's module); the kernels run_rpq_static launches
+// are loaded too.  Each context keeps its own copy of the address, so no
+// state is shared between threads, and a context created after a
+// cudaDeviceReset looks the address up afresh.
+int static_scratch_prepare(void **addr, std::string *msg) {
+  *addr = nullptr;
+  void *a = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&a, g_static_scratch);
+  if (e != cudaSuccess || !a) {
+    *msg = std::string("cudaGetSymbolAddress of the static scratch: ") + cudaGetErrorString(e);
+    return RPQ_ERR_CUDA;
+  }
+  if ((e = preload_static_msbfs_kernels()) != cudaSuccess || (e = preload_static_emit_kernels()) != cudaSuccess ||
+      (e = preload_scan_kernels()) != cudaSuccess) {
+    *msg = std::string("loading the kernels of run_rpq_static: ") + cudaGetErrorString(e);
+    return RPQ_ERR_CUDA;
+  }
+  *addr = a;
+  return RPQ_OK;
+}
+
 }  // namespace rpq
 
 using namespace rpq;
@@ -63,7 +88,6 @@ extern "C" int run_rpq_static(rpq_ctx *ctx, const rpq_graph *g, const rpq_query 
   *n_rows = 0;
   const int dev = ctx_device(ctx);
   if (dev < 0) return ctx_error(ctx, RPQ_ERR_NO_DEVICE, "host-only context has no GPU");
-  if (dev >= MAX_DEVICES) return ctx_error(ctx, RPQ_ERR_INVALID_ARG, "device index too large");
   if (n_sources == 0 || n_sources > 64)
     return ctx_error(ctx, RPQ_ERR_INVALID_ARG, "run_rpq_static takes 1 to 64 start vertices");
   const DevGraph &dg = graph_dev(g);
@@ -95,16 +119,9 @@ extern "C" int run_rpq_static(rpq_ctx *ctx, const rpq_graph *g, const rpq_query 
 
   cudaError_t e = cudaSetDevice(dev);
   if (e != cudaSuccess) return ctx_error(ctx, RPQ_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
-  if (!g_scratch_addr[dev]) {
-    // One-time set-up on this device: the host-side name of the array is not
-    // a device address; ask the runtime for the device address.
-    void *addr = nullptr;
-    e = cudaGetSymbolAddress(&addr, g_static_scratch);
-    if (e != cudaSuccess || !addr)
-      return ctx_error(ctx, RPQ_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_scratch_addr[dev] = (unsigned char *)addr;
-  }
-  unsigned char *base = g_scratch_addr[dev];
+  // the array's device address, found when the context was created
+  unsigned char *base = static_cast<unsigned char *>(ctx_static_scratch(ctx));
+  if (!base) return ctx_error(ctx, RPQ_ERR_CUDA, "the context has no static scratch address");
   size_t at = 0;
   auto take = [&](size_t bytes) {
     unsigned char *p = base + at;
@@ -197,6 +214,7 @@ extern "C" int run_rpq_static(rpq_ctx *ctx, const rpq_graph *g, const rpq_query 
   STATIC_CK(cudaMemcpyAsync(&err, &ctl->err, sizeof(err), cudaMemcpyDeviceToHost, st));
   STATIC_CK(cudaMemcpyAsync(&total, small + 2, sizeof(total), cudaMemcpyDeviceToHost, st));
   STATIC_CK(cudaStreamSynchronize(st));
+  if (err == ERR_LIST_OVERFLOW) return ctx_error(ctx, RPQ_ERR_CUDA, "internal: traversal entry list overflow");
   if (err) return ctx_error(ctx, RPQ_ERR_TIMEOUT, "traversal grid barrier wait ran out of time");
   *n_rows = total;
   if (total > max_rows)

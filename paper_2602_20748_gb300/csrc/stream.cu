@@ -237,6 +237,8 @@ void eval_thread(rpq_stream *s) {
       a.bfs_launches += st.bfs_launches;
       a.launches += st.launches;
       a.alg_bytes += st.alg_bytes;
+      a.group_product_edges += st.group_product_edges;
+      a.group_label_rows += st.group_label_rows;
       s->pending.push_back(b);
       s->cv.notify_all();
     }

@@ -65,7 +65,8 @@ class rpq_stats(ctypes.Structure):
         "product_edges", "product_vertices", "levels", "push_levels", "pull_levels", "group_edges", "group_rows",
         "group_vertices", "pull_edges", "pull_vertices", "lane_words", "lane_groups")] + [
         ("bfs_ms", ctypes.c_double), ("emit_ms", ctypes.c_double), ("bfs_launches", ctypes.c_uint64),
-        ("launches", ctypes.c_uint64), ("alg_bytes", ctypes.c_uint64), ("evicted", ctypes.c_uint64)]
+        ("launches", ctypes.c_uint64), ("alg_bytes", ctypes.c_uint64), ("evicted", ctypes.c_uint64),
+        ("group_product_edges", ctypes.c_uint64), ("group_label_rows", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
