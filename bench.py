@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--batch", type=int, default=4096, help="start vertices per step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="default workload: skip the compact batch (config 4) and CRPQ (config 3) sub-objects")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="allpairs", choices=["allpairs", "batch", "crpq", "serve"],
                     help="allpairs: the R-MAT 2^20 all-pairs line (default); batch: 4,096 single-source "
@@ -396,6 +398,16 @@ def ours(args, rank: int, world: int, local_rank: int):
                            if ratio is not None else "stale or missing (kernel sources changed)"),
         "bfs_ms": acc["bfs_ms"], "bfs_launches": acc["bfs_launches"], "ms_per_launch": ms_launch,
         "emit_ms": acc["emit_ms"]}
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_extra:
+        # configs 3 and 4 on the same record (compact: 2 steps each)
+        for q in qs:
+            q.free()
+        g.free()
+        ctx.close()
+        sub = argparse.Namespace(**{**vars(args), "steps": 2, "warmup": 1})
+        extra["batch"] = bench_batch(sub, compact=True)
+        extra["crpq"] = bench_crpq(sub, compact=True)
     if rank == 0:
         cfg = workload_config(n, m_unique, B, world)
         cfg["graph_load_s"] = round(load_s, 3)
@@ -413,6 +425,7 @@ def ours(args, rank: int, world: int, local_rank: int):
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": acc["launches"],
+            **extra,
         }
         print(json.dumps(out), flush=True)
     if dist:
@@ -420,28 +433,33 @@ def ours(args, rank: int, world: int, local_rank: int):
     return 0
 
 
-def bench_batch(args):
+def bench_batch(args, compact: bool = False):
     """4,096 single-source RPQs (1-6 Zipf symbols, 0-2 stars, 1/4 alternation
     pairs, sources proportional to out-degree) on R-MAT 2^22 / 2^26 edges /
     8 labels Zipf(1.2): one run_rpq_batch call (RPQ_PER_QUERY: each query's
-    own row count and digest) per step, against run_rpq one query per launch
-    (count only) on the first 512 queries; every one of those 512 replies must
-    agree exactly."""
+    own row count and digest) per step, after rpq_autotune_batch, against the
+    plain path -- run_rpq, one query per launch (count only) -- over all 4,096
+    queries; every reply must agree exactly.  Latency of a batched query: from
+    the start of its run_rpq_batch call until its summary is known
+    (result_query_time); of a plain query: its run_rpq call."""
     import torch
     from paper_2602_20748_gb300 import rpq, synth
 
     n = 1 << 22
+    t_gen = time.perf_counter()
     src, dst, lab = synth.rmat_graph(22, 1 << 26, 8, 1.2, seed=synth.BASE_SEED + 4)
     regexes, sources = synth.batch_queries(4096, 8, 1.2, src, n, seed=synth.BASE_SEED + 4)
+    gen_s = time.perf_counter() - t_gen
+    nq = len(regexes)
     ctx = rpq.Context(device=0)
-    rpq.rpq_set_option(ctx, "batch_multi", args.batch_multi)
     g = rpq.load_graph(ctx, n, 8, src, dst, lab)
+    del src, dst, lab
     qs = [rpq.compile_rpq(ctx, r) for r in regexes]
     t0 = time.perf_counter()
     threads, per_launch = rpq.rpq_autotune_batch(ctx, g, qs, sources)
     tune_s = time.perf_counter() - t0
-    evict_at = rpq.rpq_get_option(ctx, "batch_evict")
-    streams = rpq.rpq_get_option(ctx, "batch_streams")
+    tuned = {k: rpq.rpq_get_option(ctx, k) for k in ("batch_direct", "batch_hash", "batch_evict", "batch_lanes",
+                                                     "batch_threads", "batch_streams")}
     for _ in range(args.warmup):
         rpq.run_rpq_batch(ctx, g, qs, sources, flags=rpq.RPQ_PER_QUERY).free()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -464,56 +482,74 @@ def bench_batch(args):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
-    batched = [rpq.result_query_stats(r, i) for i in range(512)]
+    batched = [rpq.result_query_stats(r, i) for i in range(nq)]
+    b_lat = [rpq.result_query_time(r, i) for i in range(nq)]
     r.free()
     # plain path: one run_rpq launch per query, timed per query
-    k = 512
     lat = []
     agree = 0
-    for i in range(k):
+    plain_launches = 0
+    for i in range(nq):
         t1 = time.perf_counter()
         one = rpq.run_rpq(ctx, g, qs[i], [sources[i]], flags=rpq.RPQ_COUNT_ONLY)
         c, _, hs, hx = rpq.result_info(one)
-        lat.append(time.perf_counter() - t1)
+        lat.append(1000.0 * (time.perf_counter() - t1))
+        plain_launches += rpq.result_stats(one)["launches"]
         one.free()
         agree += (c, hs, hx) == batched[i]
-    plain_qps = k / sum(lat)
-    qps = 4096 / (ms / 1000.0)
+    plain_qps = nq / (sum(lat) / 1000.0)
+    qps = nq / (ms / 1000.0)
+    for q in qs:
+        q.free()
+    g.free()
+    ctx.close()
+    body = {
+        "queries_per_s": qps, "plain_queries_per_s": plain_qps, "speedup_vs_plain": qps / plain_qps,
+        "batch_ms": ms, "equal_results": {"compared": nq, "agree": int(agree)},
+        "batched_latency_ms": {"p50": float(np.percentile(b_lat, 50)), "p99": float(np.percentile(b_lat, 99))},
+        "plain_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "product_edges_per_s": W / (ms * args.steps / 1000.0), "rows_per_step": rows // args.steps,
+        "evicted_per_step": evicted // max(1, args.steps), "gpu_launches_per_step": launches // max(1, args.steps),
+        "plain_gpu_launches": plain_launches,
+        "autotuned": {**tuned, "threads": threads, "queries_per_launch": per_launch, "autotune_s": round(tune_s, 2)},
+        "config": {"workload": "rmat22-batched-single-source", "queries": nq, "vertices": n,
+                   "generated_edges": 1 << 26, "labels": 8, "zipf_s": 1.2, "mode": "per-query count + digest",
+                   "generation_s": round(gen_s, 1)},
+    }
+    if compact:
+        return body
     out = {
         "metric": "queries_per_s", "value": qps, "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "rmat22-batched-single-source", "queries": 4096, "vertices": n,
-                   "generated_edges": 1 << 26, "labels": 8, "zipf_s": 1.2, "mode": "per-query count + digest",
-                   "autotuned_threads": threads, "autotuned_queries_per_launch": per_launch,
-                   "autotuned_evict_at": evict_at, "autotuned_streams": streams, "autotune_s": round(tune_s, 3),
-                   "multi_automaton_launches": bool(args.batch_multi)},
-        "evicted_per_step": evicted // max(1, args.steps),
-        "batched_latency_ms": ms, "product_edges_per_s": W / (ms * args.steps / 1000.0),
-        "rows_per_step": rows // args.steps,
-        "plain": {"queries_per_s": plain_qps, "p50_ms": 1000 * float(np.percentile(lat, 50)),
-                  "p99_ms": 1000 * float(np.percentile(lat, 99)), "queries_timed": k},
-        "speedup_vs_plain": qps / plain_qps, "equal_results": {"compared": k, "agree": int(agree)},
+        "dtype": "u32", "data": "synthetic", "config": body.pop("config"), **body,
         "clocks": clocks, "gpu_launches": launches,
     }
     print(json.dumps(out), flush=True)
     return 0
 
 
-def bench_crpq(args):
+def bench_crpq(args, compact: bool = False):
     """3-atom triangle CRPQ x -a-> y, x -b.c*-> z, y -d*-> z on R-MAT 2^22 /
     2^26 edges / 10 labels Zipf(1.1) / 5 vertex labels, count only, over one
-    batch of x values per step."""
+    batch of --batch x values (a random permutation of the vertices) per step.
+    The full query (all 2^22 x values) has about 10^13 tuples, beyond any
+    count-by-enumeration within a bench, so the rate is measured on these
+    batches.  Per-atom time: each atom evaluated alone over the step's
+    bindings (its RPQ from the batch's distinct x / y values)."""
     import torch
     from paper_2602_20748_gb300 import rpq, synth
 
     n = 1 << 22
+    t_gen = time.perf_counter()
     src, dst, lab = synth.rmat_graph(22, 1 << 26, 10, 1.1, seed=synth.BASE_SEED + 2)
     vl = synth.vertex_labels(n, 5, seed=synth.BASE_SEED + 2)
+    gen_s = time.perf_counter() - t_gen
     ctx = rpq.Context(device=0)
     g = rpq.load_graph(ctx, n, 10, src, dst, lab, vl)
-    atoms = [(0, rpq.compile_rpq(ctx, "a"), 1), (0, rpq.compile_rpq(ctx, "b·c*"), 2), (1, rpq.compile_rpq(ctx, "d*"), 2)]
-    B = args.batch
+    del src, dst, lab
+    qa, qbc, qd = rpq.compile_rpq(ctx, "a"), rpq.compile_rpq(ctx, "b·c*"), rpq.compile_rpq(ctx, "d*")
+    atoms = [(0, qa, 1), (0, qbc, 2), (1, qd, 2)]
+    B = min(args.batch, 1024) if compact else args.batch
     rng = np.random.Generator(np.random.PCG64(11))
     perm = rng.permutation(n).astype(np.uint32)
     for i in range(args.warmup):
@@ -531,14 +567,41 @@ def bench_crpq(args):
     ev1.record()
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / args.steps
-    out = {
-        "metric": "crpq_tuples_per_s", "value": tuples / (ms * args.steps / 1000.0), "unit": "tuples/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "rmat22-triangle-crpq", "atoms": ["x -a-> y", "x -b.c*-> z", "y -d*-> z"],
-                   "x_per_step": B, "vertices": n, "generated_edges": 1 << 26, "labels": 10, "zipf_s": 1.1,
-                   "vertex_labels": 5, "mode": "count only"},
+    # per-atom time on the last step's bindings: a from x, b.c* from x, d* from the y's a reaches
+    x = np.sort(perm[(args.warmup + args.steps - 1) * B:(args.warmup + args.steps) * B])
+    per_atom = {}
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    ra = rpq.run_rpq(ctx, g, qa, x, flags=rpq.RPQ_MATERIALIZE)
+    torch.cuda.synchronize()
+    per_atom["x -a-> y"] = 1000.0 * (time.perf_counter() - t1)
+    ys = np.unique(rpq.fetch_pairs(ra)[:, 1])
+    ra.free()
+    for name, q, s_ in (("x -b.c*-> z", qbc, x), ("y -d*-> z", qd, ys)):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        rpq.run_rpq(ctx, g, q, s_, flags=rpq.RPQ_COUNT_ONLY).free()
+        torch.cuda.synchronize()
+        per_atom[name] = 1000.0 * (time.perf_counter() - t1)
+    for q in (qa, qbc, qd):
+        q.free()
+    g.free()
+    ctx.close()
+    body = {
+        "tuples_per_s": tuples / (ms * args.steps / 1000.0), "ms_per_step": ms, "x_per_step": B,
         "tuples_per_step": tuples // args.steps, "atom_product_edges_per_step": W // args.steps,
+        "per_atom_ms": per_atom,
+        "config": {"workload": "rmat22-triangle-crpq", "atoms": ["x -a-> y", "x -b.c*-> z", "y -d*-> z"],
+                   "vertices": n, "generated_edges": 1 << 26, "labels": 10, "zipf_s": 1.1, "vertex_labels": 5,
+                   "mode": "count only", "generation_s": round(gen_s, 1)},
+    }
+    if compact:
+        return body
+    out = {
+        "metric": "crpq_tuples_per_s", "value": body["tuples_per_s"], "unit": "tuples/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": body.pop("config"),
+        **body,
     }
     print(json.dumps(out), flush=True)
     return 0

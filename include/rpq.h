@@ -390,6 +390,11 @@ typedef struct {
 } rpq_stats;
 
 int result_stats(const rpq_result *r, rpq_stats *out);
+/* For a run_rpq_batch result made with RPQ_PER_QUERY: milliseconds from the
+ * start of the call until query i's summary was known on the host (queries
+ * that finish in the shared launch are known before those evaluated later in
+ * lane-mode launches).  INVALID_ARG otherwise or when i is out of range. */
+int result_query_time(const rpq_result *r, uint32_t i, double *ms);
 /* Row count and digest of query i of a run_rpq_batch result made with
  * RPQ_PER_QUERY (INVALID_ARG otherwise or when i is out of range). */
 int result_query_stats(const rpq_result *r, uint32_t i, uint64_t *count, uint64_t *digest_sum, uint64_t *digest_xor);

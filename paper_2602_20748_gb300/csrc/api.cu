@@ -55,6 +55,7 @@ struct rpq_ctx {
   int sms = 0;
   int bpsm[2] = {0, 0};  // resident traversal blocks per SM for NW = 1, 4
   int bpsm_multi = 0;    // the same for the per-group-automata kernel (set on first use)
+  int bpsm_lane[2] = {0, 0};  // and for the per-lane-automata kernel, NW = 1, 4 (set on first use)
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   float alpha = 16.0f;
   uint64_t time_limit_ns = 20ull * 1000 * 1000 * 1000;
@@ -109,6 +110,7 @@ struct rpq_result {
   uint64_t tuple_bytes = 0;
   rpq_stats stats;
   std::vector<uint64_t> qstats;  // run_rpq_batch with RPQ_PER_QUERY: 3 values per query
+  std::vector<double> qdone_ms;  // and when each query's summary was known (ms from the call's start)
 };
 
 namespace {
@@ -793,6 +795,12 @@ int rpq_set_option(rpq_ctx *ctx, const char *name, double value) {
     ctx->batch.multi = value != 0;
   } else if (n == "batch_streams" && value >= 1 && value <= 16) {
     ctx->batch.streams = (uint32_t)value;
+  } else if (n == "batch_lanes" && value >= 0 && value <= 4096) {
+    ctx->batch.lanes = (uint32_t)value;
+  } else if (n == "batch_direct" && (value == 0 || value == 1)) {
+    ctx->batch.direct = value != 0;
+  } else if (n == "batch_hash" && (value == 0 || value == 1)) {
+    ctx->batch.hash = value != 0;
   } else {
     return set_err(ctx, RPQ_ERR_INVALID_ARG, "unknown option or value out of range: " + n);
   }
@@ -820,6 +828,12 @@ int rpq_get_option(const rpq_ctx *ctx, const char *name, double *value) {
     *value = ctx->batch.multi ? 1 : 0;
   else if (n == "batch_streams")
     *value = ctx->batch.streams;
+  else if (n == "batch_lanes")
+    *value = ctx->batch.lanes;
+  else if (n == "batch_direct")
+    *value = ctx->batch.direct ? 1 : 0;
+  else if (n == "batch_hash")
+    *value = ctx->batch.hash ? 1 : 0;
   else
     return RPQ_ERR_INVALID_ARG;
   return RPQ_OK;
@@ -1062,7 +1076,10 @@ int run_rpq_batch(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_queries, const rp
   }
   bo.stats.lane_words = 0;
   rc = make_tuple_result(ctx, 2, tuples, bo.count, bo.dsum, bo.dxor, materialize, bo.stats, out);
-  if (rc == RPQ_OK && per_query) (*out)->qstats.swap(bo.qstats);
+  if (rc == RPQ_OK && per_query) {
+    (*out)->qstats.swap(bo.qstats);
+    (*out)->qdone_ms.swap(bo.qdone_ms);
+  }
   return rc;
 }
 
@@ -1075,31 +1092,43 @@ int rpq_autotune_batch(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_queries, con
   const uint32_t sample = std::min<uint32_t>(n_queries, 1024);
   BatchTuning best = ctx->batch;
   double best_s = -1;
-  const int threads[] = {256, 512};
-  // (never evicting is not a candidate: a sample that keeps its heavy queries
-  // in the shared launch says little about a full batch that would not)
-  const uint64_t evicts[] = {1ull << 12, 1ull << 14, 1ull << 16, 1ull << 18};
-  const uint32_t streams[] = {4, 8};
-  for (int t : threads)
-    for (uint64_t ev : evicts)
-      for (uint32_t ns : streams) {
-        BatchTuning cand = ctx->batch;
-        cand.threads = t;
-        cand.evict_at = ev;
-        cand.streams = ns;
-        BatchOut bo;
-        bo.per_query = true;
-        cudaStreamSynchronize(ctx->stream);
-        auto t0 = std::chrono::steady_clock::now();
-        int rc = sample ? batch_run(ctx, g, sample, queries, sources, false, cand, &bo) : RPQ_OK;
-        cudaStreamSynchronize(ctx->stream);
-        double s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        if (rc) return rc;
-        if (best_s < 0 || s < best_s) {
-          best_s = s;
-          best = cand;
-        }
+  // Candidates: every query straight to lane-mode launches, or a shared
+  // per-query launch first (visited set: dense bitmaps or hash tables; block
+  // size; eviction threshold) with the evicted queries in lane-mode launches.
+  // (Never evicting is not a candidate: a sample that keeps its heavy queries
+  // in the shared launch says little about a full batch that would not.)
+  std::vector<BatchTuning> cands;
+  {
+    BatchTuning c = ctx->batch;
+    c.direct = true;
+    if (c.lanes == 0) c.lanes = 4096;
+    cands.push_back(c);
+  }
+  for (int hash = 0; hash < 2; hash++)
+    for (int t : {256, 512})
+      for (uint64_t ev : {1ull << 10, 1ull << 12, 1ull << 14}) {
+        BatchTuning c = ctx->batch;
+        c.direct = false;
+        if (c.lanes == 0) c.lanes = 4096;
+        c.hash = hash != 0;
+        c.threads = t;
+        c.evict_at = ev;
+        cands.push_back(c);
       }
+  for (const BatchTuning &cand : cands) {
+    BatchOut bo;
+    bo.per_query = true;
+    cudaStreamSynchronize(ctx->stream);
+    auto t0 = std::chrono::steady_clock::now();
+    int rc = sample ? batch_run(ctx, g, sample, queries, sources, false, cand, &bo) : RPQ_OK;
+    cudaStreamSynchronize(ctx->stream);
+    double s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (rc) return rc;
+    if (best_s < 0 || s < best_s) {
+      best_s = s;
+      best = cand;
+    }
+  }
   ctx->batch = best;
   if (threads_out) *threads_out = (uint32_t)best.threads;
   if (queries_per_launch_out) *queries_per_launch_out = best.queries_per_launch;
@@ -1120,6 +1149,12 @@ int result_query_stats(const rpq_result *r, uint32_t i, uint64_t *count, uint64_
   if (count) *count = r->qstats[3ull * i];
   if (digest_sum) *digest_sum = r->qstats[3ull * i + 1];
   if (digest_xor) *digest_xor = r->qstats[3ull * i + 2];
+  return RPQ_OK;
+}
+
+int result_query_time(const rpq_result *r, uint32_t i, double *ms) {
+  if (!r || !ms || i >= r->qdone_ms.size()) return RPQ_ERR_INVALID_ARG;
+  *ms = r->qdone_ms[i];
   return RPQ_OK;
 }
 
@@ -1249,6 +1284,11 @@ void ctx_set_cancel(rpq_ctx *ctx, bool on) { ctx->cancel.store(on ? 1 : 0); }
 float ctx_alpha(rpq_ctx *ctx) { return ctx->alpha; }
 uint64_t ctx_time_limit_ns(rpq_ctx *ctx) { return ctx->time_limit_ns; }
 void *ctx_static_scratch(rpq_ctx *ctx) { return ctx->static_scratch; }
+void ctx_release_workspace(rpq_ctx *ctx) {
+  free_workspace(ctx);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->pool) cudaMemPoolTrimTo(ctx->pool, 0);
+}
 const DevGraph &graph_dev(const rpq_graph *g) { return g->g; }
 const HostQuery &query_host(const rpq_query *q) { return q->hq; }
 
@@ -1530,6 +1570,280 @@ int rpq_lane_stats_multi(rpq_ctx *ctx, const rpq_graph *gr, const std::vector<Mu
     stats->emit_ms += ms_emit;
     stats->bfs_launches += 1;
     stats->launches += 4;
+  }
+  return RPQ_OK;
+}
+
+// One lane-mode launch over tasks[idx[0 .. k)] (one lane each, lane i =
+// idx[i]); results into lane_stats at the tasks' indices.
+double host_seconds() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+static int lane_launch(rpq_ctx *ctx, const rpq_graph *gr, const std::vector<LaneTask> &tasks, const uint32_t *idx,
+                       uint32_t k, std::vector<uint64_t> *lane_stats, rpq_stats *stats, std::vector<double> *done_s) {
+  const DevGraph &g = gr->g;
+  const uint32_t n = g.n, L = g.L;
+  const int nw = k <= 64 ? 1 : 4;
+  const uint32_t K = 64u * nw;
+  const uint32_t G = (k + K - 1) / K;
+  if (G > 16) return set_err(ctx, RPQ_ERR_INVALID_ARG, "at most 4,096 lanes per lane-mode launch");
+  const uint64_t GW = (uint64_t)G * nw;
+  uint32_t Q = 0;
+  for (uint32_t i = 0; i < k; i++) Q = std::max(Q, query_host(tasks[idx[i]].q).d.n_states);
+  if (Q == 0) return RPQ_OK;
+  // the union's transitions (state, label, target), in that order
+  std::vector<uint8_t> used((size_t)Q * L * Q, 0);
+  for (uint32_t i = 0; i < k; i++) {
+    const HostQuery &hq = query_host(tasks[idx[i]].q);
+    const uint32_t nl = hq.d.n_labels;
+    for (uint32_t q = 0; q < hq.d.n_states; q++)
+      for (uint32_t l = 0; l < std::min(nl, L); l++) {
+        const int32_t t = hq.next[(size_t)q * nl + l];
+        if (t >= 0) used[((size_t)q * L + l) * Q + t] = 1;
+      }
+  }
+  std::vector<uint32_t> tid((size_t)Q * L * Q, 0xFFFFFFFFu);
+  std::vector<uint16_t> out_begin(Q + 1, 0);
+  std::vector<uint32_t> trans;
+  for (uint32_t q = 0; q < Q; q++) {
+    out_begin[q] = (uint16_t)trans.size();
+    for (uint32_t l = 0; l < L; l++)
+      for (uint32_t t = 0; t < Q; t++)
+        if (used[((size_t)q * L + l) * Q + t]) {
+          tid[((size_t)q * L + l) * Q + t] = (uint32_t)trans.size();
+          trans.push_back(l | (t << 16));
+        }
+  }
+  out_begin[Q] = (uint16_t)trans.size();
+  if (trans.size() >= 0xFFFF) return set_err(ctx, RPQ_ERR_TOO_COMPLEX, "union automaton too large");
+  const uint32_t T = (uint32_t)trans.size();
+  // the union's bottom-up form: per target state, per label, its source states
+  QueryDesc un;
+  std::memset(&un, 0, sizeof(un));
+  un.n_states = Q;
+  un.n_labels = L;
+  std::vector<uint16_t> in_t;
+  uint32_t cnt = 0;
+  for (uint32_t t2 = 0; t2 < Q; t2++) {
+    un.in_begin[t2] = (uint16_t)cnt;
+    for (uint32_t l = 0; l < L; l++) {
+      uint32_t from = 0;
+      for (uint32_t q = 0; q < Q; q++)
+        if (used[((size_t)q * L + l) * Q + t2]) from |= 1u << q;
+      if (!from) continue;
+      if (cnt >= RPQ_MAX_TRANSITIONS) return set_err(ctx, RPQ_ERR_TOO_COMPLEX, "union automaton too large");
+      un.in_label[cnt] = (uint8_t)l;
+      un.in_from[cnt] = from;
+      for (uint32_t q = 0; q < Q; q++)
+        in_t.push_back((from >> q) & 1u ? (uint16_t)tid[((size_t)q * L + l) * Q + t2] : (uint16_t)0xFFFF);
+      cnt++;
+    }
+  }
+  un.in_begin[Q] = (uint16_t)cnt;
+  if (in_t.empty()) in_t.push_back(0xFFFF);
+  // per-lane masks: transitions taken, accepting states, states absent
+  std::vector<u64> mask((size_t)std::max(1u, T) * GW, 0), fin((size_t)Q * GW, 0), empty_q((size_t)Q * GW, 0);
+  std::vector<uint32_t> lanes((size_t)G * K, NO_SOURCE);
+  for (uint32_t i = 0; i < G * K; i++) {
+    const uint64_t word = i / 64, bit = 1ull << (i % 64);
+    if (i >= k) {
+      for (uint32_t q = 0; q < Q; q++) empty_q[q * GW + word] |= bit;
+      continue;
+    }
+    const LaneTask &tk = tasks[idx[i]];
+    const HostQuery &hq = query_host(tk.q);
+    if (tk.source >= n) return set_err(ctx, RPQ_ERR_INVALID_ARG, "source id out of range");
+    lanes[i] = hq.d.n_states ? tk.source : NO_SOURCE;
+    const uint32_t nl = hq.d.n_labels;
+    for (uint32_t q = 0; q < Q; q++) {
+      if (q >= hq.d.n_states) {
+        empty_q[q * GW + word] |= bit;
+        continue;
+      }
+      if ((hq.d.final_mask >> q) & 1u) fin[q * GW + word] |= bit;
+      for (uint32_t l = 0; l < std::min(nl, L); l++) {
+        const int32_t t = hq.next[(size_t)q * nl + l];
+        if (t >= 0) mask[(size_t)tid[((size_t)q * L + l) * Q + t] * GW + word] |= bit;
+      }
+    }
+    if (!hq.d.n_states)
+      for (uint32_t q = 0; q < Q; q++) empty_q[q * GW + word] |= bit;
+    un.final_mask |= hq.d.final_mask;
+  }
+  un.final_mask &= Q >= 32 ? ~0u : ((1u << Q) - 1u);
+  // resident blocks of the lane-mode kernel
+  int &bpsm = ctx->bpsm_lane[nw == 1 ? 0 : 1];
+  if (bpsm == 0 && msbfs_lane_max_blocks(nw, BFS_THREADS_HOST, &bpsm))
+    return set_err(ctx, RPQ_ERR_CUDA, "occupancy query failed");
+  const int blocks = ctx_sm_share(ctx) * bpsm;
+  if (blocks <= 0) return set_err(ctx, RPQ_ERR_CUDA, "traversal kernel cannot be made resident");
+  const uint64_t slack = 2ull * blocks * (BFS_THREADS_HOST / 32) * APPEND_SEG;
+  const uint64_t words = (uint64_t)G * Q * n * nw;
+  const uint64_t lists = (uint64_t)G * Q * n + slack;
+  const uint64_t claims = nw > 1 ? (uint64_t)G * Q * n : 0;
+  {
+    const uint64_t need = workspace_bytes(words, lists, claims, G * K);
+    const uint64_t have = ctx->budget - ctx->used +
+                          workspace_bytes(ctx->ws.vis_words, ctx->ws.list_cap, ctx->ws.claim_cap, ctx->ws.lane_cap);
+    if (need + (64ull << 20) > have) {
+      if (k == 1) return set_err(ctx, RPQ_ERR_OUT_OF_BUDGET, "one lane's traversal state exceeds the budget");
+      const uint32_t h = k / 2;
+      int r = lane_launch(ctx, gr, tasks, idx, h, lane_stats, stats, done_s);
+      if (r == RPQ_OK) r = lane_launch(ctx, gr, tasks, idx + h, k - h, lane_stats, stats, done_s);
+      return r;
+    }
+  }
+  int rc = ensure_workspace(ctx, words, lists, claims, G * K);
+  if (rc) return rc;
+  Workspace &w = ctx->ws;
+  // one upload buffer for the tables
+  const size_t b_ob = (Q + 1) * 2, b_tr = std::max<size_t>(1, T) * 4, b_it = in_t.size() * 2;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t o_mask = 0, o_fin = o_mask + al(mask.size() * 8), o_emp = o_fin + al(fin.size() * 8),
+               o_ob = o_emp + al(empty_q.size() * 8), o_tr = o_ob + al(b_ob), o_it = o_tr + al(b_tr),
+               o_ls = o_it + al(b_it), tbytes = o_ls + al(24ull * G * K);
+  std::vector<unsigned char> host(o_ls);
+  std::memcpy(host.data() + o_mask, mask.data(), mask.size() * 8);
+  std::memcpy(host.data() + o_fin, fin.data(), fin.size() * 8);
+  std::memcpy(host.data() + o_emp, empty_q.data(), empty_q.size() * 8);
+  std::memcpy(host.data() + o_ob, out_begin.data(), b_ob);
+  if (T) std::memcpy(host.data() + o_tr, trans.data(), b_tr);
+  std::memcpy(host.data() + o_it, in_t.data(), b_it);
+  unsigned char *dt = nullptr;
+  if ((rc = dalloc(ctx, &dt, tbytes))) return rc;
+  cudaStream_t st = ctx->stream;
+  u64 *ls = reinterpret_cast<u64 *>(dt + o_ls);
+  cudaError_t e = cudaMemcpyAsync(dt, host.data(), o_ls, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ls, 0, 24ull * G * K, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w.lanesrc, lanes.data(), lanes.size() * 4, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    dfree(ctx, dt, tbytes);
+    return cuda_err(ctx, e, "lane tables upload");
+  }
+  BfsParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.out_off = g.out_off;
+  p.out_col = g.out_col;
+  p.in_off = g.in_off;
+  p.in_col = g.in_col;
+  p.hchunk = g.hchunk_in;
+  for (uint32_t l = 0; l <= g.L && l < g.hchunk_in_off.size(); l++) p.hchunk_off[l] = g.hchunk_in_off[l];
+  for (uint32_t l = 0; l < g.L; l++) p.label_edges[l] = g.label_edges[l];
+  p.n = n;
+  p.L = L;
+  p.G = G;
+  p.Q = Q;
+  p.lanesrc = w.lanesrc;
+  p.vis = w.vis;
+  p.fr0 = w.fr0;
+  p.fr1 = w.fr1;
+  p.claim = w.claim;
+  p.spill = w.spill;
+  p.spill_cap = ctx->spill_cap;
+  p.list0 = w.list0;
+  p.list1 = w.list1;
+  p.fbits = w.fbits;
+  p.fbits_words = w.fbits_words();
+  p.append_seg = APPEND_SEG;
+  p.list_cap = w.list_cap;
+  p.ctl = ctx->ctl;
+  p.stamp_base = ctx->stamp;
+  p.nblocks = (unsigned)blocks;
+  p.force = 0;
+  p.alpha = ctx->alpha;
+  p.time_limit_ns = ctx->time_limit_ns;
+  p.q = un;
+  p.la_out_begin = reinterpret_cast<const unsigned short *>(dt + o_ob);
+  p.la_trans = reinterpret_cast<const unsigned int *>(dt + o_tr);
+  p.la_mask = reinterpret_cast<const unsigned long long *>(dt + o_mask);
+  p.la_in_t = reinterpret_cast<const unsigned short *>(dt + o_it);
+  EmitParams ep{};
+  ep.vis = w.vis;
+  ep.n = n;
+  ep.G = G;
+  ep.Q = Q;
+  ep.final_mask = un.final_mask;
+  ep.final_lane = reinterpret_cast<const unsigned long long *>(dt + o_fin);
+  ep.lanesrc = w.lanesrc;
+  ep.segs = (n + EMIT_SEG - 1) / EMIT_SEG;
+  BfsCtl hctl;
+  std::vector<uint64_t> hls(3ull * G * K);
+  if ((e = launch_vis_init_lane(nw, p, reinterpret_cast<const u64 *>(dt + o_emp), st)) == cudaSuccess &&
+      (e = cudaMemsetAsync(ctx->ctl, 0, sizeof(BfsCtl), st)) == cudaSuccess &&
+      (e = cudaEventRecord(ctx->ev[0], st)) == cudaSuccess &&
+      (e = launch_msbfs_lane(nw, p, blocks, BFS_THREADS_HOST, st)) == cudaSuccess &&
+      (e = cudaEventRecord(ctx->ev[1], st)) == cudaSuccess && (e = launch_emit_lane_stats(nw, ep, ls, st)) == cudaSuccess &&
+      (e = cudaEventRecord(ctx->ev[2], st)) == cudaSuccess)
+    e = rb_queue(ctx, 0, ctx->ctl, sizeof(BfsCtl));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hls.data(), ls, hls.size() * 8, cudaMemcpyDeviceToHost, st);
+  dfree(ctx, dt, tbytes);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "lane-mode launch");
+  std::memcpy(&hctl, ctx->rb_host, sizeof(BfsCtl));
+  if (hctl.err) return traversal_error(ctx, hctl.err);
+  ctx->stamp += (uint32_t)hctl.levels + 3;
+  const double now = host_seconds();
+  for (uint32_t i = 0; i < k; i++) {
+    for (int c = 0; c < 3; c++) (*lane_stats)[3ull * idx[i] + c] = hls[3ull * i + c];
+    if (done_s) (*done_s)[idx[i]] = now;
+  }
+  if (ctx->trace) {
+    uint32_t nl = (uint32_t)std::min<uint64_t>(hctl.levels, TRACE_LEVELS);
+    std::fprintf(stderr, "[rpq trace] lanes k=%u G=%u NW=%d Q=%u T=%u levels=%llu W=%llu\n", k, G, nw, Q, T,
+                 (unsigned long long)hctl.levels, (unsigned long long)hctl.stats[ST_W]);
+    for (uint32_t l = 0; l < nl; l++)
+      std::fprintf(stderr, "[rpq trace]   level %2u %s n=%10llu mf=%12llu %9.3f ms\n", l,
+                   hctl.trace_mode[l] == 1 ? "push" : "pull", (unsigned long long)hctl.trace_n[l],
+                   (unsigned long long)hctl.trace_mf[l], (hctl.trace_t[l + 1] - hctl.trace_t[l]) * 1e-6);
+  }
+  if (stats) {
+    float ms_bfs = 0, ms_emit = 0;
+    cudaEventElapsedTime(&ms_bfs, ctx->ev[0], ctx->ev[1]);
+    cudaEventElapsedTime(&ms_emit, ctx->ev[1], ctx->ev[2]);
+    stats->product_edges += hctl.stats[ST_W];
+    stats->product_vertices += hctl.stats[ST_N];
+    stats->levels += hctl.levels;
+    stats->push_levels += hctl.stats[ST_PUSH_LEVELS];
+    stats->pull_levels += hctl.stats[ST_PULL_LEVELS];
+    stats->group_edges += hctl.stats[ST_GROUP_EDGES];
+    stats->group_rows += hctl.stats[ST_GROUP_ROWS];
+    stats->group_vertices += hctl.stats[ST_GROUP_VERTICES];
+    stats->pull_edges += hctl.stats[ST_PULL_EDGES];
+    stats->pull_vertices += hctl.stats[ST_PULL_VERTICES];
+    stats->alg_bytes += hctl.stats[ST_ALG_BYTES];
+    stats->group_product_edges += hctl.stats[ST_GROUP_W];
+    stats->group_label_rows += hctl.stats[ST_GROUP_X];
+    stats->lane_groups += G;
+    stats->bfs_ms += ms_bfs;
+    stats->emit_ms += ms_emit;
+    stats->bfs_launches += 1;
+    stats->launches += 6;
+  }
+  return RPQ_OK;
+}
+
+int rpq_lane_stats_lanes(rpq_ctx *ctx, const rpq_graph *gr, const std::vector<LaneTask> &tasks, uint32_t max_lanes,
+                         std::vector<uint64_t> *lane_stats, rpq_stats *stats, std::vector<double> *done_s) {
+  lane_stats->assign(3 * tasks.size(), 0);
+  if (done_s) done_s->assign(tasks.size(), host_seconds());
+  max_lanes = std::max(1u, std::min(max_lanes, 4096u));
+  // tasks ordered by state count (a launch is sized by its largest automaton),
+  // automata with more than 8 states apart from the rest
+  std::vector<uint32_t> order;
+  for (uint32_t i = 0; i < tasks.size(); i++) {
+    if (!tasks[i].q) return set_err(ctx, RPQ_ERR_INVALID_ARG, "null query");
+    if (query_host(tasks[i].q).d.n_states) order.push_back(i);
+  }
+  auto states = [&](uint32_t i) { return query_host(tasks[i].q).d.n_states; };
+  std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return states(a) < states(b); });
+  for (size_t b = 0; b < order.size();) {
+    size_t e = std::min(order.size(), b + max_lanes);
+    if (states(order[b]) <= 8)
+      while (e > b + 1 && states(order[e - 1]) > 8) e--;
+    const int rc = lane_launch(ctx, gr, tasks, order.data() + b, (uint32_t)(e - b), lane_stats, stats, done_s);
+    if (rc) return rc;
+    b = e;
   }
   return RPQ_OK;
 }

@@ -44,6 +44,9 @@ uint64_t ctx_time_limit_ns(rpq_ctx *ctx);
 // Device address of the static scratch array of run_rpq_static on the
 // context's device (looked up by rpq_create).
 void *ctx_static_scratch(rpq_ctx *ctx);
+// Frees the context's traversal workspace and returns its pool's unused
+// memory to the device (the next evaluation allocates afresh).
+void ctx_release_workspace(rpq_ctx *ctx);
 int static_scratch_prepare(void **addr, std::string *msg);
 const DevGraph &graph_dev(const rpq_graph *g);
 const HostQuery &query_host(const rpq_query *q);
@@ -59,6 +62,20 @@ struct MultiUnit {
 };
 int rpq_lane_stats_multi(rpq_ctx *ctx, const rpq_graph *g, const std::vector<MultiUnit> &units,
                          std::vector<uint64_t> *lane_stats, rpq_stats *stats);
+// One single-source task of a lane-mode launch: a query and its start vertex.
+struct LaneTask {
+  const rpq_query *q = nullptr;
+  uint32_t source = 0;
+};
+// Count-only evaluation of single-source tasks with a different automaton per
+// lane: tasks are packed up to max_lanes (<= 4,096) per launch, ordered by
+// their automata's state counts; task i's own (rows, digest sum, digest xor)
+// go to lane_stats[3 * i ..], counters are added to *stats.
+// done_s (optional): per task, the host steady-clock time (s) at which its
+// launch's summaries were read back.
+int rpq_lane_stats_lanes(rpq_ctx *ctx, const rpq_graph *g, const std::vector<LaneTask> &tasks, uint32_t max_lanes,
+                         std::vector<uint64_t> *lane_stats, rpq_stats *stats, std::vector<double> *done_s = nullptr);
+double host_seconds();  // steady clock
 int rpq_lane_stats_for_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q,
                                const std::vector<uint32_t> &srcs, std::vector<uint64_t> *lane_stats,
                                rpq_stats *stats);

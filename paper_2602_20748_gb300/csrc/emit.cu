@@ -82,7 +82,9 @@ __device__ __forceinline__ void batch_fetch(const EmitParams &p, u32 final_mask,
     if (v < nv && w < p.n)
       for (u32 fm = final_mask; fm; fm &= fm - 1) {
         const u32 q = __ffs(fm) - 1;
-        word |= __ldg(p.vis + (((u64)q * p.n + w) * p.G + g) * NW + h);
+        u64 x = __ldg(p.vis + (((u64)q * p.n + w) * p.G + g) * NW + h);
+        if (p.final_lane) x &= __ldg(p.final_lane + ((u64)q * p.G + g) * NW + h);  // lane mode
+        word |= x;
       }
     pre[r] = word;
   }

@@ -146,10 +146,15 @@ __device__ bool grid_barrier(BfsCtl *c, unsigned nblocks, u64 limit_ns) {
   return stop == 0;
 }
 
-// Automaton of group g: its own in multi mode, else the launch's.
-template <bool MULTI>
+// Automaton modes of a launch: one automaton for every lane, one per lane
+// group (multi), or one per lane (lane mode).
+constexpr int AM_ONE = 0, AM_GROUP = 1, AM_LANE = 2;
+
+// Automaton of group g: its own in multi mode, else the launch's (the union
+// in lane mode).
+template <int AM>
 __device__ __forceinline__ const QueryDesc &gdesc(const BfsParams &p, u32 g) {
-  if constexpr (MULTI)
+  if constexpr (AM == AM_GROUP)
     return p.qg[g];
   else
     return p.q;
@@ -168,6 +173,34 @@ __device__ __forceinline__ u32 degsum(const BfsParams &p, const QueryDesc &qd, u
     r++;
   }
   if (rows) *rows = r;
+  return s;
+}
+
+// Lane mode: the rows a top-down step over (q, v) reads -- the out-degree of
+// v summed over the union's transitions leaving q (returned; their number in
+// *rows) -- and, for the lanes set in m (group g's words), each lane's own
+// product-edge count: deg_l(v) for every label l its automaton leaves q on,
+// added into W.
+template <int NW>
+__device__ __forceinline__ u32 la_degsum(const BfsParams &p, u32 q, u32 v, u32 g, const Word<NW> &m, u64 &W,
+                                         u32 *rows) {
+  u32 s = 0, r = 0;
+  const u32 n1 = p.n + 1;
+  const u64 gw = (u64)p.G * NW;
+  for (u32 t = p.la_out_begin[q]; t < p.la_out_begin[q + 1]; t++) {
+    const u32 l = p.la_trans[t] & 0xFFFFu;
+    if (l >= p.L) continue;
+    const u32 *off = p.out_off + (u64)l * n1 + v;
+    const u32 d = __ldg(off + 1) - __ldg(off);
+    const u64 *mk = p.la_mask + t * gw + (u64)g * NW;
+    u32 c = 0;
+#pragma unroll
+    for (int k = 0; k < NW; k++) c += __popcll(m.w[k] & __ldg(mk + k));
+    W += (u64)c * d;
+    s += d;
+    r++;
+  }
+  *rows = r;
   return s;
 }
 
@@ -234,7 +267,7 @@ __device__ __forceinline__ void append_close(const BfsParams &p, Appender &a, u6
   a.pos = a.end = 0;
 }
 
-template <int NW, bool MULTI>
+template <int NW, int AM>
 __device__ void seed_phase(const BfsParams &p, u64 *stat) {
   const u32 K = 64 * NW;
   const u64 total = (u64)p.G * K;
@@ -261,9 +294,16 @@ __device__ void seed_phase(const BfsParams &p, u64 *stat) {
           take = atomicMax(p.claim + ((u64)s * p.G + g), p.stamp_base + 1) < p.stamp_base + 1;
         entry = ((u64)g * p.Q << 32) | s;
         if (take && p.fbits) atomicOr(p.fbits + (s >> 5), 1u << (s & 31));  // state 0, bitmap 0
-        u32 rows = 0;
-        u32 d = degsum(p, gdesc<MULTI>(p, g), 0, s, &rows);
-        W += d;
+        u32 rows = 0, d;
+        if constexpr (AM == AM_LANE) {
+          Word<NW> me;
+#pragma unroll
+          for (int k = 0; k < NW; k++) me.w[k] = (lane / 64 == (u32)k) ? bit : 0ull;
+          d = la_degsum<NW>(p, 0, s, g, me, W, &rows);
+        } else {
+          d = degsum(p, gdesc<AM>(p, g), 0, s, &rows);
+          W += d;
+        }
         N += 1;
         if (take) {
           mf += d;
@@ -320,7 +360,7 @@ __device__ __forceinline__ bool relax(const BfsParams &p, u64 *FB, u32 tgq, u32 
 // entries at a time and spreads the edges of their rows evenly over its lanes
 // (prefix sum of row lengths, owner found by binary search); rows longer than
 // SPILL_EDGES are queued in chunks for the spill sub-phase.
-template <int NW, bool MULTI>
+template <int NW, int AM>
 __device__ void push_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u64 n_cur, u32 stamp, u64 *stat) {
   const u64 *list = lp ? p.list1 : p.list0;
   u64 *nlist = lp ? p.list0 : p.list1;
@@ -346,17 +386,35 @@ __device__ void push_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u64 n_c
     for (int i = 0; i < NW; i++) fm.w[i] = 0;
     if (valid) fm = load_cg<NW>(F + widx<NW>(p, g, q, v));
     entries += valid;
-    const QueryDesc &qd = gdesc<MULTI>(p, valid ? g : 0);
-    u32 t_beg = valid ? qd.out_begin[q] : 0;
-    u32 nt = valid ? qd.out_begin[q + 1] - t_beg : 0;
+    const QueryDesc &qd = gdesc<AM>(p, valid ? g : 0);
+    u32 t_beg, nt;
+    if constexpr (AM == AM_LANE) {
+      t_beg = valid ? p.la_out_begin[q] : 0;
+      nt = valid ? p.la_out_begin[q + 1] - t_beg : 0;
+    } else {
+      t_beg = valid ? qd.out_begin[q] : 0;
+      nt = valid ? qd.out_begin[q + 1] - t_beg : 0;
+    }
     u32 max_nt = __reduce_max_sync(FULL_MASK, nt);
     for (u32 j = 0; j < max_nt; j++) {
       u32 rbeg = 0, rlen = 0, tgq = 0;
+      Word<NW> fmt = fm;  // the entry's lanes that take this transition
       if (j < nt) {
         u32 t = t_beg + j;
-        u32 l = qd.out_label[t];
-        tgq = g * Q + qd.out_to[t];
-        if (l < p.L) {
+        u32 l, to;
+        if constexpr (AM == AM_LANE) {
+          const u32 e = p.la_trans[t];
+          l = e & 0xFFFFu;
+          to = e >> 16;
+          const u64 *mk = p.la_mask + (u64)t * ((u64)p.G * NW) + (u64)g * NW;
+#pragma unroll
+          for (int k = 0; k < NW; k++) fmt.w[k] &= __ldg(mk + k);
+        } else {
+          l = qd.out_label[t];
+          to = qd.out_to[t];
+        }
+        tgq = g * Q + to;
+        if (l < p.L && (AM != AM_LANE || any_bits(fmt))) {
           const u32 *off = p.out_off + (u64)l * n1 + v;
           rbeg = __ldg(off);
           rlen = __ldg(off + 1) - rbeg;
@@ -372,7 +430,7 @@ __device__ void push_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u64 n_c
           rec[0] = ((u64)tgq << 32) | (rbeg + c * SPILL_EDGES);
           rec[1] = min(SPILL_EDGES, rlen - c * SPILL_EDGES);
 #pragma unroll
-          for (int t = 0; t < NW; t++) rec[2 + t] = fm.w[t];
+          for (int t = 0; t < NW; t++) rec[2 + t] = fmt.w[t];
         }
         // the chunks that did not fit stay with this warp
         const u32 moved = min(rlen, fit * SPILL_EDGES);
@@ -403,7 +461,7 @@ __device__ void push_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u64 n_c
         u32 o_gq = __shfl_sync(FULL_MASK, tgq, o);
         Word<NW> ofm;
 #pragma unroll
-        for (int i = 0; i < NW; i++) ofm.w[i] = __shfl_sync(FULL_MASK, fm.w[i], o);
+        for (int i = 0; i < NW; i++) ofm.w[i] = __shfl_sync(FULL_MASK, fmt.w[i], o);
         bool take = false;
         u32 w = 0;
         if (k < total) {
@@ -473,12 +531,25 @@ __device__ void spill_phase(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 st
 // sub-warp (lanes sg_mask) leaves the row when all its lanes have (with many
 // groups a vertex practically never runs out, and the test costs more than it
 // saves).  Returns the in-edges examined.
-template <int NW, int PER, bool EARLY>
+template <int NW, int PER, bool EARLY, bool LANE>
 __device__ __forceinline__ u32 gather_row(const BfsParams &p, const u64 *F, const u32 *bits, u32 from, u32 beg,
                                           u32 end, u32 lane_off, bool lane_on, u32 sg_mask,
-                                          const u64 (&vis)[PER], u64 (&acc)[PER], u32 &gathers) {
+                                          const u64 (&vis)[PER], u64 (&acc)[PER], u32 &gathers,
+                                          const unsigned short *tin) {
   const u32 n = p.n;
   const u64 wpv = (u64)p.G * NW;
+  // lane mode: the gathered words of source state s are masked with the lanes
+  // that take this group's transition from s (tin[s]); else all lanes
+  auto lane_mask = [&](u32 st, u64 (&mk)[PER]) {
+    if constexpr (LANE) {
+      const u64 *mp = p.la_mask + (u64)tin[st] * wpv + lane_off;
+#pragma unroll
+      for (int k = 0; k < PER; k++) mk[k] = __ldg(mp + k);
+    } else {
+#pragma unroll
+      for (int k = 0; k < PER; k++) mk[k] = ~0ull;
+    }
+  };
   auto done = [&]() {
     bool d = true;
 #pragma unroll
@@ -496,6 +567,8 @@ __device__ __forceinline__ u32 gather_row(const BfsParams &p, const u64 *F, cons
         v3 = __ldg(p.in_col + i + 3);
     if (!fin) {
       for (u32 fb = from; fb; fb &= fb - 1) {
+        u64 mk[PER];
+        lane_mask(__ffs(fb) - 1, mk);
         const u64 qb = (u64)(__ffs(fb) - 1) * n;
         // with a frontier bitmap, neighbours outside the frontier are skipped
         bool h0 = true, h1 = true, h2 = true, h3 = true;
@@ -514,11 +587,12 @@ __device__ __forceinline__ u32 gather_row(const BfsParams &p, const u64 *F, cons
           ulonglong2 a1 = h1 ? __ldcg(reinterpret_cast<const ulonglong2 *>(f1)) : z;
           ulonglong2 a2 = h2 ? __ldcg(reinterpret_cast<const ulonglong2 *>(f2)) : z;
           ulonglong2 a3 = h3 ? __ldcg(reinterpret_cast<const ulonglong2 *>(f3)) : z;
-          acc[0] |= a0.x | a1.x | a2.x | a3.x;
-          acc[1] |= a0.y | a1.y | a2.y | a3.y;
+          acc[0] |= (a0.x | a1.x | a2.x | a3.x) & mk[0];
+          acc[1] |= (a0.y | a1.y | a2.y | a3.y) & mk[1];
         } else {
-          acc[0] |= (h0 ? __ldcg(f0) : 0ull) | (h1 ? __ldcg(f1) : 0ull) | (h2 ? __ldcg(f2) : 0ull) |
-                    (h3 ? __ldcg(f3) : 0ull);
+          acc[0] |= ((h0 ? __ldcg(f0) : 0ull) | (h1 ? __ldcg(f1) : 0ull) | (h2 ? __ldcg(f2) : 0ull) |
+                     (h3 ? __ldcg(f3) : 0ull)) &
+                    mk[0];
         }
       }
       if (EARLY) fin = done();
@@ -532,9 +606,11 @@ __device__ __forceinline__ u32 gather_row(const BfsParams &p, const u64 *F, cons
       const u64 bi = (u64)(__ffs(fb) - 1) * n + v;
       if (bits && !((__ldcg(bits + (bi >> 5)) >> (bi & 31)) & 1u)) continue;
       gathers++;
+      u64 mk[PER];
+      lane_mask(__ffs(fb) - 1, mk);
       const u64 *f = F + bi * wpv + lane_off;
 #pragma unroll
-      for (int k = 0; k < PER; k++) acc[k] |= __ldcg(f + k);
+      for (int k = 0; k < PER; k++) acc[k] |= __ldcg(f + k) & mk[k];
     }
   }
   return end - beg;
@@ -594,7 +670,7 @@ __device__ __forceinline__ void pull_finish(const BfsParams &p, Appender &app, u
 // chunk taken dynamically over the (target state, transition group) pairs
 // whose source states are active; the sub-warps split the chunk's edges and
 // OR their gathers together.
-template <int NW, bool EARLY, bool MULTI>
+template <int NW, bool EARLY, int AM>
 __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 active, u32 stamp, const u32 *bits,
                            u64 *stat) {
   constexpr int PER = (NW >= 2) ? 2 : 1;
@@ -695,9 +771,11 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
           if (end - beg >= HEAVY_ROW && chunked) continue;
           // in multi mode each lane gathers through its own group's transitions
           u32 lfrom = from;
-          if constexpr (MULTI) lfrom = lane_on ? p.from_tab[((u64)my_g * Q + q2) * p.L + l] & active : 0u;
+          if constexpr (AM == AM_GROUP) lfrom = lane_on ? p.from_tab[((u64)my_g * Q + q2) * p.L + l] & active : 0u;
           u32 gat = 0;
-          const u32 ex = gather_row<NW, PER, EARLY>(p, F, bits, lfrom, beg, end, lane_off, lane_on, sg_mask, vis, acc, gat);
+          const u32 ex = gather_row<NW, PER, EARLY, AM == AM_LANE>(p, F, bits, lfrom, beg, end, lane_off, lane_on,
+                                                                   sg_mask, vis, acc, gat,
+                                                                   p.la_in_t + (u64)j * Q);
           edges += (li == 0) ? ex : 0;
           // column ids, frontier-bit words when tested, gathered frontier words
           bytes += (li == 0) ? 8 + (u64)ex * (4 + (bits ? 4 * __popc(from) : 0)) + (u64)gat * gword : 0;
@@ -718,7 +796,7 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
       it = __shfl_sync(FULL_MASK, it, 0);
       // map the item number to (target state, transition group, chunk)
       u64 acc_base = 0, ci = 0;
-      u32 q2s = 0, from = 0, ls = 0;
+      u32 q2s = 0, from = 0, ls = 0, js = 0;
       bool found = false;
       for (u32 q2 = 0; q2 < Q && !found; q2++)
         for (u32 j = p.q.in_begin[q2]; j < p.q.in_begin[q2 + 1]; j++) {
@@ -729,6 +807,7 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
             found = true;
             q2s = q2;
             ls = l;
+            js = j;
             from = p.q.in_from[j] & active;
             ci = p.hchunk_off[l] + (it - acc_base);
             break;
@@ -752,9 +831,10 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
       const u32 len = end - beg, per = (len + VPW - 1) / VPW;
       const u32 sb = beg + min(len, sg * per), se = beg + min(len, (sg + 1) * per);
       u32 lfrom = from;
-      if constexpr (MULTI) lfrom = lane_on ? p.from_tab[((u64)my_g * Q + q2s) * p.L + ls] & active : 0u;
+      if constexpr (AM == AM_GROUP) lfrom = lane_on ? p.from_tab[((u64)my_g * Q + q2s) * p.L + ls] & active : 0u;
       u32 gat = 0;
-      const u32 ex = gather_row<NW, PER, EARLY>(p, F, bits, lfrom, sb, se, lane_off, lane_on, sg_mask, vis, acc, gat);
+      const u32 ex = gather_row<NW, PER, EARLY, AM == AM_LANE>(p, F, bits, lfrom, sb, se, lane_off, lane_on, sg_mask,
+                                                               vis, acc, gat, p.la_in_t + (u64)js * Q);
       for (u32 o = SW; o < 32; o <<= 1) {
 #pragma unroll
         for (int k = 0; k < PER; k++) acc[k] |= __shfl_xor_sync(FULL_MASK, acc[k], o);
@@ -777,7 +857,7 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
 // the DFA states present in the new frontier, clear the old frontier words.
 // set_bits: the next frontier may be sparse enough for bottom-up levels to
 // test its bitmap, so its bits are set; clear_bits: this level's bits were set.
-template <int NW, bool MULTI>
+template <int NW, int AM>
 __device__ void commit_phase(const BfsParams &p, int lp, u32 nxt, u64 n_cur, bool set_bits, bool clear_bits,
                              u64 *stat) {
   const u64 *list = lp ? p.list1 : p.list0;
@@ -806,9 +886,13 @@ __device__ void commit_phase(const BfsParams &p, int lp, u32 nxt, u64 n_cur, boo
       atomicOr(p.fbits + (lp ? 0 : p.fbits_words) + (bi >> 5), 1u << (bi & 31));
     }
     u32 c = popc_w(m);
-    u32 rows = 0;
-    u32 d = degsum(p, gdesc<MULTI>(p, g), q, w, &rows);
-    W += (u64)c * d;
+    u32 rows = 0, d;
+    if constexpr (AM == AM_LANE) {
+      d = la_degsum<NW>(p, q, w, g, m, W, &rows);
+    } else {
+      d = degsum(p, gdesc<AM>(p, g), q, w, &rows);
+      W += (u64)c * d;
+    }
     N += c;
     mf += d;
     gx += rows;
@@ -872,7 +956,7 @@ __device__ double pull_bytes(const BfsParams &p, u32 active) {
   return b;
 }
 
-template <int NW, bool MULTI>
+template <int NW, int AM>
 __global__ void __launch_bounds__(BFS_THREADS, 4) msbfs_kernel(const __grid_constant__ BfsParams p) {
   // per-warp statistics, summed into the control block at the end
   u64 stat[ST_COUNT];
@@ -881,7 +965,7 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) msbfs_kernel(const __grid_cons
   BfsCtl *c = p.ctl;
   const bool tracer = blockIdx.x == 0 && threadIdx.x == 0;
 
-  seed_phase<NW, MULTI>(p, stat);
+  seed_phase<NW, AM>(p, stat);
   if (!grid_barrier(c, p.nblocks, p.time_limit_ns)) return;
 
   u32 level = 0;
@@ -916,7 +1000,7 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) msbfs_kernel(const __grid_cons
     }
     const u32 stamp = p.stamp_base + level + 2;  // the seeds used stamp_base + 1
     if (push) {
-      push_level<NW, MULTI>(p, lp, cur, nxt, n_cur, stamp, stat);
+      push_level<NW, AM>(p, lp, cur, nxt, n_cur, stamp, stat);
       if (!grid_barrier(c, p.nblocks, p.time_limit_ns)) return;
       if (*(volatile unsigned long long *)&c->spill_count[cur] != 0) {
         spill_phase<NW>(p, lp, cur, nxt, stamp, stat);
@@ -927,12 +1011,13 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) msbfs_kernel(const __grid_cons
       // (implies n_cur * 4 < n * Q, so the commit that built this frontier set its bits)
       const bool sparse = p.fbits && n_cur * 4 < (u64)p.n * __popc(active);
       const u32 *bits = sparse ? p.fbits + (lp ? p.fbits_words : 0) : nullptr;
-      // early exit pays where few lanes are live: one lane group, or the
-      // per-group automata of a multi launch (typically one start vertex each)
-      if (p.G == 1 || MULTI)
-        pull_level<NW, true, MULTI>(p, lp, cur, nxt, active, stamp, bits, stat);
+      // early exit pays where few lanes are live: one lane group, the
+      // per-group automata of a multi launch (typically one start vertex
+      // each), or per-lane automata (lanes of short queries go quiet early)
+      if (p.G == 1 || AM != AM_ONE)
+        pull_level<NW, true, AM>(p, lp, cur, nxt, active, stamp, bits, stat);
       else
-        pull_level<NW, false, MULTI>(p, lp, cur, nxt, active, stamp, bits, stat);
+        pull_level<NW, false, AM>(p, lp, cur, nxt, active, stamp, bits, stat);
       if (!grid_barrier(c, p.nblocks, p.time_limit_ns)) return;
     }
     {
@@ -942,7 +1027,7 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) msbfs_kernel(const __grid_cons
       const u64 sparse_cap = (u64)p.n * p.Q;
       const bool set_bits = p.fbits && n_next * 4 < sparse_cap;
       const bool clear_bits = p.fbits && (level == 0 || n_cur * 4 < sparse_cap);
-      commit_phase<NW, MULTI>(p, lp, nxt, n_cur, set_bits, clear_bits, stat);
+      commit_phase<NW, AM>(p, lp, nxt, n_cur, set_bits, clear_bits, stat);
     }
     if (!grid_barrier(c, p.nblocks, p.time_limit_ns)) return;
   }
@@ -979,6 +1064,31 @@ cudaError_t launch_vis_init(int nw, const BfsParams &p, const unsigned long long
   return cudaGetLastError();
 }
 
+// Lane mode: VIS words start as empty_q[(q * G + g) * NW + k], the lanes that
+// are empty or whose automaton has no state q (so they look visited there).
+template <int NW>
+__global__ void vis_init_lane_kernel(u64 *__restrict__ vis, u64 total, u64 per_state, u32 G,
+                                     const u64 *__restrict__ empty_q) {
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (u64)gridDim.x * blockDim.x) {
+    const u64 q = i / per_state;
+    const u32 gk = (u32)(i % ((u64)G * NW));
+    vis[i] = empty_q[q * G * NW + gk];
+  }
+}
+
+cudaError_t launch_vis_init_lane(int nw, const BfsParams &p, const unsigned long long *empty_q, cudaStream_t st) {
+  const u64 per_state = (u64)p.n * p.G * nw;
+  const u64 total = per_state * p.Q;
+  u64 blocks = (total + 255) / 256;
+  if (blocks > 152ull * 32) blocks = 152ull * 32;
+  if (blocks == 0) blocks = 1;
+  if (nw == 1)
+    vis_init_lane_kernel<1><<<(unsigned)blocks, 256, 0, st>>>(p.vis, total, per_state, p.G, empty_q);
+  else
+    vis_init_lane_kernel<4><<<(unsigned)blocks, 256, 0, st>>>(p.vis, total, per_state, p.G, empty_q);
+  return cudaGetLastError();
+}
+
 // flag[i] = 1 when start vertex srcs[i] has an edge on a label of label_mask
 // in the traversal's forward direction (off = the forward offsets).
 __global__ void source_filter_kernel(const u32 *__restrict__ off, u32 n, u32 L, unsigned long long label_mask,
@@ -1009,8 +1119,8 @@ cudaError_t launch_source_filter(const uint32_t *off, uint32_t n, uint32_t L, un
 cudaError_t launch_msbfs(int nw, const BfsParams &p, int blocks, int threads, cudaStream_t st) {
   void *args[] = {(void *)&p};
   if (nw == 1)
-    return cudaLaunchCooperativeKernel((void *)msbfs_kernel<1, false>, blocks, threads, args, 0, st);
-  return cudaLaunchCooperativeKernel((void *)msbfs_kernel<4, false>, blocks, threads, args, 0, st);
+    return cudaLaunchCooperativeKernel((void *)msbfs_kernel<1, AM_ONE>, blocks, threads, args, 0, st);
+  return cudaLaunchCooperativeKernel((void *)msbfs_kernel<4, AM_ONE>, blocks, threads, args, 0, st);
 }
 
 int msbfs_max_blocks(int nw, int threads, int *blocks_per_sm, int *sms) {
@@ -1019,26 +1129,42 @@ int msbfs_max_blocks(int nw, int threads, int *blocks_per_sm, int *sms) {
   cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
   cudaError_t e;
   if (nw == 1)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, msbfs_kernel<1, false>, threads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, msbfs_kernel<1, AM_ONE>, threads, 0);
   else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, msbfs_kernel<4, false>, threads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, msbfs_kernel<4, AM_ONE>, threads, 0);
   return e == cudaSuccess ? 0 : -1;
 }
 
 cudaError_t preload_static_msbfs_kernels() {
   cudaFuncAttributes a;
-  cudaError_t e = cudaFuncGetAttributes(&a, msbfs_kernel<1, false>);
+  cudaError_t e = cudaFuncGetAttributes(&a, msbfs_kernel<1, AM_ONE>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, vis_init_kernel<1>);
   return e;
 }
 
 cudaError_t launch_msbfs_multi(const BfsParams &p, int blocks, int threads, cudaStream_t st) {
   void *args[] = {(void *)&p};
-  return cudaLaunchCooperativeKernel((void *)msbfs_kernel<1, true>, blocks, threads, args, 0, st);
+  return cudaLaunchCooperativeKernel((void *)msbfs_kernel<1, AM_GROUP>, blocks, threads, args, 0, st);
+}
+
+cudaError_t launch_msbfs_lane(int nw, const BfsParams &p, int blocks, int threads, cudaStream_t st) {
+  void *args[] = {(void *)&p};
+  if (nw == 1)
+    return cudaLaunchCooperativeKernel((void *)msbfs_kernel<1, AM_LANE>, blocks, threads, args, 0, st);
+  return cudaLaunchCooperativeKernel((void *)msbfs_kernel<4, AM_LANE>, blocks, threads, args, 0, st);
+}
+
+int msbfs_lane_max_blocks(int nw, int threads, int *blocks_per_sm) {
+  cudaError_t e;
+  if (nw == 1)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, msbfs_kernel<1, AM_LANE>, threads, 0);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, msbfs_kernel<4, AM_LANE>, threads, 0);
+  return e == cudaSuccess ? 0 : -1;
 }
 
 int msbfs_multi_max_blocks(int threads, int *blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, msbfs_kernel<1, true>, threads, 0) ==
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, msbfs_kernel<1, AM_GROUP>, threads, 0) ==
                  cudaSuccess
              ? 0
              : -1;

@@ -166,6 +166,20 @@ struct BfsParams {
   // + l] is the set of group g's states that reach q2 on label l.
   const QueryDesc *qg;
   const unsigned int *from_tab;
+  // Per-lane automata (lane mode; nullptr otherwise): every lane runs its own
+  // minimal DFA (states 0 .. Q_i - 1, start state 0).  q then holds the union
+  // of the lanes' automata in its bottom-up form (in_begin / in_label /
+  // in_from over states 0 .. Q - 1): it drives bottom-up iteration and the
+  // cost estimates.  The union's transitions (state, label, target) are listed
+  // per source state: transition t of state s is la_trans[t] for
+  // la_out_begin[s] <= t < la_out_begin[s + 1], the label in the low 16 bits
+  // and the target above; la_mask[t * G * NW + g * NW + k] holds the lanes of
+  // word k of group g that take it.  la_in_t[j * Q + s] is the transition
+  // from state s of bottom-up group j (the group's label into its target).
+  const unsigned short *la_out_begin;
+  const unsigned int *la_trans;
+  const unsigned long long *la_mask;
+  const unsigned short *la_in_t;
   BfsCtl *ctl;
   unsigned int stamp_base;     // claim stamps continue across launches
   unsigned int nblocks;
@@ -181,6 +195,11 @@ cudaError_t launch_msbfs(int nw, const BfsParams &p, int blocks, int threads, cu
 // Per-group automata (p.qg set): one lane word per group (NW = 1).
 cudaError_t launch_msbfs_multi(const BfsParams &p, int blocks, int threads, cudaStream_t st);
 int msbfs_multi_max_blocks(int threads, int *blocks_per_sm);
+// Per-lane automata (p.la_* set), NW = 1 or 4.  VIS starts as empty_q[(q * G +
+// g) * NW + k]: the lanes that are empty or whose automaton has no state q.
+cudaError_t launch_msbfs_lane(int nw, const BfsParams &p, int blocks, int threads, cudaStream_t st);
+int msbfs_lane_max_blocks(int nw, int threads, int *blocks_per_sm);
+cudaError_t launch_vis_init_lane(int nw, const BfsParams &p, const unsigned long long *empty_q, cudaStream_t st);
 // flag[i] = whether srcs[i] has an edge (offsets `off`, per label) on a label of label_mask.
 cudaError_t launch_source_filter(const uint32_t *off, uint32_t n, uint32_t L, unsigned long long label_mask,
                                  const uint32_t *srcs, unsigned long long count, unsigned char *flag,
@@ -200,6 +219,10 @@ struct EmitParams {
   uint32_t *dst;                 // output destinations (write pass)
   unsigned long long *digest;    // [2]: sum, xor
   const uint32_t *final_g;       // per-group accepting masks (multi mode), else nullptr
+  // per-lane accepting lanes (lane mode), else nullptr: word [q * G * NW + g
+  // * NW + k] holds the lanes of word k of group g whose automaton accepts in
+  // state q (final_mask is then the union of the lanes' accepting states)
+  const unsigned long long *final_lane;
 };
 constexpr int EMIT_TILES = 128;  // 32-vertex tiles per segment
 constexpr int EMIT_SEG = 32 * EMIT_TILES;

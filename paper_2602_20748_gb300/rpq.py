@@ -289,6 +289,18 @@ _lib.result_query_stats.argtypes = [c_void_p, c_u32, P(c_u64), P(c_u64), P(c_u64
 EXPORTED += ["run_rpq_batch", "rpq_autotune_batch", "result_query_stats"]
 
 
+_lib.result_query_time.argtypes = [c_void_p, c_u32, P(ctypes.c_double)]
+EXPORTED += ["result_query_time"]
+
+
+def result_query_time(r: Result, i: int) -> float:
+    """Milliseconds from the start of run_rpq_batch (RPQ_PER_QUERY) until
+    query i's summary was known."""
+    ms = ctypes.c_double()
+    r.ctx.check(_lib.result_query_time(r.h, i, ctypes.byref(ms)))
+    return ms.value
+
+
 def result_query_stats(r: Result, i: int):
     """(rows, digest sum, digest xor) of query i of a RPQ_PER_QUERY batch."""
     c, s, x = c_u64(), c_u64(), c_u64()
