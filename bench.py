@@ -56,7 +56,7 @@ def parse_args():
     ap.add_argument("--no-extra", action="store_true",
                     help="default workload: skip the compact batch (config 4) and CRPQ (config 3) sub-objects")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="allpairs", choices=["allpairs", "batch", "crpq", "serve"],
+    ap.add_argument("--workload", default="allpairs", choices=["allpairs", "batch", "crpq", "serve", "plan"],
                     help="allpairs: the R-MAT 2^20 all-pairs line (default); batch: 4,096 single-source "
                          "queries on R-MAT 2^22; crpq: the 3-atom triangle CRPQ on R-MAT 2^22; serve: a Poisson "
                          "stream of mixed requests on R-MAT 2^24")
@@ -65,8 +65,6 @@ def parse_args():
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: mean arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serve: arrival window (s)")
     ap.add_argument("--drain", type=float, default=10.0, help="serve: time after the window before cancelling (s)")
-    ap.add_argument("--batch-multi", type=int, default=0, choices=[0, 1],
-                    help="batch / serve: evicted small automaton groups share multi-automaton launches")
     return ap.parse_args()
 
 
@@ -133,17 +131,26 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-KERNEL_SOURCES = ("msbfs.cu", "rpq_internal.h", "device_common.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "msbfs_traffic_rmat18.json")
 
 
-def kernel_source_sha1() -> str:
-    """SHA-1 over the traversal kernel's source files, to tell whether stored
-    ncu counters still describe the kernel that runs."""
+def kernel_source_sha1(read=None) -> str:
+    """SHA-1 over what the traversal kernel is compiled from -- msbfs.cu,
+    device_common.cuh and the BfsCtl / BfsParams definitions of
+    rpq_internal.h -- to tell whether stored ncu counters still describe the
+    kernel that runs.  `read(name)` returns a file's bytes (default: the
+    working tree)."""
+    if read is None:
+        def read(name):
+            with open(os.path.join(ROOT, "paper_2602_20748_gb300", "csrc", name), "rb") as f:
+                return f.read()
     h = hashlib.sha1()
-    for name in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2602_20748_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+    h.update(read("msbfs.cu"))
+    h.update(read("device_common.cuh"))
+    hdr = read("rpq_internal.h").decode()
+    a = hdr.index("struct BfsCtl {")
+    b = hdr.index("};", hdr.index("struct BfsParams {")) + 2
+    h.update(hdr[a:b].encode())
     return h.hexdigest()
 
 
@@ -607,6 +614,50 @@ def bench_crpq(args, compact: bool = False):
     return 0
 
 
+def bench_plan(args, compact: bool = False):
+    """Forward plan (A0) against the start-in-the-middle plan (A3 executed as
+    A5: R(b.c*) materialized, joined with a) for a.b.c* on the R-MAT 2^20
+    workload, all-pairs, count only; the two counts and digests must agree."""
+    import torch
+    from paper_2602_20748_gb300 import rpq
+
+    scale = args.scale if args.scale is not None else SCALE
+    n, src, dst, lab = make_graph(scale)
+    ctx = rpq.Context(device=0)
+    g = rpq.load_graph(ctx, n, N_LABELS, src, dst, lab)
+    del src, dst, lab
+    q0 = rpq.compile_rpq(ctx, "a·b·c*")
+    qa, qbc = rpq.compile_rpq(ctx, "a"), rpq.compile_rpq(ctx, "b·c*")
+    out = {}
+    for name, run in (("A0_forward", lambda: rpq.run_rpq(ctx, g, q0, flags=rpq.RPQ_COUNT_ONLY)),
+                      ("A3_middle", lambda: rpq.run_rpq_middle(ctx, g, qa, qbc, flags=rpq.RPQ_COUNT_ONLY))):
+        run().free()  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = run()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        c, _, hs, hx = rpq.result_info(r)
+        st = rpq.result_stats(r)
+        out[name] = {"s": dt, "rows": c, "digest": [hs, hx], "bfs_ms": st["bfs_ms"], "emit_ms": st["emit_ms"],
+                     "launches": st["launches"]}
+        r.free()
+    for q in (q0, qa, qbc):
+        q.free()
+    g.free()
+    ctx.close()
+    body = {"plans": out, "speedup_middle_over_forward": out["A0_forward"]["s"] / out["A3_middle"]["s"],
+            "equal_results": out["A0_forward"]["rows"] == out["A3_middle"]["rows"] and
+            out["A0_forward"]["digest"] == out["A3_middle"]["digest"],
+            "config": {"workload": f"rmat{scale}-allpairs-abcstar-plans", "query": "a.b.c*", "vertices": n,
+                       "generated_edges": 16 * n, "labels": N_LABELS, "zipf_s": ZIPF_S, "mode": "count only"}}
+    if compact:
+        return body
+    print(json.dumps({"metric": "plan_seconds", "value": out["A3_middle"]["s"], "unit": "s", "n_gpus": 1,
+                      "higher_is_better": False, **body}), flush=True)
+    return 0
+
+
 def _pct(lat_ms, offered: int, q: float):
     """Latency percentile over all offered requests; requests not completed in
     the run count as slower than any completed one (None if the percentile
@@ -656,7 +707,6 @@ def bench_serve(args):
                                             seed=synth.BASE_SEED + 5)
     gen_s = time.perf_counter() - t_gen
     ctx = rpq.Context(device=0)
-    rpq.rpq_set_option(ctx, "batch_multi", args.batch_multi)
     g = rpq.load_graph(ctx, n, L, src, dst, lab)
     del src, dst, lab
     cache = {}
@@ -728,45 +778,67 @@ def bench_serve(args):
         if s_stat[i] == 0 and s_lat[i] / 1000.0 + float(t_arr[i]) > horizon:
             s_stat[i] = 1
 
-    # ---- plain FIFO -----------------------------------------------------------
+    # ---- plain: one FIFO worker per request class ---------------------------
+    # Each class has its own context (own stream) and thread, and runs its
+    # requests one per call in arrival order: run_rpq for a single-source
+    # request, run_rpq_range / run_crpq slices of 4,096 start values for
+    # all-pairs / CRPQ requests.  The three workers run side by side, so a
+    # long all-pairs request does not hold back the single-source ones.
+    import threading
+
     f_lat = [0.0] * m
     f_stat = [1] * m
     f_val = [None] * m
     SL = 4096
     t0 = time.perf_counter()
     deadline = t0 + horizon
-    for i, (k, p) in enumerate(reqs):
-        d = t_arr[i] - (time.perf_counter() - t0)
-        if d > 0:
-            time.sleep(d)
-        if time.perf_counter() >= deadline:
-            break
-        cnt = dsum = dxor = 0
-        ok = True
-        if k == 1:
-            r = rpq.run_rpq(ctx, g, p[0], [p[1]], flags=rpq.RPQ_COUNT_ONLY)
-            cnt, _, dsum, dxor = rpq.result_info(r)
-            r.free()
-        else:
-            for b in range(0, n, SL):
-                if time.perf_counter() >= deadline:
-                    ok = False
-                    break
-                if k == 2:
-                    r = rpq.run_rpq_range(ctx, g, p, b, min(n, b + SL), rpq.RPQ_COUNT_ONLY)
-                else:
-                    r = rpq.run_crpq(ctx, g, 3, p, restrict0=np.arange(b, min(n, b + SL), dtype=np.uint32),
-                                     flags=rpq.RPQ_COUNT_ONLY)
-                c, _, hs, hx = rpq.result_info(r)
+
+    def plain_worker(kind):
+        stream = torch.cuda.Stream()  # kept alive for the context's lifetime
+        c = rpq.Context(device=0, mem_budget_bytes=int(torch.cuda.mem_get_info(0)[0] * 0.25),
+                        stream=stream.cuda_stream)
+        rpq.rpq_set_option(c, "grid_share", {1: 0.5, 2: 0.3, 3: 0.2}[kind])
+        for i, (k, p) in enumerate(reqs):
+            if k != kind:
+                continue
+            d = t_arr[i] - (time.perf_counter() - t0)
+            if d > 0:
+                time.sleep(d)
+            if time.perf_counter() >= deadline:
+                break
+            cnt = dsum = dxor = 0
+            ok = True
+            if k == 1:
+                r = rpq.run_rpq(c, g, p[0], [p[1]], flags=rpq.RPQ_COUNT_ONLY)
+                cnt, _, dsum, dxor = rpq.result_info(r)
                 r.free()
-                cnt += c
-                dsum = (dsum + hs) & 0xFFFFFFFFFFFFFFFF
-                dxor ^= hx
-        done = time.perf_counter()
-        if ok and done <= deadline:
-            f_stat[i] = 0
-            f_lat[i] = (done - (t0 + float(t_arr[i]))) * 1000.0
-            f_val[i] = (cnt, dsum, dxor)
+            else:
+                for b in range(0, n, SL):
+                    if time.perf_counter() >= deadline:
+                        ok = False
+                        break
+                    if k == 2:
+                        r = rpq.run_rpq_range(c, g, p, b, min(n, b + SL), rpq.RPQ_COUNT_ONLY)
+                    else:
+                        r = rpq.run_crpq(c, g, 3, p, restrict0=np.arange(b, min(n, b + SL), dtype=np.uint32),
+                                         flags=rpq.RPQ_COUNT_ONLY)
+                    cc, _, hs, hx = rpq.result_info(r)
+                    r.free()
+                    cnt += cc
+                    dsum = (dsum + hs) & 0xFFFFFFFFFFFFFFFF
+                    dxor ^= hx
+            done = time.perf_counter()
+            if ok and done <= deadline:
+                f_stat[i] = 0
+                f_lat[i] = (done - (t0 + float(t_arr[i]))) * 1000.0
+                f_val[i] = (cnt, dsum, dxor)
+        c.close()
+
+    workers = [threading.Thread(target=plain_worker, args=(k,)) for k in (1, 2, 3)]
+    for w in workers:
+        w.start()
+    for w in workers:
+        w.join()
     fifo_wall = time.perf_counter() - t0
 
     both = [i for i in range(m) if s_stat[i] == 0 and f_stat[i] == 0]
@@ -787,14 +859,16 @@ def bench_serve(args):
                    "zipf_s": 1.2, "rate_per_s": args.rate, "arrival_window_s": args.serve_seconds,
                    "drain_s": args.drain, "mix": {"single": 0.80, "allpairs": 0.15, "crpq": 0.05},
                    "bulk_labels": "Zipf tail, ranks 9-16", "generation_s": round(gen_s, 1),
-                   "multi_automaton_launches": bool(args.batch_multi)},
-        "offered": m, "served": served, "fifo": fifo,
-        "fifo_requests_per_s": f_done / horizon,
-        "single_p99_fifo_over_served": ratio(fifo["single"]["p99_ms"], served["single"]["p99_ms"]),
-        "completed_ratio_served_over_fifo": ratio(s_done, f_done),
+                   "plain": "one FIFO worker per class (own context, stream and SM share), one request per call"},
+        "offered": m, "served": served, "plain": fifo,
+        "plain_requests_per_s": f_done / horizon,
+        "single_p99_plain_over_served": ratio(fifo["single"]["p99_ms"], served["single"]["p99_ms"]),
+        "single_completed_p99_plain_over_served": ratio(fifo["single"]["completed_p99_ms"],
+                                                        served["single"]["completed_p99_ms"]),
+        "completed_ratio_served_over_plain": ratio(s_done, f_done),
         "batches": batches, "batched_singles": carried, "submit_lag_s": round(submit_lag, 4),
         "equal_results": {"compared": len(both), "agree": agree},
-        "wall_s": {"served": round(served_wall, 2), "fifo": round(fifo_wall, 2)},
+        "wall_s": {"served": round(served_wall, 2), "plain": round(fifo_wall, 2)},
         "clocks": clocks,
     }
     print(json.dumps(out), flush=True)
@@ -814,6 +888,8 @@ def main():
         return bench_crpq(args)
     if args.workload == "serve":
         return bench_serve(args)
+    if args.workload == "plan":
+        return bench_plan(args)
     return ours(args, rank, world, local_rank)
 
 

@@ -196,6 +196,27 @@ int run_rpq(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, const uint32_t
 int run_rpq_range(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, uint32_t src_begin, uint32_t src_end,
                   uint32_t flags, rpq_result **out);
 
+/* ---- start-in-the-middle plan (Section 2.3 WavePlan, plan A3, executed as
+ *      A5 of Section 6.3: a sub-RPQ materialized, then joined) ------------- */
+
+/* Evaluates rho = alpha . beta (concatenation) from the listed start vertices
+ * (NULL / 0: all-pairs) by starting in the middle: R(beta) is first
+ * evaluated and materialized from every vertex at which an alpha path can
+ * end (every vertex if the empty word is in L(alpha), else those with an
+ * in-edge on a label entering an accepting state of alpha); its pairs
+ * become the edges of one extra label X of a temporary graph beside G's own
+ * edges; then alpha . X is evaluated over that graph by the ordinary
+ * traversal.  The result is the same relation as run_rpq of alpha . beta
+ * (Definition 1) -- the plan only changes the order of exploration.  flags:
+ * RPQ_MATERIALIZE or RPQ_COUNT_ONLY (optionally RPQ_FORCE_*).  result_stats
+ * counts the work of both phases (it differs from the forward plan's W).
+ * Device memory: R(beta) is held once as rows and once as a graph label.
+ * Errors: INVALID_ARG, OUT_OF_BUDGET, TOO_COMPLEX (the graph already uses
+ * RPQ_MAX_LABELS labels, or G's edges plus R(beta) exceed 2^32), CUDA,
+ * TIMEOUT. */
+int run_rpq_middle(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *alpha, const rpq_query *beta,
+                   const uint32_t *sources, uint32_t n_sources, uint32_t flags, rpq_result **out);
+
 /* ---- batched single-source RPQs (many expressions, one launch) ----------- */
 
 /* Evaluates n_queries single-source RPQs together: query i is the compiled
@@ -286,16 +307,26 @@ int run_crpq(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_vars, const int32_t *v
 /* ---- serving: continuous batching of mixed requests ----------------------- */
 
 /* A server evaluates RPQ and CRPQ requests that arrive over time against one
- * resident graph.  Two worker threads with their own CUDA streams share the
- * device (half of the SMs each for persistent grids): one batches every
- * waiting single-source request it can admit (up to max_batch, and only while
- * the admitted queries' visited bitmaps fit its memory share) into one launch,
- * so requests that arrive while a batch runs join the next one; the other
- * runs all-pairs requests and CRPQs, oldest first.  Replies carry the row
- * count and digest the standalone call would report (results are counted,
- * not kept) and the request's latencies.  The
- * graph, queries and atom queries must stay alive until their requests have
- * been waited for.  mem_budget_bytes = 0 uses 80% of the free device memory. */
+ * resident graph, with continuous batching.  Single-source requests enter a
+ * persistent serving launch through a ring in mapped host memory: at every
+ * BFS level boundary the launch admits as many waiting requests as it has
+ * free slots for (each slot holds one query's open-addressing visited set
+ * and result set, so admission is bounded by that device memory; max_batch
+ * caps the slots), and a query leaves its slot the level its frontier runs
+ * empty, with its row count and digest already accumulated, so requests that
+ * arrive while others are on the device join them and finish on their own
+ * schedule.  A query that grows past 4,096 product vertices leaves the launch
+ * and is finished, with every other such query waiting, in lane-mode
+ * launches (one automaton per bit lane).  All-pairs requests and CRPQs run on
+ * two bulk workers; each starts the oldest such request once its estimated
+ * device memory (traversal state, entry lists, emission scratch, sized by
+ * the lane groups it will use) fits what the running bulk requests leave of
+ * the bulk share of the budget.  The three kinds of work have their own
+ * streams and shares of the SMs, so they overlap on the device.  Replies
+ * carry the row count and digest the standalone call would report (results
+ * are counted, not kept) and the request's latencies.  The graph, queries
+ * and atom queries must stay alive until their requests have been waited
+ * for.  mem_budget_bytes = 0 uses 80% of the free device memory. */
 typedef struct rpq_server rpq_server;
 
 #define RPQ_REQ_SINGLE 1u   /* rho from one start vertex                    */
@@ -329,13 +360,15 @@ int rpq_server_submit(rpq_server *s, const rpq_request *req, uint64_t *ticket);
 /* Waits (timeout_s < 0: without limit) for the request and takes its reply;
  * TIMEOUT if it is not done in time (it stays queued). */
 int rpq_server_wait(rpq_server *s, uint64_t ticket, double timeout_s, rpq_reply *reply);
-/* Batched launches so far and the single-source requests they carried. */
+/* Serving launches so far and the single-source requests admitted into
+ * them (a request that arrives while a launch runs joins it, so launches can
+ * be far fewer than requests). */
 int rpq_server_stats(rpq_server *s, uint64_t *batches, uint64_t *batched_requests);
-/* Cancels every request not yet done: queued ones complete at once, and the
- * all-pairs request or CRPQ in service stops before its next launch (next
- * slice of start vertices, next batch of variable-0 values), all with status
- * RPQ_ERR_CANCELLED.  A single-source batch already on the device runs to its
- * end and keeps its replies.  The server stays usable. */
+/* Cancels every request not yet done: they complete at once with status
+ * RPQ_ERR_CANCELLED (the device finishes single-source requests it has
+ * already admitted and drops their replies), and the all-pairs request or
+ * CRPQ in service stops before its next launch (next slice of start
+ * vertices, next batch of variable-0 values).  The server stays usable. */
 int rpq_server_cancel(rpq_server *s);
 /* Finishes the queued requests, stops the workers and releases the server. */
 void rpq_server_destroy(rpq_server *s);

@@ -1018,6 +1018,158 @@ int run_rpq_range(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, uint32_t
   return run_sources(ctx, g, q, srcs, flags, out);
 }
 
+int run_rpq_middle(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *alpha, const rpq_query *beta,
+                   const uint32_t *sources, uint32_t n_sources, uint32_t flags, rpq_result **out) {
+  if (!ctx || !gr || !alpha || !beta || !out) return set_err(ctx, RPQ_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (!usable(ctx)) return RPQ_ERR_NO_DEVICE;
+  int rc = check_rpq_flags(ctx, flags);
+  if (rc) return rc;
+  if (flags & RPQ_REVERSE) return set_err(ctx, RPQ_ERR_INVALID_ARG, "RPQ_REVERSE is not a start-in-the-middle flag");
+  if (!sources && n_sources) return set_err(ctx, RPQ_ERR_INVALID_ARG, "sources NULL but n_sources > 0");
+  const DevGraph &g = gr->g;
+  const uint32_t n = g.n;
+  std::vector<uint32_t> srcs;
+  if (!sources) {
+    srcs.resize(n);
+    for (uint32_t v = 0; v < n; v++) srcs[v] = v;
+  } else {
+    srcs.assign(sources, sources + n_sources);
+    for (uint32_t s : srcs)
+      if (s >= n) return set_err(ctx, RPQ_ERR_INVALID_ARG, "source id out of range");
+    std::sort(srcs.begin(), srcs.end());
+    srcs.erase(std::unique(srcs.begin(), srcs.end()), srcs.end());
+  }
+  const HostQuery &ha = alpha->hq;
+  // the label X of the materialized pairs: above the graph's labels and alpha's
+  const uint32_t X = std::max(g.L, ha.d.n_labels);
+  if (X >= RPQ_MAX_LABELS) return set_err(ctx, RPQ_ERR_TOO_COMPLEX, "no label id left for the materialized pairs");
+  rpq_query qx;
+  {
+    std::string msg;
+    if ((rc = dfa_then_label(ha, X, &qx.hq, &msg))) return set_err(ctx, rc, msg);
+  }
+  rpq_result *res = new rpq_result;
+  res->ctx = ctx;
+  ctx->live++;
+  res->arity = 2;
+  res->materialized = (flags & RPQ_MATERIALIZE) != 0;
+  std::memset(&res->stats, 0, sizeof(res->stats));
+  cudaStream_t st = ctx->stream;
+  // 1. where alpha paths can end: every vertex when alpha accepts the empty
+  //    word, else the vertices with an in-edge on a label entering an
+  //    accepting state of alpha
+  std::vector<uint32_t> mid;
+  if (ha.d.n_states && (ha.d.final_mask & 1u)) {
+    mid.resize(n);
+    for (uint32_t v = 0; v < n; v++) mid[v] = v;
+  } else if (ha.d.n_states) {
+    unsigned long long lmask = 0;
+    for (uint32_t q = 0; q < ha.d.n_states; q++)
+      for (uint32_t l = 0; l < ha.d.n_labels && l < g.L; l++) {
+        const int32_t t = ha.next[(size_t)q * ha.d.n_labels + l];
+        if (t >= 0 && ((ha.d.final_mask >> t) & 1u)) lmask |= 1ull << l;
+      }
+    if (lmask) {
+      u32 *dall = nullptr;
+      unsigned char *dflag = nullptr;
+      std::vector<uint32_t> all(n);
+      for (uint32_t v = 0; v < n; v++) all[v] = v;
+      std::vector<unsigned char> flag(n);
+      if ((rc = dalloc(ctx, &dall, n)) || (rc = dalloc(ctx, &dflag, n))) {
+        dfree(ctx, dall, n);
+        free_result(res);
+        return rc;
+      }
+      cudaError_t e = cudaMemcpyAsync(dall, all.data(), 4ull * n, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = launch_source_filter(g.in_off, n, g.L, lmask, dall, n, dflag, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(flag.data(), dflag, n, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      dfree(ctx, dall, n);
+      dfree(ctx, dflag, n);
+      if (e != cudaSuccess) {
+        free_result(res);
+        return cuda_err(ctx, e, "middle vertices");
+      }
+      for (uint32_t v = 0; v < n; v++)
+        if (flag[v]) mid.push_back(v);
+    }
+  }
+  // 2. R(beta) from those vertices, materialized per start vertex
+  std::vector<RowChunk> chunks;
+  rpq_stats bst;
+  std::memset(&bst, 0, sizeof(bst));
+  if (!mid.empty() && (rc = rpq_rows_for_sources(ctx, gr, beta, mid, false, &chunks, &bst))) {
+    for (RowChunk &c : chunks) free_row_chunk(ctx, c);
+    free_result(res);
+    return rc;
+  }
+  uint64_t R = 0;
+  for (const RowChunk &c : chunks) R += c.rows;
+  // 3. a temporary graph: G's edges plus the pairs of R(beta) as label X
+  const uint64_t m2 = g.m + R;
+  if (m2 >= (1ull << 32)) {
+    for (RowChunk &c : chunks) free_row_chunk(ctx, c);
+    free_result(res);
+    return set_err(ctx, RPQ_ERR_TOO_COMPLEX, "the materialized pairs and the graph exceed 2^32 edges");
+  }
+  rpq_graph g2;
+  g2.ctx = ctx;
+  u32 *d_src = nullptr, *d_dst = nullptr;
+  uint16_t *d_lab = nullptr;
+  if ((rc = dalloc(ctx, &d_src, m2)) || (rc = dalloc(ctx, &d_dst, m2)) || (rc = dalloc(ctx, &d_lab, m2))) {
+    dfree(ctx, d_src, m2);
+    dfree(ctx, d_dst, m2);
+    for (RowChunk &c : chunks) free_row_chunk(ctx, c);
+    free_result(res);
+    return rc;
+  }
+  cudaError_t e = launch_csr_triples(g.out_off, g.out_col, n, g.L, d_src, d_dst, d_lab, st);
+  uint64_t base = g.m;
+  for (const RowChunk &c : chunks) {
+    if (e == cudaSuccess)
+      e = launch_chunk_triples(c.lanesrc, c.lane_off, c.n_lanes, c.dst, base, (uint16_t)X, d_src, d_dst, d_lab, st);
+    base += c.rows;
+  }
+  for (RowChunk &c : chunks) free_row_chunk(ctx, c);
+  std::string msg;
+  if (e == cudaSuccess) {
+    rc = build_graph(&g2.g, n, X + 1, m2, d_src, d_dst, d_lab, st, &msg);
+    if (rc) set_err(ctx, rc, msg);
+  } else {
+    rc = cuda_err(ctx, e, "middle-plan edge list");
+  }
+  dfree(ctx, d_src, m2);
+  dfree(ctx, d_dst, m2);
+  dfree(ctx, d_lab, m2);
+  // 4. alpha . X over the temporary graph, from the requested start vertices
+  if (rc == RPQ_OK) rc = eval_rpq(ctx, &g2, &qx, srcs, flags, res);
+  if (g2.g.out_off) cudaFreeAsync(g2.g.out_off, st);
+  if (g2.g.in_off) cudaFreeAsync(g2.g.in_off, st);
+  if (g2.g.out_col) cudaFreeAsync(g2.g.out_col, st);
+  if (g2.g.in_col) cudaFreeAsync(g2.g.in_col, st);
+  if (g2.g.hchunk_in) cudaFreeAsync(g2.g.hchunk_in, st);
+  if (g2.g.hchunk_out) cudaFreeAsync(g2.g.hchunk_out, st);
+  if (rc) {
+    free_result(res);
+    return rc;
+  }
+  // the plan's work: the materialization and the final traversal
+  rpq_stats &s2 = res->stats;
+  s2.product_edges += bst.product_edges;
+  s2.product_vertices += bst.product_vertices;
+  s2.levels += bst.levels;
+  s2.push_levels += bst.push_levels;
+  s2.pull_levels += bst.pull_levels;
+  s2.bfs_ms += bst.bfs_ms;
+  s2.emit_ms += bst.emit_ms;
+  s2.bfs_launches += bst.bfs_launches;
+  s2.launches += bst.launches + 2 + chunks.size();
+  s2.alg_bytes += bst.alg_bytes;
+  *out = res;
+  return RPQ_OK;
+}
+
 int run_crpq(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_vars, const int32_t *var_label, const crpq_atom *atoms,
              uint32_t n_atoms, const uint32_t *restrict0, uint32_t n_restrict0, uint32_t flags, rpq_result **out) {
   if (!ctx || !g || !atoms || !out) return set_err(ctx, RPQ_ERR_INVALID_ARG, "null argument");

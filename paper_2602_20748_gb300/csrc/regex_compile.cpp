@@ -510,4 +510,29 @@ int compile_regex(const char *regex, const char *const *names, uint32_t n_names,
   return RPQ_OK;
 }
 
+// The minimal DFA of L(alpha) . x for a label x that alpha does not use: from
+// every accepting state of alpha an x-edge leads to one new accepting state,
+// and alpha's own accepting states stop accepting.
+int dfa_then_label(const HostQuery &alpha, uint32_t x, HostQuery *out, std::string *msg) {
+  const int Q = (int)alpha.d.n_states;
+  const int A0 = (int)alpha.d.n_labels;
+  if ((int)x < A0 || x >= RPQ_MAX_LABELS) {
+    *msg = "the extra label must be above alpha's labels and below RPQ_MAX_LABELS";
+    return RPQ_ERR_INVALID_ARG;
+  }
+  const int A = (int)x + 1, F = Q;
+  std::vector<int> raw((size_t)(Q + 1) * A, -1);
+  std::vector<char> acc(Q + 1, 0);
+  for (int q = 0; q < Q; q++) {
+    for (int c = 0; c < A0; c++) raw[(size_t)q * A + c] = alpha.next[(size_t)q * A0 + c];
+    if ((alpha.d.final_mask >> q) & 1u) raw[(size_t)q * A + x] = F;
+  }
+  acc[F] = 1;
+  HostQuery hq;
+  hq.has_rev = false;
+  const int rc = finish_dfa(Q + 1, A, raw, acc, &hq.d, &hq.next, msg);
+  if (rc == RPQ_OK) *out = hq;
+  return rc;
+}
+
 }  // namespace rpq

@@ -44,6 +44,9 @@ struct HostQuery {
 
 // Parses and compiles; returns RPQ_OK or an error code with *msg set.
 int compile_regex(const char *regex, const char *const *names, uint32_t n_names, HostQuery *out, std::string *msg);
+// The minimal DFA of L(alpha) followed by one edge of label x (x above every
+// label alpha uses).
+int dfa_then_label(const HostQuery &alpha, uint32_t x, HostQuery *out, std::string *msg);
 
 // ---------------------------------------------------------------------------
 // Device-resident graph: one CSR per edge label over the full id space, for
@@ -259,6 +262,15 @@ cudaError_t exclusive_scan_u32_to_u64(const uint32_t *in, unsigned long long *ou
                                       unsigned long long *total, unsigned long long *tmp, cudaStream_t st);
 cudaError_t exclusive_scan_u64(const unsigned long long *in, unsigned long long *out, size_t n,
                                unsigned long long *total, unsigned long long *tmp, cudaStream_t st);
+
+// Start-in-the-middle plan: (src, dst, label) triples of the out-CSR (triple
+// e = out_col index e), and of a materialized chunk's rows with label x from
+// position base.
+cudaError_t launch_csr_triples(const uint32_t *off, const uint32_t *col, uint32_t n, uint32_t L, uint32_t *src,
+                               uint32_t *dst, uint16_t *lab, cudaStream_t st);
+cudaError_t launch_chunk_triples(const uint32_t *lanesrc, const unsigned long long *lane_off, uint32_t n_lanes,
+                                 const uint32_t *cdst, unsigned long long base, uint16_t x, uint32_t *src,
+                                 uint32_t *dst, uint16_t *lab, cudaStream_t st);
 
 // Graph construction.  Returns RPQ_OK or an error code with *msg set.
 int build_graph(DevGraph *g, uint32_t n, uint32_t L, uint64_t m, const uint32_t *d_src, const uint32_t *d_dst,

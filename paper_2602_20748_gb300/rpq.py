@@ -227,6 +227,20 @@ def run_rpq(ctx: Context, g: Graph, q: Query, sources=None, flags: int = RPQ_MAT
     return Result(ctx, h)
 
 
+_lib.run_rpq_middle.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_u32, c_u32, P(c_void_p)]
+EXPORTED += ["run_rpq_middle"]
+
+
+def run_rpq_middle(ctx: Context, g: Graph, alpha: Query, beta: Query, sources=None,
+                   flags: int = RPQ_MATERIALIZE) -> Result:
+    """run_rpq_middle: alpha . beta by the start-in-the-middle plan."""
+    s = None if sources is None else np.ascontiguousarray(sources, dtype=np.uint32)
+    h = c_void_p()
+    ctx.check(_lib.run_rpq_middle(ctx.h, g.h, alpha.h, beta.h, _ptr(s), 0 if s is None else len(s), flags,
+                                  ctypes.byref(h)))
+    return Result(ctx, h)
+
+
 def run_rpq_range(ctx: Context, g: Graph, q: Query, src_begin: int, src_end: int,
                   flags: int = RPQ_MATERIALIZE) -> Result:
     h = c_void_p()
