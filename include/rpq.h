@@ -111,6 +111,8 @@ int rpq_set_stream(rpq_ctx *ctx, void *cuda_stream);
  * name or a value out of range):
  *   "alpha"        top-down is chosen for a level when alpha * its bytes are
  *                  below the bottom-up bytes (default 16)
+ *   "lane_alpha"   the same for lane-mode launches (one automaton per lane;
+ *                  default 2)
  *   "grid_share"   fraction (0, 1] of the SMs the persistent traversal grids
  *                  occupy (default 1; 0.5 lets two contexts' searches run
  *                  side by side)
@@ -120,10 +122,18 @@ int rpq_set_stream(rpq_ctx *ctx, void *cuda_stream);
  *                  which a query leaves the shared launch (0: never)
  *   "batch_streams" helper contexts evaluating evicted queries side by
  *                  side, 1 .. 16 (default 4)
- *   "batch_multi"  1: evicted queries of small automaton groups share
- *                  multi-automaton launches; 0 (default): one launch per
- *                  automaton (the same throughput on 4,096 mixed queries,
- *                  lower latency per batch when serving)
+ *   "batch_lanes"  run_rpq_batch with RPQ_PER_QUERY: evicted queries run in
+ *                  lane-mode launches of up to this many lanes, one automaton
+ *                  per lane, 1 .. 4096 (default 4096); 0: one bit-sliced
+ *                  launch per distinct automaton instead
+ *   "batch_direct" 1: every query of such a batch goes straight to the
+ *                  lane-mode launches (no shared per-query launch first)
+ *   "batch_hash"   1: the shared per-query launch keeps an open-addressing
+ *                  visited set (and result set) of 2 x batch_evict slots per
+ *                  query instead of dense per-state bitmaps; rows are counted
+ *                  as they are found, and a full table evicts its query
+ *   "batch_multi"  with batch_lanes = 0: evicted queries of small automaton
+ *                  groups share multi-automaton launches
  * A server's workers take the tunables of the context it was created on. */
 int rpq_set_option(rpq_ctx *ctx, const char *name, double value);
 /* Reads a tunable set by rpq_set_option or chosen by rpq_autotune_batch
@@ -231,8 +241,10 @@ int run_rpq_middle(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *alpha, con
  * them (result_query_stats), and result_info totals those summaries.  In
  * that mode a query whose product graph grows past a threshold (option
  * "batch_evict", product vertices; default 65,536) leaves the shared launch,
- * and such queries are then evaluated together by the multi-source engine,
- * one bit-sliced traversal per distinct automaton with a lane per query.
+ * and such queries are then evaluated together by the multi-source engine in
+ * lane-mode launches: one bit lane per query, each lane with its own
+ * automaton (option "batch_lanes"; "batch_direct" sends every query there).
+ * result_query_time gives each query's completion time.
  * Block size, queries per launch and the threshold come from the last
  * rpq_autotune_batch on the context (defaults otherwise).
  * Errors: INVALID_ARG, OUT_OF_BUDGET, CUDA, TIMEOUT. */
@@ -240,11 +252,15 @@ int run_rpq_batch(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_queries, const rp
                   const uint32_t *sources, uint32_t flags, rpq_result **out);
 
 /* Times run_rpq_batch (RPQ_PER_QUERY) on a sample of the given batch (its
- * first 1,024 queries) for each candidate block size (256, 512 threads),
- * eviction threshold (2^12, 2^14, 2^16, 2^18 product vertices) and number of
- * side-by-side evaluations of evicted queries (4, 8), keeps the
- * fastest on the context for later run_rpq_batch calls and reports it (out
- * pointers may be NULL; queries per launch is reported as set).
+ * first 1,024 queries) for each candidate visited-set representation and
+ * schedule -- every query straight to lane-mode launches (bit-sliced visited
+ * words, one automaton per lane), or a shared per-query launch first with
+ * dense bitmaps or open-addressing hash tables, block size 256 or 512 and
+ * eviction threshold 2^10, 2^12 or 2^14 product vertices, the evicted
+ * queries then in lane-mode launches -- keeps the fastest on the context for
+ * later run_rpq_batch calls (options batch_direct, batch_hash, batch_evict,
+ * batch_threads) and reports it (out pointers may be NULL; queries per launch
+ * is reported as set).
  * Errors: as run_rpq_batch. */
 int rpq_autotune_batch(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_queries, const rpq_query *const *queries,
                        const uint32_t *sources, uint32_t *threads_out, uint32_t *queries_per_launch_out);

@@ -58,6 +58,7 @@ struct rpq_ctx {
   int bpsm_lane[2] = {0, 0};  // and for the per-lane-automata kernel, NW = 1, 4 (set on first use)
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   float alpha = 16.0f;
+  float lane_alpha = 2.0f;  // the same trade-off for lane-mode launches
   uint64_t time_limit_ns = 20ull * 1000 * 1000 * 1000;
   uint32_t max_groups = 16;
   bool trace = false;    // print per-level timings of each traversal (RPQ_TRACE=1)
@@ -783,6 +784,8 @@ int rpq_set_option(rpq_ctx *ctx, const char *name, double value) {
   const std::string n(name);
   if (n == "alpha" && value > 0) {
     ctx->alpha = (float)value;
+  } else if (n == "lane_alpha" && value > 0) {
+    ctx->lane_alpha = (float)value;
   } else if (n == "grid_share" && value > 0 && value <= 1) {
     ctx->grid_share = value;
   } else if (n == "max_groups" && value >= 1 && value <= 16) {
@@ -812,6 +815,8 @@ int rpq_get_option(const rpq_ctx *ctx, const char *name, double *value) {
   const std::string n(name);
   if (n == "alpha")
     *value = ctx->alpha;
+  else if (n == "lane_alpha")
+    *value = ctx->lane_alpha;
   else if (n == "grid_share")
     *value = ctx->grid_share;
   else if (n == "max_groups")
@@ -1386,6 +1391,7 @@ bool ctx_trace(rpq_ctx *ctx) { return ctx->trace; }
 BatchTuning ctx_batch_tuning(rpq_ctx *ctx) { return ctx->batch; }
 void ctx_copy_tunables(rpq_ctx *to, const rpq_ctx *from) {
   to->alpha = from->alpha;
+  to->lane_alpha = from->lane_alpha;
   to->time_limit_ns = from->time_limit_ns;
   to->spill_cap = from->spill_cap;
   to->batch = from->batch;
@@ -1906,6 +1912,7 @@ static int lane_launch(rpq_ctx *ctx, const rpq_graph *gr, const std::vector<Lane
   p.alpha = ctx->alpha;
   p.time_limit_ns = ctx->time_limit_ns;
   p.q = un;
+  p.alpha = ctx->lane_alpha;
   p.la_out_begin = reinterpret_cast<const unsigned short *>(dt + o_ob);
   p.la_trans = reinterpret_cast<const unsigned int *>(dt + o_tr);
   p.la_mask = reinterpret_cast<const unsigned long long *>(dt + o_mask);

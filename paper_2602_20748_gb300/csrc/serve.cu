@@ -63,7 +63,7 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
 
 // SM shares of the three kinds of work (they sum below 1, so that the
 // cooperative launches of all three fit on the device at once)
-constexpr double SHARE_SERVE = 0.35, SHARE_LANE = 0.4, SHARE_BULK = 0.1;
+constexpr double SHARE_SERVE = 0.2, SHARE_LANE = 0.55, SHARE_BULK = 0.1;
 constexpr int BULK_WORKERS = 2;
 constexpr uint32_t SERVE_HASH_BITS = 13;  // 8,192-slot visited and result sets per query
 constexpr uint64_t SERVE_EVICT_AT = 4096;  // product vertices before a query moves to lane mode

@@ -39,6 +39,12 @@ def test_reverse_is_transposed_forward(ctx, case):
     rev = rpq.fetch_pairs(rpq.run_rpq(ctx, g, q, targets, flags=rpq.RPQ_MATERIALIZE | rpq.RPQ_REVERSE))
     want = sorted((int(d), int(s)) for s, d in fwd.tolist() if d in set(targets.tolist()))
     assert [tuple(r) for r in rev.tolist()] == want, regex
+    # and against the oracle directly: R_G(rho) restricted to the targets, transposed
+    og = oracle.Graph(n, L, src, dst, lab)
+    orows = oracle.rpq(og, regex).rows
+    tset = set(targets.tolist())
+    want_o = sorted((int(d), int(s)) for s, d in orows.tolist() if d in tset)
+    assert [tuple(r) for r in rev.tolist()] == want_o, regex
 
 
 def test_handles_freed_after_context(ctx):
