@@ -380,6 +380,19 @@ int rpq_server_wait(rpq_server *s, uint64_t ticket, double timeout_s, rpq_reply 
  * them (a request that arrives while a launch runs joins it, so launches can
  * be far fewer than requests). */
 int rpq_server_stats(rpq_server *s, uint64_t *batches, uint64_t *batched_requests);
+/* Counters of a server (all cumulative). */
+typedef struct {
+  uint64_t launches;       /* serving launches (a new one starts when requests
+                              arrive while none is running)                   */
+  uint64_t admitted;       /* single-source requests admitted into them       */
+  uint64_t lane_requests;  /* of those, finished in lane-mode launches after
+                              outgrowing the serving launch                   */
+  uint64_t lane_launches;  /* lane-mode launches                              */
+  uint32_t graph;          /* 1: serving launches replay a CUDA graph captured
+                              at creation; 0: they are issued directly        */
+  uint32_t slots;          /* queries the serving launch holds at once        */
+} rpq_server_counters;
+int rpq_server_info(rpq_server *s, rpq_server_counters *out);
 /* Cancels every request not yet done: they complete at once with status
  * RPQ_ERR_CANCELLED (the device finishes single-source requests it has
  * already admitted and drops their replies), and the all-pairs request or

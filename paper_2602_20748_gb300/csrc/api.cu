@@ -59,6 +59,7 @@ struct rpq_ctx {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   float alpha = 16.0f;
   float lane_alpha = 2.0f;  // the same trade-off for lane-mode launches
+  unsigned pull_dynamic = 1;  // bottom-up vertex chunks from a cursor
   uint64_t time_limit_ns = 20ull * 1000 * 1000 * 1000;
   uint32_t max_groups = 16;
   bool trace = false;    // print per-level timings of each traversal (RPQ_TRACE=1)
@@ -435,6 +436,7 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
     p.nblocks = (unsigned)blocks;
     p.force = force;
     p.alpha = ctx->alpha;
+    p.pull_dynamic = ctx->pull_dynamic;
     p.time_limit_ns = ctx->time_limit_ns;
     p.q = qd;
 
@@ -576,9 +578,10 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
       std::fprintf(stderr, "[rpq trace] G=%u Q=%u levels=%llu W=%llu\n", Gb, Q, (unsigned long long)hctl.levels,
                    (unsigned long long)hctl.stats[ST_W]);
       for (uint32_t l = 0; l < nl; l++)
-        std::fprintf(stderr, "[rpq trace]   level %2u %s n=%10llu mf=%12llu %9.3f ms\n", l,
+        std::fprintf(stderr, "[rpq trace]   level %2u %s n=%10llu mf=%12llu %9.3f ms (commit %7.3f ms)\n", l,
                      hctl.trace_mode[l] == 1 ? "push" : "pull", (unsigned long long)hctl.trace_n[l],
-                     (unsigned long long)hctl.trace_mf[l], (hctl.trace_t[l + 1] - hctl.trace_t[l]) * 1e-6);
+                     (unsigned long long)hctl.trace_mf[l], (hctl.trace_t[l + 1] - hctl.trace_t[l]) * 1e-6,
+                     hctl.trace_c[l] ? (hctl.trace_t[l + 1] - hctl.trace_c[l]) * 1e-6 : 0.0);
     }
     ctx->stamp += (uint32_t)hctl.levels + 3;
 
@@ -786,6 +789,8 @@ int rpq_set_option(rpq_ctx *ctx, const char *name, double value) {
     ctx->alpha = (float)value;
   } else if (n == "lane_alpha" && value > 0) {
     ctx->lane_alpha = (float)value;
+  } else if (n == "pull_dynamic" && (value == 0 || value == 1)) {
+    ctx->pull_dynamic = value != 0 ? 1u : 0u;
   } else if (n == "grid_share" && value > 0 && value <= 1) {
     ctx->grid_share = value;
   } else if (n == "max_groups" && value >= 1 && value <= 16) {
@@ -817,6 +822,8 @@ int rpq_get_option(const rpq_ctx *ctx, const char *name, double *value) {
     *value = ctx->alpha;
   else if (n == "lane_alpha")
     *value = ctx->lane_alpha;
+  else if (n == "pull_dynamic")
+    *value = ctx->pull_dynamic;
   else if (n == "grid_share")
     *value = ctx->grid_share;
   else if (n == "max_groups")
@@ -1392,6 +1399,7 @@ BatchTuning ctx_batch_tuning(rpq_ctx *ctx) { return ctx->batch; }
 void ctx_copy_tunables(rpq_ctx *to, const rpq_ctx *from) {
   to->alpha = from->alpha;
   to->lane_alpha = from->lane_alpha;
+  to->pull_dynamic = from->pull_dynamic;
   to->time_limit_ns = from->time_limit_ns;
   to->spill_cap = from->spill_cap;
   to->batch = from->batch;
@@ -1682,6 +1690,7 @@ int rpq_lane_stats_multi(rpq_ctx *ctx, const rpq_graph *gr, const std::vector<Mu
   p.nblocks = (unsigned)blocks;
   p.force = 0;
   p.alpha = ctx->alpha;
+  p.pull_dynamic = ctx->pull_dynamic;
   p.time_limit_ns = ctx->time_limit_ns;
   p.q = un;
   p.qg = d_desc;
@@ -1910,6 +1919,7 @@ static int lane_launch(rpq_ctx *ctx, const rpq_graph *gr, const std::vector<Lane
   p.nblocks = (unsigned)blocks;
   p.force = 0;
   p.alpha = ctx->alpha;
+  p.pull_dynamic = ctx->pull_dynamic;
   p.time_limit_ns = ctx->time_limit_ns;
   p.q = un;
   p.alpha = ctx->lane_alpha;

@@ -1048,6 +1048,8 @@ struct ServeEngine {
   bool running = false;
   int blocks = 0;
   uint64_t launches = 0;
+  ServeParams params;                  // fixed for the engine's lifetime
+  cudaGraphExec_t graph = nullptr;     // the captured relaunch sequence (nullptr: launched directly)
 };
 
 uint64_t serve_engine_bytes(uint32_t slots, uint32_t hash_bits) {
@@ -1074,6 +1076,88 @@ static int serve_reset_state(ServeEngine *e) {
       (err = cudaMemcpyAsync(e->st.p, &h, sizeof(h), cudaMemcpyHostToDevice, st)) || (err = cudaStreamSynchronize(st)))
     return berr(e->ctx, err, "serving state reset");
   return RPQ_OK;
+}
+
+// The serving launch's parameters: the engine's buffers, fixed for its life.
+static void serve_params(ServeEngine *e) {
+  ServeParams &sp = e->params;
+  std::memset(&sp, 0, sizeof(sp));
+  const DevGraph &dg = graph_dev(e->g);
+  BatchParams &p = sp.b;
+  p.out_off = dg.out_off;
+  p.out_col = dg.out_col;
+  p.n = dg.n;
+  p.L = dg.L;
+  p.nq = e->slots;
+  p.qd = e->slot_qd.p;
+  p.vis_off = nullptr;
+  p.srcs = e->slot_src.p;
+  p.vis = e->vis.p;
+  p.vis_words = (uint64_t)e->slots << e->hbits;
+  p.m = dg.m;
+  p.wps = 0;
+  p.list0 = e->list0.p;
+  p.list1 = e->list1.p;
+  p.list_cap = e->list_cap;
+  p.spill = e->spill.p;
+  p.spill_cap = SPILL_CAP;
+  p.ctl = e->ctl.p;
+  p.nblocks = (unsigned)e->blocks;
+  p.time_limit_ns = ctx_time_limit_ns(e->ctx);
+  p.qn = e->qn.p;
+  p.qw = e->qw.p;
+  p.evicted = e->evicted.p;
+  p.evict_at = e->evict_at;
+  p.append_seg = APPEND_SEG;
+  p.hash_bits = e->hbits;
+  p.rtab = e->rtab.p;
+  p.qstats = e->qstats.p;
+  p.active = e->active.p;
+  sp.sh = static_cast<ServeShared *>(e->sh_d);
+  sp.reqs = static_cast<const ServeReq *>(e->reqs_d);
+  sp.dones = static_cast<ServeDone *>(e->dones_d);
+  sp.ring = SERVE_RING;
+  sp.admit_max = SERVE_ADMIT_MAX;
+  sp.slot_src = e->slot_src.p;
+  sp.slot_qd = e->slot_qd.p;
+  sp.free_stack = e->free_stack.p;
+  sp.busy = e->busy.p;
+  sp.tickets = e->tickets.p;
+  sp.st = e->st.p;
+}
+
+// One relaunch: the control block cleared, then the persistent kernel.
+static cudaError_t serve_issue(ServeEngine *e, cudaStream_t st) {
+  void *args[] = {(void *)&e->params};
+  cudaError_t err = cudaMemsetAsync(e->ctl.p, 0, sizeof(BfsCtl), st);
+  if (err == cudaSuccess)
+    err = cudaLaunchCooperativeKernel((void *)serve_kernel, e->blocks, SERVE_THREADS, args, 0, st);
+  return err;
+}
+
+// Captures the relaunch sequence in a CUDA graph (instantiated once, launched
+// on every relaunch).  If the runtime refuses the capture the engine keeps
+// launching directly.
+static void serve_capture(ServeEngine *e) {
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t err = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (err == cudaSuccess) {
+    const cudaError_t issued = serve_issue(e, cs);
+    err = cudaStreamEndCapture(cs, &graph);
+    if (issued != cudaSuccess) err = issued;
+  }
+  if (err == cudaSuccess && graph) err = cudaGraphInstantiate(&e->graph, graph, 0);
+  if (err != cudaSuccess) {
+    e->graph = nullptr;
+    cudaGetLastError();
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
 }
 
 int serve_engine_create(rpq_ctx *ctx, const rpq_graph *g, uint32_t slots, uint32_t hash_bits, uint64_t evict_at,
@@ -1139,6 +1223,8 @@ int serve_engine_create(rpq_ctx *ctx, const rpq_graph *g, uint32_t slots, uint32
     serve_engine_destroy(e);
     return rc;
   }
+  serve_params(e);
+  serve_capture(e);
   *out = e;
   return RPQ_OK;
 }
@@ -1148,6 +1234,7 @@ void serve_engine_destroy(ServeEngine *e) {
   if (e->running) cudaEventSynchronize(e->done_ev);
   cudaStreamSynchronize(ctx_stream(e->ctx));
   if (e->done_ev) cudaEventDestroy(e->done_ev);
+  if (e->graph) cudaGraphExecDestroy(e->graph);
   if (e->sh) cudaFreeHost(e->sh);
   delete e;  // device buffers return to the context's budget
 }
@@ -1215,60 +1302,15 @@ int serve_engine_kick(ServeEngine *e, std::vector<uint64_t> *lost) {
   }
   if (serve_engine_waiting(e) == 0) return RPQ_OK;
   cudaStream_t st = ctx_stream(e->ctx);
-  ServeParams sp;
-  std::memset(&sp, 0, sizeof(sp));
-  const DevGraph &dg = graph_dev(e->g);
-  BatchParams &p = sp.b;
-  p.out_off = dg.out_off;
-  p.out_col = dg.out_col;
-  p.n = dg.n;
-  p.L = dg.L;
-  p.nq = e->slots;
-  p.qd = e->slot_qd.p;
-  p.vis_off = nullptr;
-  p.srcs = e->slot_src.p;
-  p.vis = e->vis.p;
-  p.vis_words = (uint64_t)e->slots << e->hbits;
-  p.m = dg.m;
-  p.wps = 0;
-  p.list0 = e->list0.p;
-  p.list1 = e->list1.p;
-  p.list_cap = e->list_cap;
-  p.spill = e->spill.p;
-  p.spill_cap = SPILL_CAP;
-  p.ctl = e->ctl.p;
-  p.nblocks = (unsigned)e->blocks;
-  p.time_limit_ns = ctx_time_limit_ns(e->ctx);
-  p.qn = e->qn.p;
-  p.qw = e->qw.p;
-  p.evicted = e->evicted.p;
-  p.evict_at = e->evict_at;
-  p.append_seg = APPEND_SEG;
-  p.hash_bits = e->hbits;
-  p.rtab = e->rtab.p;
-  p.qstats = e->qstats.p;
-  p.active = e->active.p;
-  sp.sh = static_cast<ServeShared *>(e->sh_d);
-  sp.reqs = static_cast<const ServeReq *>(e->reqs_d);
-  sp.dones = static_cast<ServeDone *>(e->dones_d);
-  sp.ring = SERVE_RING;
-  sp.admit_max = SERVE_ADMIT_MAX;
-  sp.slot_src = e->slot_src.p;
-  sp.slot_qd = e->slot_qd.p;
-  sp.free_stack = e->free_stack.p;
-  sp.busy = e->busy.p;
-  sp.tickets = e->tickets.p;
-  sp.st = e->st.p;
-  void *args[] = {(void *)&sp};
-  cudaError_t err = cudaMemsetAsync(e->ctl.p, 0, sizeof(BfsCtl), st);
-  if (err == cudaSuccess)
-    err = cudaLaunchCooperativeKernel((void *)serve_kernel, e->blocks, SERVE_THREADS, args, 0, st);
+  cudaError_t err = e->graph ? cudaGraphLaunch(e->graph, st) : serve_issue(e, st);
   if (err == cudaSuccess) err = cudaEventRecord(e->done_ev, st);
   if (err != cudaSuccess) return berr(e->ctx, err, "serving launch");
   e->running = true;
   e->launches++;
   return RPQ_OK;
 }
+
+bool serve_engine_graphed(ServeEngine *e) { return e->graph != nullptr; }
 
 int batch_run(rpq_ctx *ctx, const rpq_graph *g, uint32_t nq, const rpq_query *const *queries,
               const uint32_t *sources, bool materialize, const BatchTuning &tun, BatchOut *out) {

@@ -94,6 +94,8 @@ void serve_engine_poll(ServeEngine *e, std::vector<ServeReply> *out);
 // then lost: *lost gets their tickets, and the engine is reset).
 int serve_engine_kick(ServeEngine *e, std::vector<uint64_t> *lost);
 bool serve_engine_running(ServeEngine *e);
+// Whether relaunches go through a captured CUDA graph.
+bool serve_engine_graphed(ServeEngine *e);
 // Launches so far and levels run.
 void serve_engine_counters(ServeEngine *e, uint64_t *launches, uint64_t *admitted);
 

@@ -700,8 +700,17 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
   // coalesced reads of the in-row offsets, the target states into which
   // vertex c0 + i has a light in-row on an active transition; only those
   // (vertex, state) pairs are then visited, VPW vertices at a time (their
-  // offsets are in L1 by then).
-  for (u64 c0 = warp * 32; c0 < n; c0 += n_warps * 32) {
+  // offsets are in L1 by then).  With pull_dynamic the chunks are taken from
+  // a cursor (the level's list cursor, unused by bottom-up levels), so a
+  // warp whose chunks had little work takes more of them; else chunk k goes
+  // to warp k mod warps.
+  u64 c0 = warp * 32;
+  if (p.pull_dynamic) {
+    u64 t = 0;
+    if (lane == 0) t = atomicAdd(&p.ctl->cursor[cur], 32ull);
+    c0 = __shfl_sync(FULL_MASK, t, 0);
+  }
+  for (; c0 < n;) {
     u32 qmask = 0, hmask = 0;  // hmask: states with a long in-row (its chunks also produce)
     if (c0 + lane < n) {
       const u32 v = (u32)(c0 + lane);
@@ -786,6 +795,13 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
       pull_finish<NW, PER>(p, app, FB, nlist, nxt, q2, w, stamp, li, lane_on && work, my_g, ((vh >> q2) & 1u) != 0,
                            vis, acc);
     }
+    }
+    if (p.pull_dynamic) {
+      u64 t = 0;
+      if (lane == 0) t = atomicAdd(&p.ctl->cursor[cur], 32ull);
+      c0 = __shfl_sync(FULL_MASK, t, 0);
+    } else {
+      c0 += n_warps * 32;
     }
   }
 
@@ -1027,6 +1043,7 @@ __global__ void __launch_bounds__(BFS_THREADS, 4) msbfs_kernel(const __grid_cons
       const u64 sparse_cap = (u64)p.n * p.Q;
       const bool set_bits = p.fbits && n_next * 4 < sparse_cap;
       const bool clear_bits = p.fbits && (level == 0 || n_cur * 4 < sparse_cap);
+      if (tracer && level < (u32)TRACE_LEVELS) c->trace_c[level] = globaltimer_ns();
       commit_phase<NW, AM>(p, lp, nxt, n_cur, set_bits, clear_bits, stat);
     }
     if (!grid_barrier(c, p.nblocks, p.time_limit_ns)) return;

@@ -121,6 +121,7 @@ struct BfsCtl {
   unsigned long long trace_n[TRACE_LEVELS];
   unsigned int trace_mode[TRACE_LEVELS];
   unsigned long long trace_mf[TRACE_LEVELS];  // frontier out-edges (top-down cost)
+  unsigned long long trace_c[TRACE_LEVELS];   // start time (ns) of each level's commit phase
 };
 
 // A top-down row longer than SPILL_EDGES is cut into chunks of SPILL_EDGES
@@ -186,6 +187,7 @@ struct BfsParams {
   BfsCtl *ctl;
   unsigned int stamp_base;     // claim stamps continue across launches
   unsigned int nblocks;
+  unsigned int pull_dynamic;   // bottom-up levels take vertex chunks from a cursor (else round-robin)
   int force;                   // 0 auto, 1 push only, 2 pull only
   float alpha;                 // push if alpha * push_cost < pull_cost
   unsigned long long time_limit_ns;

@@ -77,6 +77,7 @@ struct rpq_server {
   const rpq_graph *g = nullptr;
   rpq::ServeEngine *eng = nullptr;
   uint32_t lanes = 4096;
+  uint32_t slots = 0;
   uint64_t bulk_budget = 0, bulk_reserved = 0;
   std::mutex mu;
   std::condition_variable cv_work, cv_lane, cv_bulk, cv_done;
@@ -325,6 +326,7 @@ int rpq_server_create(rpq_ctx *ctx, const rpq_graph *g, uint64_t mem_budget_byte
   const uint64_t lane_b = (budget - std::min(budget, serve_b)) / 2;
   s->bulk_budget = budget - std::min(budget, serve_b + lane_b);
   s->lanes = 4096;
+  s->slots = slots;
   int rc = RPQ_OK;
   for (auto &st : s->streams)
     if (rc == RPQ_OK && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) rc = RPQ_ERR_CUDA;
@@ -459,6 +461,20 @@ int rpq_server_stats(rpq_server *s, uint64_t *batches, uint64_t *batched_request
   }
   if (batches) *batches = launches;
   if (batched_requests) *batched_requests = admitted;
+  return RPQ_OK;
+}
+
+int rpq_server_info(rpq_server *s, rpq_server_counters *out) {
+  if (!s || !out) return RPQ_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    rpq::serve_engine_counters(s->eng, &out->launches, &out->admitted);
+  }
+  out->lane_requests = s->lane_requests;
+  out->lane_launches = s->lane_launches;
+  out->graph = rpq::serve_engine_graphed(s->eng) ? 1u : 0u;
+  out->slots = s->slots;
   return RPQ_OK;
 }
 

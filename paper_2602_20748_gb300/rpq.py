@@ -391,6 +391,15 @@ def rpq_get_option(ctx: Context, name: str) -> float:
     return v.value
 
 
+class rpq_server_counters(ctypes.Structure):
+    _fields_ = [("launches", c_u64), ("admitted", c_u64), ("lane_requests", c_u64), ("lane_launches", c_u64),
+                ("graph", c_u32), ("slots", c_u32)]
+
+
+_lib.rpq_server_info.argtypes = [c_void_p, P(rpq_server_counters)]
+EXPORTED += ["rpq_server_info"]
+
+
 class Server:
     """rpq_server_*: continuous batching of mixed requests on one graph."""
 
@@ -431,6 +440,15 @@ class Server:
     def cancel(self):
         """Cancels every request not yet done (status RPQ_ERR_CANCELLED)."""
         _lib.rpq_server_cancel(self.h)
+
+    def info(self) -> dict:
+        """rpq_server_info: launches, admitted, lane_requests, lane_launches,
+        graph (1 = serving launches replay a captured CUDA graph), slots."""
+        c = rpq_server_counters()
+        rc = _lib.rpq_server_info(self.h, ctypes.byref(c))
+        if rc != 0:
+            raise RPQError(rc, "server info failed")
+        return {k: getattr(c, k) for k, _ in c._fields_}
 
     def stats(self):
         b, r = c_u64(), c_u64()

@@ -77,6 +77,8 @@ def test_served_results_equal_oracle_alone_and_in_the_mix(setup):
     # every single-source request passed through the serving launch, and they
     # shared launches (a request that arrives while one runs joins it)
     assert admitted == len(regexes) and launches < len(regexes)
+    info = server.info()
+    assert info["launches"] == launches and info["admitted"] == admitted and info["graph"] == 1
     server.close()
     # alone: one request at a time
     server = rpq.Server(ctx, g, max_batch=64)
@@ -114,6 +116,8 @@ def test_stream_with_evictions_matches_oracle():
         assert rep["status"] == 0
         assert (rep["count"], rep["digest_sum"], rep["digest_xor"]) == oracle.pair_digest(want.rows), i
     assert evicted_possible > 0
+    info = server.info()
+    assert info["lane_requests"] >= evicted_possible and info["lane_launches"] > 0
     server.close()
 
 
