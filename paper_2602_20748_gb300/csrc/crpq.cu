@@ -230,6 +230,98 @@ __global__ void digest_rows(const ColPtrs cols, u32 arity, u64 n, u64 *__restric
   }
 }
 
+// Count-only binding of the last variable, fused: work item t is chunk c of
+// tuple i's generating row (items numbered by the exclusive scan coff of the
+// tuples' chunk counts); a warp takes one item, looks up the rows of the
+// tuple's constraints once, and for each of the chunk's candidates tests the
+// vertex label and every other constraint by binary search, counting and
+// digesting the survivors in place (no candidate arrays, no compaction, no
+// second pass over the tuples).  The tuples are distinct because every bound
+// value of a partial tuple and every candidate of a sorted row is.
+constexpr u32 LAST_CHUNK = 256;
+
+struct LastParams {
+  StepParams p;
+  const uint8_t *which;          // generating constraint per tuple
+  const u32 *cnt;                // its row length
+  const u64 *coff;               // exclusive scan of ceil(cnt / LAST_CHUNK)
+  u64 nT, items;
+  u32 arity;                     // variables of the query
+  const u32 *dcol[RPQ_MAX_VARS]; // declaration-order columns of the bound variables (nullptr: the new one)
+  u64 *acc;                      // [0] digest sum, [1] digest xor, [5] count
+};
+
+__global__ void count_last_kernel(const LastParams lp) {
+  const StepParams &p = lp.p;
+  const u64 warp = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
+  const u32 lane = lane_id();
+  u64 cnt = 0, hs = 0, hx = 0;
+  for (u64 t = warp; t < lp.items; t += nwarps) {
+    // the tuple of item t: the largest i with coff[i] <= t
+    u64 lo = 0, hi = lp.nT;
+    while (hi - lo > 1) {
+      const u64 mid = (lo + hi) >> 1;
+      if (lp.coff[mid] <= t)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    const u64 i = lo;
+    const u32 gen = lp.which[i];
+    const u32 c = (u32)(t - lp.coff[i]);
+    // rows of the tuple's constraints (lane k looks up constraint k)
+    u64 b = 0;
+    u32 l = 0;
+    if (lane < p.nc) lookup(p.c[lane].rows, p.c[lane].col[i], &b, &l);
+    const u64 gb = __shfl_sync(FULL_MASK, b, gen);
+    const u32 gl = __shfl_sync(FULL_MASK, l, gen);
+    u64 rb[MAXC];
+    u32 rl[MAXC];
+#pragma unroll
+    for (int k = 0; k < MAXC; k++) {
+      rb[k] = __shfl_sync(FULL_MASK, b, k);
+      rl[k] = __shfl_sync(FULL_MASK, l, k);
+    }
+    // the bound columns of the tuple, declaration order
+    u32 vals[RPQ_MAX_VARS];
+#pragma unroll
+    for (int v = 0; v < RPQ_MAX_VARS; v++) vals[v] = (v < (int)lp.arity && lp.dcol[v]) ? lp.dcol[v][i] : 0u;
+    const u32 end = min(gl, (c + 1) * LAST_CHUNK);
+    for (u32 j = c * LAST_CHUNK + lane; j < end; j += 32) {
+      const u32 z = p.c[gen].rows.dst[gb + j];
+      bool ok = p.want_label < 0 || p.vlabel[z] == (uint8_t)p.want_label;
+      for (u32 k = 0; k < p.nc && ok; k++)
+        if (k != gen) ok = row_has(p.c[k].rows.dst, rb[k], rl[k], z);
+      if (!ok) continue;
+      u64 h;
+      if (lp.arity == 1) {
+        h = splitmix64((u64)z);
+      } else {
+        const u32 a0 = lp.dcol[0] ? vals[0] : z, a1 = lp.dcol[1] ? vals[1] : z;
+        h = splitmix64(((u64)a0 << 32) | (u64)a1);
+        for (u32 v = 2; v < lp.arity; v++) h = splitmix64(h ^ (u64)(lp.dcol[v] ? vals[v] : z));
+      }
+      cnt++;
+      hs += h;
+      hx ^= h;
+    }
+  }
+  cnt = warp_sum(cnt);
+  hs = warp_sum(hs);
+  hx = warp_xor(hx);
+  if (lane == 0 && cnt) {
+    atomicAdd(&lp.acc[5], cnt);
+    atomicAdd(&lp.acc[0], hs);
+    atomicXor(&lp.acc[1], hx);
+  }
+}
+
+__global__ void chunk_counts(const u32 *__restrict__ cnt, u64 n, u32 *__restrict__ out) {
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
+    out[i] = (cnt[i] + LAST_CHUNK - 1) / LAST_CHUNK;
+}
+
 unsigned grid1(u64 n) {
   u64 b = (n + 255) / 256;
   if (b > 152ull * 32) b = 152ull * 32;
@@ -451,6 +543,9 @@ struct Engine {
     if ((rc = cuda(cudaMemcpyAsync(off.p + T.n, small.p + 4, 8, cudaMemcpyDeviceToDevice, st), "copy"))) return rc;
     if ((rc = cuda(cudaStreamSynchronize(st), "sync"))) return rc;
     stats.launches += 2;
+    bool has_self = false;
+    for (auto &c : cons[k]) has_self |= c.bound_pos < 0;
+    if (k == (int)n_vars - 1 && !materialize && !has_self) return count_last(k, T, p, cnt.p, which.p);
     for (u64 c0 = 0; c0 < total; c0 += CAND_CAP) {
       u64 nc = std::min<u64>(CAND_CAP, total - c0);
       Buf<u32> ct, cv;
@@ -461,8 +556,6 @@ struct Engine {
       // self-loop constraints need the candidate values
       std::vector<OwnedRows> self_rows;
       StepParams ps = p;
-      bool has_self = false;
-      for (auto &c : cons[k]) has_self |= c.bound_pos < 0;
       if (has_self) {
         StepParams tmpp;
         if ((rc = prepare(k, T, cv.p, nc, self_rows, tmpp, true))) return rc;
@@ -471,6 +564,45 @@ struct Engine {
       }
       if ((rc = bind(k, T, ct.p, cv.p, nc, ps, which.p))) return rc;
     }
+    return RPQ_OK;
+  }
+
+  // The last variable of a count-only query: fused binding, count and digest.
+  int count_last(int k, Table &T, const StepParams &p, const u32 *cnt, const uint8_t *which) {
+    Buf<u32> nch;
+    Buf<u64> coff, tmp;
+    int rc;
+    if ((rc = nch.alloc(ctx, T.n)) || (rc = coff.alloc(ctx, T.n + 1)) ||
+        (rc = tmp.alloc(ctx, scan_tmp_words(T.n + 1))))
+      return rc;
+    chunk_counts<<<grid1(T.n), 256, 0, st>>>(cnt, T.n, nch.p);
+    if ((rc = cuda(cudaGetLastError(), "chunk_counts"))) return rc;
+    if ((rc = cuda(exclusive_scan_u32_to_u64(nch.p, coff.p, T.n, small.p + 4, tmp.p, st), "scan"))) return rc;
+    u64 items = 0, got = 0;
+    if ((rc = cuda(cudaMemcpyAsync(&items, small.p + 4, 8, cudaMemcpyDeviceToHost, st), "copy")) ||
+        (rc = cuda(cudaMemsetAsync(small.p + 5, 0, 8, st), "memset")) || (rc = cuda(cudaStreamSynchronize(st), "sync")))
+      return rc;
+    LastParams lp;
+    std::memset(&lp, 0, sizeof(lp));
+    lp.p = p;
+    lp.which = which;
+    lp.cnt = cnt;
+    lp.coff = coff.p;
+    lp.nT = T.n;
+    lp.items = items;
+    lp.arity = n_vars;
+    for (uint32_t v = 0; v < n_vars; v++) lp.dcol[v] = pos[v] < k ? T.cols[pos[v]].p : nullptr;
+    lp.acc = small.p;
+    if (items) {
+      const u64 warps = std::min<u64>(items, 152ull * 64);
+      count_last_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(lp);
+      if ((rc = cuda(cudaGetLastError(), "count_last"))) return rc;
+    }
+    if ((rc = cuda(cudaMemcpyAsync(&got, small.p + 5, 8, cudaMemcpyDeviceToHost, st), "copy")) ||
+        (rc = cuda(cudaStreamSynchronize(st), "sync")))
+      return rc;
+    stats.launches += 3;
+    count += got;
     return RPQ_OK;
   }
 

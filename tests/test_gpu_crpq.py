@@ -106,6 +106,9 @@ def test_random_crpq(ctx, case):
     assert rows.tolist() == want.rows.tolist(), atoms
     assert info[0] == len(want.rows)
     assert (info[0], info[2], info[3]) == oracle.row_digest(want.rows)
+    # count only: the last variable is bound, counted and digested in one pass
+    _, info_c = crpq_gpu(ctx, g, nv, atoms, var_label=var_label, restrict0=restrict0, flags=rpq.RPQ_COUNT_ONLY)
+    assert (info_c[0], info_c[2], info_c[3]) == oracle.row_digest(want.rows), atoms
 
 
 def test_crpq_errors(ctx):
@@ -149,6 +152,8 @@ def test_rmat22_triangle_sampled(ctx, rmat22):
     rows, info = crpq_gpu(ctx, g, 3, TRIANGLE, restrict0=sample)
     assert rows.tolist() == want.rows.tolist()
     assert (info[0], info[2], info[3]) == oracle.row_digest(want.rows)
+    _, info_c = crpq_gpu(ctx, g, 3, TRIANGLE, restrict0=sample, flags=rpq.RPQ_COUNT_ONLY)
+    assert (info_c[0], info_c[2], info_c[3]) == oracle.row_digest(want.rows)
     # with vertex labels on y and z
     vlab = [-1, 1, 2]
     want = oracle.crpq(og, 3, TRIANGLE, var_label=vlab, restrict0=sample)
