@@ -711,17 +711,53 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
     c0 = __shfl_sync(FULL_MASK, t, 0);
   }
   for (; c0 < n;) {
-    u32 qmask = 0, hmask = 0;  // hmask: states with a long in-row (its chunks also produce)
+    // hmask: states with a long in-row (its chunks also produce); with a
+    // sparse frontier (bits), lane i also tests up to PRESCAN in-edges of
+    // its own vertex against the frontier bitmap, so that a state none of
+    // whose in-neighbours is in the frontier is dropped here, 32 vertices at
+    // a time; tmask: states whose light rows are longer than that and showed
+    // no hit yet -- the sub-warp tests the rest of them below
+    constexpr u32 PRESCAN = 16;
+    u32 qmask = 0, hmask = 0, tmask = 0;
     if (c0 + lane < n) {
       const u32 v = (u32)(c0 + lane);
       for (u32 q2 = 0; q2 < Q; q2++)
         for (u32 j = p.q.in_begin[q2]; j < p.q.in_begin[q2 + 1]; j++) {
           const u32 l = p.q.in_label[j];
-          if (!(p.q.in_from[j] & active) || l >= p.L) continue;
+          const u32 from = p.q.in_from[j] & active;
+          if (!from || l >= p.L) continue;
           const u32 *off = p.in_off + (u64)l * n1 + v;
-          const u32 len = __ldg(off + 1) - __ldg(off);
-          if (len > 0 && (len < HEAVY_ROW || !chunked)) qmask |= 1u << q2;
-          if (len >= HEAVY_ROW && chunked) hmask |= 1u << q2;
+          const u32 beg = __ldg(off), len = __ldg(off + 1) - beg;
+          if (len >= HEAVY_ROW && chunked) {
+            hmask |= 1u << q2;
+            continue;
+          }
+          if (len == 0 || (((qmask & ~tmask) >> q2) & 1u)) continue;  // a hit is known already
+          if (!bits) {
+            qmask |= 1u << q2;
+            continue;
+          }
+          bool hit = false;
+          const u32 scan = min(len, PRESCAN);
+          for (u32 i = 0; i < scan && !hit; i += 4) {
+            u32 u[4];
+#pragma unroll
+            for (int t = 0; t < 4; t++) u[t] = i + t < scan ? __ldg(p.in_col + beg + i + t) : NO_SOURCE;
+            for (u32 fb = from; fb; fb &= fb - 1) {
+              const u64 qb = (u64)(__ffs(fb) - 1) * n;
+#pragma unroll
+              for (int t = 0; t < 4; t++)
+                if (u[t] != NO_SOURCE) hit |= (__ldcg(bits + ((qb + u[t]) >> 5)) >> ((qb + u[t]) & 31)) & 1u;
+            }
+          }
+          bytes += (u64)scan * (4 + 4 * __popc(from));
+          if (hit) {
+            qmask |= 1u << q2;
+            tmask &= ~(1u << q2);
+          } else if (len > PRESCAN) {
+            qmask |= 1u << q2;
+            tmask |= 1u << q2;
+          }
         }
     }
     const u32 M = __ballot_sync(FULL_MASK, qmask != 0);
@@ -730,16 +766,19 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
       const u32 s = s0 + sg;
       const u32 vq = __shfl_sync(FULL_MASK, qmask, s);
       const u32 vh = __shfl_sync(FULL_MASK, hmask, s);
+      const u32 vt = __shfl_sync(FULL_MASK, tmask, s);
       const bool wv = vq != 0;
       const u32 w = wv ? (u32)(c0 + s) : 0;
     for (u32 q2 = 0; q2 < Q; q2++) {
       const u32 gb = p.q.in_begin[q2], ge = p.q.in_begin[q2 + 1];
       bool any = wv && ((vq >> q2) & 1u);
-      if (bits) {
-        // sparse frontier: a vertex none of whose in-neighbours is in it is
-        // skipped before its visited words are read (the sub-warp's lanes
-        // test the in-edges in turn: a column id and a bitmap word each)
+      if (bits && __any_sync(FULL_MASK, any && ((vt >> q2) & 1u))) {
+        // sparse frontier, rows the pre-scan left undecided: a vertex none of
+        // whose in-neighbours is in the frontier is skipped before its
+        // visited words are read (the sub-warp's lanes test the in-edges in
+        // turn: a column id and a bitmap word each)
         bool hit = false;
+        if (!((vt >> q2) & 1u)) any = false, hit = wv && ((vq >> q2) & 1u);
         for (u32 j = gb; j < ge && !hit && any; j++) {
           const u32 l = p.q.in_label[j];
           const u32 from = p.q.in_from[j] & active;
