@@ -452,9 +452,10 @@ def bench_batch(args, compact: bool = False):
     import torch
     from paper_2602_20748_gb300 import rpq, synth
 
-    n = 1 << 22
+    scale = args.scale if args.scale is not None and not compact else 22
+    n = 1 << scale
     t_gen = time.perf_counter()
-    src, dst, lab = synth.rmat_graph(22, 1 << 26, 8, 1.2, seed=synth.BASE_SEED + 4)
+    src, dst, lab = synth.rmat_graph(scale, 16 << scale, 8, 1.2, seed=synth.BASE_SEED + 4)
     regexes, sources = synth.batch_queries(4096, 8, 1.2, src, n, seed=synth.BASE_SEED + 4)
     gen_s = time.perf_counter() - t_gen
     nq = len(regexes)
@@ -519,8 +520,8 @@ def bench_batch(args, compact: bool = False):
         "evicted_per_step": evicted // max(1, args.steps), "gpu_launches_per_step": launches // max(1, args.steps),
         "plain_gpu_launches": plain_launches,
         "autotuned": {**tuned, "threads": threads, "queries_per_launch": per_launch, "autotune_s": round(tune_s, 2)},
-        "config": {"workload": "rmat22-batched-single-source", "queries": nq, "vertices": n,
-                   "generated_edges": 1 << 26, "labels": 8, "zipf_s": 1.2, "mode": "per-query count + digest",
+        "config": {"workload": f"rmat{scale}-batched-single-source", "queries": nq, "vertices": n,
+                   "generated_edges": 16 << scale, "labels": 8, "zipf_s": 1.2, "mode": "per-query count + digest",
                    "generation_s": round(gen_s, 1)},
     }
     if compact:
