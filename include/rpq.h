@@ -113,6 +113,16 @@ int rpq_set_stream(rpq_ctx *ctx, void *cuda_stream);
  *                  below the bottom-up bytes (default 16)
  *   "lane_alpha"   the same for lane-mode launches (one automaton per lane;
  *                  default 2)
+ *   "crpq_bitset_frac" run_crpq: an atom's row with at least this fraction
+ *                  of the vertices among its destinations is also written as
+ *                  a bitset over the vertices, so that a membership test in
+ *                  it is one load instead of a binary search; in the last
+ *                  step of a count-only CRPQ such rows are kept as bitsets
+ *                  only, and a partial tuple whose rows are all bitsets is
+ *                  extended by a word-by-word AND of them.  0 .. 2 (default
+ *                  1/64: the bitset is at most twice the row's list; 0: every
+ *                  non-empty row; above 1: none).  Bitsets take at most half
+ *                  of the budget left, longest rows first.
  *   "grid_share"   fraction (0, 1] of the SMs the persistent traversal grids
  *                  occupy (default 1; 0.5 lets two contexts' searches run
  *                  side by side)

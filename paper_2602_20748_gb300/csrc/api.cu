@@ -60,6 +60,7 @@ struct rpq_ctx {
   float alpha = 16.0f;
   float lane_alpha = 2.0f;  // the same trade-off for lane-mode launches
   unsigned pull_dynamic = 1;  // bottom-up vertex chunks from a cursor
+  double crpq_bitset_frac = 1.0 / 64;  // CRPQ rows of at least this fraction of the vertices get a bitset
   uint64_t time_limit_ns = 20ull * 1000 * 1000 * 1000;
   uint32_t max_groups = 16;
   bool trace = false;    // print per-level timings of each traversal (RPQ_TRACE=1)
@@ -97,6 +98,11 @@ struct Chunk {
   uint64_t rows = 0;
   uint32_t n_lanes = 0;
   uint64_t bytes = 0;
+  u64 *bits = nullptr;  // bitset rows (see RowChunk)
+  u32 *lane_slot = nullptr;
+  uint64_t bwords = 0;
+  uint32_t n_bits = 0;
+  bool lists_kept = true;
 };
 
 }  // namespace
@@ -280,13 +286,63 @@ void free_chunk(rpq_ctx *ctx, Chunk &c) {
   dfree(ctx, c.lanesrc, c.n_lanes);
   dfree(ctx, c.lane_off, (uint64_t)c.n_lanes + 1);
   dfree(ctx, c.dst, c.rows);
+  if (c.bits) {
+    dfree(ctx, c.bits, (uint64_t)c.n_bits * c.bwords);
+    dfree(ctx, c.lane_slot, c.n_lanes);
+  }
+}
+
+// Picks the lanes of a chunk whose rows become bitsets (bits_req): reads the
+// lanes' row counts from the scanned offsets, keeps the rows of at least
+// min_len destinations, longest first, while the bitsets take at most half of
+// the budget left, and allocates them into c.  Returns the lanes' slots on
+// the host (NO_SOURCE: listed only).
+int pick_bit_lanes(rpq_ctx *ctx, const RowBitsReq &req, const u64 *off, uint32_t segs, uint32_t n, Chunk &c) {
+  std::vector<u64> lane_off(c.n_lanes + 1);
+  u64 *d_lane_off = nullptr;
+  int rc;
+  if ((rc = dalloc(ctx, &d_lane_off, (uint64_t)c.n_lanes + 1))) return rc;
+  cudaError_t e = launch_gather_lane_off(off, segs, c.n_lanes, ctx->small + 2, d_lane_off, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(lane_off.data(), d_lane_off, lane_off.size() * 8, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  dfree(ctx, d_lane_off, (uint64_t)c.n_lanes + 1);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "row lengths");
+  std::vector<uint32_t> sel;
+  for (uint32_t i = 0; i < c.n_lanes; i++)
+    if (lane_off[i + 1] - lane_off[i] >= std::max<uint64_t>(req.min_len, 1)) sel.push_back(i);
+  if (sel.empty()) return RPQ_OK;
+  std::stable_sort(sel.begin(), sel.end(), [&](uint32_t a, uint32_t b) {
+    return lane_off[a + 1] - lane_off[a] > lane_off[b + 1] - lane_off[b];
+  });
+  const uint64_t bwords = ((uint64_t)n + 255) / 256 * 4;
+  const uint64_t left = ctx->used < ctx->budget ? ctx->budget - ctx->used : 0;
+  const uint64_t cap = left / 2 / (bwords * 8);
+  if (sel.size() > cap) sel.resize(cap);
+  if (sel.empty()) return RPQ_OK;
+  std::vector<uint32_t> slot(c.n_lanes, NO_SOURCE);
+  for (size_t k = 0; k < sel.size(); k++) slot[sel[k]] = (uint32_t)k;
+  if ((rc = dalloc(ctx, &c.bits, sel.size() * bwords))) return rc;
+  if ((rc = dalloc(ctx, &c.lane_slot, c.n_lanes))) {
+    dfree(ctx, c.bits, sel.size() * bwords);
+    c.bits = nullptr;
+    return rc;
+  }
+  c.n_bits = (uint32_t)sel.size();
+  c.bwords = bwords;
+  c.lists_kept = req.keep_lists;
+  e = cudaMemcpyAsync(c.lane_slot, slot.data(), (uint64_t)c.n_lanes * 4, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);  // slot is a host temporary
+  if (e != cudaSuccess) return cuda_err(ctx, e, "bitset slots");
+  return RPQ_OK;
 }
 
 // Evaluates one RPQ from the sorted, distinct start vertices `srcs`.
 // With lane_stats (count-only), (rows, digest sum, digest xor) of every
 // source's own rows are stored at lane_stats[3 * i ..] for srcs[i].
 int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::vector<uint32_t> &srcs_in,
-             uint32_t flags, rpq_result *res, std::vector<uint64_t> *lane_stats = nullptr) {
+             uint32_t flags, rpq_result *res, std::vector<uint64_t> *lane_stats = nullptr,
+             const RowBitsReq *bits_req = nullptr) {
   const DevGraph &g = gr->g;
   const bool reverse = (flags & RPQ_REVERSE) != 0;
   if (reverse && !qr->hq.has_rev)
@@ -589,8 +645,31 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
       Chunk c;
       c.n_lanes = n_lanes;
       c.rows = total;
+      if (bits_req) {
+        if ((rc = pick_bit_lanes(ctx, *bits_req, off, segs, n, c))) {
+          free_chunk(ctx, c);
+          dfree(ctx, cnt, ncnt);
+          dfree(ctx, off, ncnt);
+          dfree(ctx, tmp, tmpw);
+          return rc;
+        }
+        ep.lane_slot = c.lane_slot;
+        ep.bits = c.bits;
+        ep.bwords = c.bwords;
+        ep.keep_lists = c.lists_kept ? 1u : 0u;
+        if (c.bits && !c.lists_kept) {
+          // bitset rows are not listed: offsets of the listed rows only
+          u64 listed = 0;
+          CK(launch_zero_lane_counts(cnt, segs, n_lanes, c.lane_slot, ctx->stream));
+          CK(exclusive_scan_u32_to_u64(cnt, off, ncnt, ctx->small + 2, tmp, ctx->stream));
+          CK(cudaMemcpyAsync(&listed, ctx->small + 2, 8, cudaMemcpyDeviceToHost, ctx->stream));
+          CK(cudaStreamSynchronize(ctx->stream));
+          c.rows = listed;
+          res->stats.launches += 2;
+        }
+      }
       if ((rc = dalloc(ctx, &c.lanesrc, n_lanes)) || (rc = dalloc(ctx, &c.lane_off, (uint64_t)n_lanes + 1)) ||
-          (rc = dalloc(ctx, &c.dst, total))) {
+          (rc = dalloc(ctx, &c.dst, c.rows))) {
         free_chunk(ctx, c);
         dfree(ctx, cnt, ncnt);
         dfree(ctx, off, ncnt);
@@ -791,6 +870,8 @@ int rpq_set_option(rpq_ctx *ctx, const char *name, double value) {
     ctx->lane_alpha = (float)value;
   } else if (n == "pull_dynamic" && (value == 0 || value == 1)) {
     ctx->pull_dynamic = value != 0 ? 1u : 0u;
+  } else if (n == "crpq_bitset_frac" && value >= 0 && value <= 2) {
+    ctx->crpq_bitset_frac = value;
   } else if (n == "grid_share" && value > 0 && value <= 1) {
     ctx->grid_share = value;
   } else if (n == "max_groups" && value >= 1 && value <= 16) {
@@ -824,6 +905,8 @@ int rpq_get_option(const rpq_ctx *ctx, const char *name, double *value) {
     *value = ctx->lane_alpha;
   else if (n == "pull_dynamic")
     *value = ctx->pull_dynamic;
+  else if (n == "crpq_bitset_frac")
+    *value = ctx->crpq_bitset_frac;
   else if (n == "grid_share")
     *value = ctx->grid_share;
   else if (n == "max_groups")
@@ -1400,6 +1483,7 @@ void ctx_copy_tunables(rpq_ctx *to, const rpq_ctx *from) {
   to->alpha = from->alpha;
   to->lane_alpha = from->lane_alpha;
   to->pull_dynamic = from->pull_dynamic;
+  to->crpq_bitset_frac = from->crpq_bitset_frac;
   to->time_limit_ns = from->time_limit_ns;
   to->spill_cap = from->spill_cap;
   to->batch = from->batch;
@@ -1448,6 +1532,8 @@ int ctx_pinned(rpq_ctx *ctx, int count, size_t bytes, void **out) {
 bool ctx_cancelled(rpq_ctx *ctx) { return ctx->cancel.load(std::memory_order_relaxed) != 0; }
 void ctx_set_cancel(rpq_ctx *ctx, bool on) { ctx->cancel.store(on ? 1 : 0); }
 float ctx_alpha(rpq_ctx *ctx) { return ctx->alpha; }
+double ctx_crpq_bitset_frac(rpq_ctx *ctx) { return ctx->crpq_bitset_frac; }
+uint64_t ctx_budget_left(rpq_ctx *ctx) { return ctx->used < ctx->budget ? ctx->budget - ctx->used : 0; }
 uint64_t ctx_time_limit_ns(rpq_ctx *ctx) { return ctx->time_limit_ns; }
 void *ctx_static_scratch(rpq_ctx *ctx) { return ctx->static_scratch; }
 void ctx_release_workspace(rpq_ctx *ctx) {
@@ -1462,12 +1548,12 @@ const HostQuery &query_host(const rpq_query *q) { return q->hq; }
 // back the per-lane CSR chunks (ownership passes to the caller).
 int rpq_rows_for_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, std::vector<uint32_t> &srcs,
                          bool reverse, std::vector<RowChunk> *chunks, rpq_stats *stats, uint64_t *dsum,
-                         uint64_t *dxor) {
+                         uint64_t *dxor, const RowBitsReq *bits_req) {
   rpq_result r;
   r.ctx = ctx;
   r.materialized = true;
   std::memset(&r.stats, 0, sizeof(r.stats));
-  int rc = eval_rpq(ctx, g, q, srcs, RPQ_MATERIALIZE | (reverse ? RPQ_REVERSE : 0u), &r);
+  int rc = eval_rpq(ctx, g, q, srcs, RPQ_MATERIALIZE | (reverse ? RPQ_REVERSE : 0u), &r, nullptr, bits_req);
   if (dsum) *dsum += r.dsum;
   if (dxor) *dxor ^= r.dxor;
   if (stats) {
@@ -1498,6 +1584,11 @@ int rpq_rows_for_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, s
       rc_.dst = c.dst;
       rc_.rows = c.rows;
       rc_.n_lanes = c.n_lanes;
+      rc_.bits = c.bits;
+      rc_.lane_slot = c.lane_slot;
+      rc_.bwords = c.bwords;
+      rc_.n_bits = c.n_bits;
+      rc_.lists_kept = c.lists_kept;
       chunks->push_back(rc_);
     } else {
       free_chunk(ctx, c);
@@ -2021,6 +2112,11 @@ void free_row_chunk(rpq_ctx *ctx, RowChunk &c) {
   dfree(ctx, c.lanesrc, c.n_lanes);
   dfree(ctx, c.lane_off, (uint64_t)c.n_lanes + 1);
   dfree(ctx, c.dst, c.rows);
+  if (c.bits) {
+    dfree(ctx, c.bits, (uint64_t)c.n_bits * c.bwords);
+    dfree(ctx, c.lane_slot, c.n_lanes);
+  }
+  c = RowChunk{};
 }
 
 int make_tuple_result(rpq_ctx *ctx, uint32_t arity, u32 *tuples, uint64_t rows, uint64_t dsum, uint64_t dxor,

@@ -23,6 +23,8 @@
 //   * Complete tuples of a batch are sorted lexicographically in declaration
 //     order (stable LSD passes over the columns) and digested.
 #include <algorithm>
+#include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <functional>
 #include <numeric>
@@ -37,11 +39,11 @@ constexpr uint64_t CAND_CAP = 1ull << 26;  // candidate pairs per expansion slic
 constexpr uint32_t BATCH0 = 4096;          // values of variable 0 per batch
 constexpr int MAXC = RPQ_MAX_ATOMS;
 
-struct DevRows {  // sorted rows of one atom for a sorted set of endpoint values
-  const u32 *src;
-  const u64 *beg;
-  const u32 *len;
-  const u32 *dst;
+struct DevRows {  // rows of one atom for a sorted set of endpoint values
+  const u32 *src;   // the values with a row, ascending
+  const u64 *ptr;   // per row: device address of its sorted destinations
+  const u64 *bptr;  // per row: device address of its bitset over the vertices, or 0
+  const u32 *len;   // per row: its number of destinations
   u32 ns;
 };
 
@@ -55,15 +57,26 @@ struct StepParams {
   u32 gen_mask;  // constraints that may generate candidates
   int want_label;
   const uint8_t *vlabel;
+  // count-only last step: rows with a bitset have no list (they generate no
+  // candidates), and a tuple whose rows all have bitsets is joined word by
+  // word (DENSE); lbits = the vertices of label want_label as a bitset
+  u32 fused;
+  u64 bwords;
+  const u64 *lbits;
   Cons c[MAXC];
 };
+
+constexpr uint8_t DENSE = 0x80;  // flag in a tuple's generator byte
 
 struct ColPtrs {
   const u32 *in[RPQ_MAX_VARS];
   u32 *out[RPQ_MAX_VARS + 1];
 };
 
-__device__ __forceinline__ bool lookup(const DevRows &r, u32 v, u64 *b, u32 *l) {
+// Row of value v: its destinations (sorted; nullptr when the row is kept as
+// a bitset only) and their number (0 if v has no row); returns the row's
+// bitset, or nullptr when it has none.
+__device__ __forceinline__ const u64 *lookup(const DevRows &r, u32 v, const u32 **row, u32 *l) {
   u32 lo = 0, hi = r.ns;
   while (lo < hi) {
     u32 mid = (lo + hi) >> 1;
@@ -74,44 +87,59 @@ __device__ __forceinline__ bool lookup(const DevRows &r, u32 v, u64 *b, u32 *l) 
       hi = mid;
   }
   if (lo < r.ns && r.src[lo] == v) {
-    *b = r.beg[lo];
+    *row = reinterpret_cast<const u32 *>(r.ptr[lo]);
     *l = r.len[lo];
-    return true;
+    return reinterpret_cast<const u64 *>(r.bptr[lo]);
   }
-  *b = 0;
+  *row = nullptr;
   *l = 0;
-  return false;
+  return nullptr;
 }
 
-__device__ __forceinline__ bool row_has(const u32 *dst, u64 b, u32 l, u32 y) {
+__device__ __forceinline__ bool row_has(const u32 *row, u32 l, u32 y) {
   u32 lo = 0, hi = l;
   while (lo < hi) {
     u32 mid = (lo + hi) >> 1;
-    u32 s = dst[b + mid];
+    u32 s = row[mid];
     if (s < y)
       lo = mid + 1;
     else
       hi = mid;
   }
-  return lo < l && dst[b + lo] == y;
+  return lo < l && row[lo] == y;
 }
 
-// Per tuple: the generating constraint (shortest row) and its length.
+// y in the row (its bitset when it has one, else its sorted destinations)?
+__device__ __forceinline__ bool member(const u32 *row, u32 l, const u64 *bits, u32 y) {
+  if (bits) return (bits[y >> 6] >> (y & 63)) & 1ull;
+  return row_has(row, l, y);
+}
+
+// Per tuple: the generating constraint (shortest listed row) and its length;
+// in a fused step, DENSE when every row of the tuple is a bitset.
 __global__ void choose_gen(const StepParams p, u64 nT, u32 *__restrict__ cnt, uint8_t *__restrict__ which) {
   for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < nT; i += (u64)gridDim.x * blockDim.x) {
     u32 best = 0xffffffffu, w = 0xff;
+    bool all_bits = p.fused != 0;
     for (u32 k = 0; k < p.nc; k++) {
       if (!(p.gen_mask >> k & 1u)) continue;
-      u64 b;
+      const u32 *row;
       u32 l;
-      lookup(p.c[k].rows, p.c[k].col[i], &b, &l);
+      const u64 *bits = lookup(p.c[k].rows, p.c[k].col[i], &row, &l);
+      if (p.fused && bits) continue;  // bitset only
+      all_bits = false;
       if (l < best) {
         best = l;
         w = k;
       }
     }
-    cnt[i] = (w == 0xff) ? 0u : best;
-    which[i] = (uint8_t)w;
+    if (all_bits) {
+      cnt[i] = 0;
+      which[i] = DENSE;
+    } else {
+      cnt[i] = (w == 0xff) ? 0u : best;
+      which[i] = (uint8_t)w;
+    }
   }
 }
 
@@ -131,11 +159,11 @@ __global__ void expand_cands(const StepParams p, u64 nT, const u64 *__restrict__
         hi = mid;
     }
     const Cons &c = p.c[which[lo]];
-    u64 b;
+    const u32 *row;
     u32 l;
-    lookup(c.rows, c.col[lo], &b, &l);
+    lookup(c.rows, c.col[lo], &row, &l);
     cand_t[k] = (u32)lo;
-    cand_v[k] = c.rows.dst[b + (j - off[lo])];
+    cand_v[k] = row[j - off[lo]];
   }
 }
 
@@ -150,10 +178,10 @@ __global__ void filter_cands(const StepParams p, u64 n, const u32 *__restrict__ 
     for (u32 k = 0; k < p.nc && ok; k++) {
       if (k == skip) continue;
       u32 x = p.c[k].col ? p.c[k].col[cand_t[j]] : y;
-      u64 b;
+      const u32 *row;
       u32 l;
-      lookup(p.c[k].rows, x, &b, &l);
-      ok = row_has(p.c[k].rows.dst, b, l, y);
+      const u64 *bits = lookup(p.c[k].rows, x, &row, &l);
+      ok = member(row, l, bits, y);
     }
     flag[j] = ok ? 1u : 0u;
   }
@@ -171,15 +199,36 @@ __global__ void compact_cands(u64 n, const u32 *__restrict__ flag, const u64 *__
   }
 }
 
+// Row index of one chunk: lane i (source lanesrc[i]) is row lane_base + i.
 __global__ void rows_index(const u32 *__restrict__ lanesrc, const u64 *__restrict__ lane_off, u32 n_lanes,
-                           u32 lane_base, u64 dst_base, u32 *__restrict__ src, u64 *__restrict__ beg,
-                           u32 *__restrict__ len) {
+                           u32 lane_base, const u32 *__restrict__ dst, const u32 *__restrict__ lane_slot,
+                           const u64 *__restrict__ bits, u64 bwords, u32 *__restrict__ src, u64 *__restrict__ ptr,
+                           u64 *__restrict__ bptr, u32 *__restrict__ len, u32 lists_kept) {
   for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n_lanes; i += gridDim.x * blockDim.x) {
-    u32 s = lanesrc[i];
+    const u32 s = lanesrc[i];
     if (s == NO_SOURCE) continue;
+    const u32 slot = lane_slot ? lane_slot[i] : NO_SOURCE;
     src[lane_base + i] = s;
-    beg[lane_base + i] = dst_base + lane_off[i];
-    len[lane_base + i] = (u32)(lane_off[i + 1] - lane_off[i]);
+    bptr[lane_base + i] = slot == NO_SOURCE ? 0ull : reinterpret_cast<u64>(bits + (u64)slot * bwords);
+    if (slot == NO_SOURCE || lists_kept) {
+      ptr[lane_base + i] = reinterpret_cast<u64>(dst + lane_off[i]);
+      len[lane_base + i] = (u32)(lane_off[i + 1] - lane_off[i]);
+    } else {
+      ptr[lane_base + i] = 0;
+    }
+  }
+}
+
+// Vertices of label `label` as a bitset (bwords words).
+__global__ void label_bits(const uint8_t *__restrict__ vlabel, u32 n, uint8_t label, u64 bwords,
+                           u64 *__restrict__ out) {
+  for (u64 w = (u64)blockIdx.x * blockDim.x + threadIdx.x; w < bwords; w += (u64)gridDim.x * blockDim.x) {
+    u64 m = 0;
+    for (u32 b = 0; b < 64; b++) {
+      const u64 v = w * 64 + b;
+      if (v < n && vlabel[v] == label) m |= 1ull << b;
+    }
+    out[w] = m;
   }
 }
 
@@ -230,26 +279,50 @@ __global__ void digest_rows(const ColPtrs cols, u32 arity, u64 n, u64 *__restric
   }
 }
 
-// Count-only binding of the last variable, fused: work item t is chunk c of
-// tuple i's generating row (items numbered by the exclusive scan coff of the
-// tuples' chunk counts); a warp takes one item, looks up the rows of the
-// tuple's constraints once, and for each of the chunk's candidates tests the
-// vertex label and every other constraint by binary search, counting and
-// digesting the survivors in place (no candidate arrays, no compaction, no
-// second pass over the tuples).  The tuples are distinct because every bound
-// value of a partial tuple and every candidate of a sorted row is.
+// Count-only binding of the last variable, fused: the tuples' work is cut
+// into items (numbered by the exclusive scan coff of the tuples' item
+// counts) and a warp takes one item at a time, looks up the rows of the
+// tuple's constraints once, and counts and digests the tuples that extend it
+// in place (no candidate arrays, no compaction, no second pass over the
+// tuples).  An item of a tuple with a generating row is LAST_CHUNK of that
+// row's candidates, each tested against the vertex label and every other
+// constraint (bitset or binary search); an item of a DENSE tuple (all rows
+// bitsets) is DENSE_WORDS words of the AND of the rows' bitsets and the
+// label's, whose set bits are the new values.  The tuples are distinct
+// because every bound value of a partial tuple is, and every candidate of a
+// sorted row or bit of a bitset.
 constexpr u32 LAST_CHUNK = 256;
+constexpr u32 DENSE_WORDS = 2048;
 
 struct LastParams {
   StepParams p;
-  const uint8_t *which;          // generating constraint per tuple
+  const uint8_t *which;          // generating constraint per tuple, or DENSE
   const u32 *cnt;                // its row length
-  const u64 *coff;               // exclusive scan of ceil(cnt / LAST_CHUNK)
+  const u64 *coff;               // exclusive scan of the tuples' item counts
   u64 nT, items;
   u32 arity;                     // variables of the query
+  u32 newpos;                    // declaration position of the variable being bound
   const u32 *dcol[RPQ_MAX_VARS]; // declaration-order columns of the bound variables (nullptr: the new one)
   u64 *acc;                      // [0] digest sum, [1] digest xor, [5] count
 };
+
+// Digest hash of the tuple (vals with z at position newpos), given pre = the
+// fold over positions 0 .. newpos - 1 when newpos >= 2 (see result_info).
+__device__ __forceinline__ u64 last_hash(const LastParams &lp, const u32 (&vals)[RPQ_MAX_VARS], u64 pre, u32 z) {
+  u64 h;
+  if (lp.arity == 1) return splitmix64((u64)z);
+  u32 v;
+  if (lp.newpos >= 2) {
+    h = splitmix64(pre ^ (u64)z);
+    v = lp.newpos + 1;
+  } else {
+    const u32 a0 = lp.newpos == 0 ? z : vals[0], a1 = lp.newpos == 1 ? z : vals[1];
+    h = splitmix64(((u64)a0 << 32) | (u64)a1);
+    v = 2;
+  }
+  for (; v < lp.arity; v++) h = splitmix64(h ^ (u64)vals[v]);
+  return h;
+}
 
 __global__ void count_last_kernel(const LastParams lp) {
   const StepParams &p = lp.p;
@@ -271,37 +344,52 @@ __global__ void count_last_kernel(const LastParams lp) {
     const u32 gen = lp.which[i];
     const u32 c = (u32)(t - lp.coff[i]);
     // rows of the tuple's constraints (lane k looks up constraint k)
-    u64 b = 0;
+    const u32 *row = nullptr;
     u32 l = 0;
-    if (lane < p.nc) lookup(p.c[lane].rows, p.c[lane].col[i], &b, &l);
-    const u64 gb = __shfl_sync(FULL_MASK, b, gen);
-    const u32 gl = __shfl_sync(FULL_MASK, l, gen);
-    u64 rb[MAXC];
+    u64 bp = 0;
+    if (lane < p.nc) bp = (u64)lookup(p.c[lane].rows, p.c[lane].col[i], &row, &l);
+    const u32 *rrow[MAXC];
     u32 rl[MAXC];
+    const u64 *rbits[MAXC];
 #pragma unroll
     for (int k = 0; k < MAXC; k++) {
-      rb[k] = __shfl_sync(FULL_MASK, b, k);
+      rrow[k] = (const u32 *)__shfl_sync(FULL_MASK, (u64)row, k);
       rl[k] = __shfl_sync(FULL_MASK, l, k);
+      rbits[k] = (const u64 *)__shfl_sync(FULL_MASK, bp, k);
     }
-    // the bound columns of the tuple, declaration order
+    // the bound columns of the tuple, declaration order, and their hash prefix
     u32 vals[RPQ_MAX_VARS];
 #pragma unroll
     for (int v = 0; v < RPQ_MAX_VARS; v++) vals[v] = (v < (int)lp.arity && lp.dcol[v]) ? lp.dcol[v][i] : 0u;
-    const u32 end = min(gl, (c + 1) * LAST_CHUNK);
+    u64 pre = 0;
+    if (lp.newpos >= 2) {
+      pre = splitmix64(((u64)vals[0] << 32) | (u64)vals[1]);
+      for (u32 v = 2; v < lp.newpos; v++) pre = splitmix64(pre ^ (u64)vals[v]);
+    }
+    if (gen == DENSE) {
+      const u64 w0 = (u64)c * DENSE_WORDS, w1 = min(p.bwords, w0 + DENSE_WORDS);
+      for (u64 w = w0 + lane; w < w1; w += 32) {
+        u64 m = p.lbits ? p.lbits[w] : ~0ull;
+#pragma unroll
+        for (int k = 0; k < MAXC; k++)
+          if (k < (int)p.nc) m &= rbits[k][w];
+        for (; m; m &= m - 1) {
+          const u64 h = last_hash(lp, vals, pre, (u32)(w * 64 + (__ffsll((long long)m) - 1)));
+          cnt++;
+          hs += h;
+          hx ^= h;
+        }
+      }
+      continue;
+    }
+    const u32 end = min(rl[gen], (c + 1) * LAST_CHUNK);
     for (u32 j = c * LAST_CHUNK + lane; j < end; j += 32) {
-      const u32 z = p.c[gen].rows.dst[gb + j];
+      const u32 z = rrow[gen][j];
       bool ok = p.want_label < 0 || p.vlabel[z] == (uint8_t)p.want_label;
       for (u32 k = 0; k < p.nc && ok; k++)
-        if (k != gen) ok = row_has(p.c[k].rows.dst, rb[k], rl[k], z);
+        if (k != gen) ok = member(rrow[k], rl[k], rbits[k], z);
       if (!ok) continue;
-      u64 h;
-      if (lp.arity == 1) {
-        h = splitmix64((u64)z);
-      } else {
-        const u32 a0 = lp.dcol[0] ? vals[0] : z, a1 = lp.dcol[1] ? vals[1] : z;
-        h = splitmix64(((u64)a0 << 32) | (u64)a1);
-        for (u32 v = 2; v < lp.arity; v++) h = splitmix64(h ^ (u64)(lp.dcol[v] ? vals[v] : z));
-      }
+      const u64 h = last_hash(lp, vals, pre, z);
       cnt++;
       hs += h;
       hx ^= h;
@@ -317,9 +405,12 @@ __global__ void count_last_kernel(const LastParams lp) {
   }
 }
 
-__global__ void chunk_counts(const u32 *__restrict__ cnt, u64 n, u32 *__restrict__ out) {
+// Items per tuple of the fused last step.
+__global__ void chunk_counts(const u32 *__restrict__ cnt, const uint8_t *__restrict__ which, u64 n, u64 bwords,
+                             u32 *__restrict__ out) {
   for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
-    out[i] = (cnt[i] + LAST_CHUNK - 1) / LAST_CHUNK;
+    out[i] = which[i] == DENSE ? (u32)((bwords + DENSE_WORDS - 1) / DENSE_WORDS)
+                               : (cnt[i] + LAST_CHUNK - 1) / LAST_CHUNK;
 }
 
 unsigned grid1(u64 n) {
@@ -348,11 +439,18 @@ struct Buf {
   ~Buf() { release(); }
 };
 
+// Rows of one atom: an index over the values (sorted) pointing into the
+// chunks the traversals wrote, which the rows own.
 struct OwnedRows {
-  Buf<u32> src, len, dst;
-  Buf<u64> beg;
+  rpq_ctx *ctx = nullptr;
+  Buf<u32> src, len;
+  Buf<u64> ptr, bptr;
+  std::vector<RowChunk> chunks;
   u32 ns = 0;
-  DevRows view() const { return DevRows{src.p, beg.p, len.p, dst.p, ns}; }
+  DevRows view() const { return DevRows{src.p, ptr.p, bptr.p, len.p, ns}; }
+  ~OwnedRows() {
+    for (auto &c : chunks) free_row_chunk(ctx, c);
+  }
 };
 
 struct Table {
@@ -381,6 +479,9 @@ struct Engine {
   Buf<u64> small;                       // digest accumulators, counters
   std::vector<Table> batch_out;         // complete tables of the current batch
   std::vector<std::pair<u32 *, uint64_t>> out_chunks;  // sorted row-major batches
+  double t_rows = 0, t_gen = 0, t_join = 0;  // host seconds per phase (trace)
+  Buf<u64> lbits;        // vertices of label lbits_label as a bitset
+  int lbits_label = -1;
 
   Engine(rpq_ctx *c, const rpq_graph *gr) : ctx(c), g(gr), dg(graph_dev(gr)), st(ctx_stream(c)) {
     std::memset(&stats, 0, sizeof(stats));
@@ -416,44 +517,67 @@ struct Engine {
     return RPQ_OK;
   }
 
-  // Rows of atom `a` for the given sorted distinct values.
-  int rows_for(uint32_t a, bool reverse, std::vector<uint32_t> &vals, OwnedRows *r) {
-    std::vector<RowChunk> chunks;
-    int rc = rpq_rows_for_sources(ctx, g, atoms[a].q, vals, reverse, &chunks, &stats);
-    uint64_t total = 0;
-    for (auto &c : chunks) total += c.rows;
+  // Rows of atom `a` for the given sorted distinct values.  Rows of at least
+  // crpq_bitset_frac * n destinations also come out as bitsets; with
+  // `fused` (a count-only last step) such rows are kept as bitsets only.
+  int rows_for(uint32_t a, bool reverse, std::vector<uint32_t> &vals, OwnedRows *r, bool fused) {
+    const double frac = ctx_crpq_bitset_frac(ctx);
+    RowBitsReq req;
+    req.min_len = std::max<uint64_t>(1, (uint64_t)std::ceil(frac * dg.n));
+    req.keep_lists = !fused;
+    const double t0 = host_seconds();
+    r->ctx = ctx;
+    int rc = rpq_rows_for_sources(ctx, g, atoms[a].q, vals, reverse, &r->chunks, &stats, nullptr, nullptr,
+                                  frac > 1.0 ? nullptr : &req);
+    const double t1 = host_seconds();
+    t_rows += t1 - t0;
     r->ns = (u32)vals.size();
-    if (!rc && ((rc = r->src.alloc(ctx, r->ns)) || (rc = r->beg.alloc(ctx, r->ns)) ||
-                (rc = r->len.alloc(ctx, r->ns)) || (rc = r->dst.alloc(ctx, total)))) {
+    if (!rc && ((rc = r->src.alloc(ctx, r->ns)) || (rc = r->ptr.alloc(ctx, r->ns)) ||
+                (rc = r->bptr.alloc(ctx, r->ns)) || (rc = r->len.alloc(ctx, r->ns)))) {
     }
     if (!rc && r->ns) {
-      // languages whose automaton is empty produce no chunks: all rows empty
+      // a value without a lane (no edge out of its start state, or an empty
+      // language) has no row: lookups of it find none
       cudaMemsetAsync(r->len.p, 0, (uint64_t)r->ns * 4, st);
-      cudaMemsetAsync(r->beg.p, 0, (uint64_t)r->ns * 8, st);
+      cudaMemsetAsync(r->ptr.p, 0, (uint64_t)r->ns * 8, st);
+      cudaMemsetAsync(r->bptr.p, 0, (uint64_t)r->ns * 8, st);
       cudaMemsetAsync(r->src.p, 0xff, (uint64_t)r->ns * 4, st);
-      if (chunks.empty()) {
-        // keep the source column sorted so lookups find every value
-        Buf<u32> tmp;
-        if (!(rc = tmp.alloc(ctx, r->ns)))
-          rc = cuda(cudaMemcpyAsync(r->src.p, vals.data(), (uint64_t)r->ns * 4, cudaMemcpyHostToDevice, st), "copy");
-        if (!rc) rc = cuda(cudaStreamSynchronize(st), "sync");
-      }
     }
-    uint64_t base = 0;
     uint32_t lane_base = 0;
-    for (auto &c : chunks) {
+    uint64_t n_bits = 0;
+    for (auto &c : r->chunks) {
       if (!rc) {
-        rows_index<<<grid1(c.n_lanes), 256, 0, st>>>(c.lanesrc, c.lane_off, c.n_lanes, lane_base, base, r->src.p,
-                                                     r->beg.p, r->len.p);
+        rows_index<<<grid1(c.n_lanes), 256, 0, st>>>(c.lanesrc, c.lane_off, c.n_lanes, lane_base, c.dst,
+                                                     c.lane_slot, c.bits, c.bwords, r->src.p, r->ptr.p, r->bptr.p,
+                                                     r->len.p, c.lists_kept ? 1u : 0u);
         rc = cuda(cudaGetLastError(), "rows_index");
-        if (!rc && c.rows)
-          rc = cuda(cudaMemcpyAsync(r->dst.p + base, c.dst, c.rows * 4, cudaMemcpyDeviceToDevice, st), "copy");
+        stats.launches += 1;
       }
-      base += c.rows;
       lane_base += c.n_lanes;
-      free_row_chunk(ctx, c);
+      n_bits += c.n_bits;
+    }
+    if (ctx_trace(ctx)) {
+      uint64_t listed = 0;
+      for (auto &c : r->chunks) listed += c.rows;
+      std::fprintf(stderr, "[rpq trace] crpq rows=%u listed=%llu bitsets=%llu (%.1f MB) %s\n", r->ns,
+                   (unsigned long long)listed, (unsigned long long)n_bits,
+                   n_bits * (((uint64_t)dg.n + 255) / 256 * 4) * 8 / 1e6, fused ? "bitsets only" : "lists kept");
     }
     return rc;
+  }
+
+  // Vertices of label `label` as a bitset of bwords words (kept per engine).
+  int label_bitset(int label, uint64_t bwords, const u64 **out) {
+    int rc;
+    if (lbits_label != label) {
+      if ((rc = lbits.alloc(ctx, bwords))) return rc;
+      label_bits<<<grid1(bwords), 256, 0, st>>>(dg.vlabel, dg.n, (uint8_t)label, bwords, lbits.p);
+      if ((rc = cuda(cudaGetLastError(), "label_bits"))) return rc;
+      stats.launches += 1;
+      lbits_label = label;
+    }
+    *out = lbits.p;
+    return RPQ_OK;
   }
 
   // Binds variable order[k] from the candidates (cand_t, cand_v) of table T
@@ -494,12 +618,14 @@ struct Engine {
   }
 
   // Fills p.c for the constraints of position k; self-loop rows come from
-  // the candidate values.
+  // the candidate values.  fused: the count-only last step.
   int prepare(int k, Table &T, const u32 *cand_v, uint64_t nc, std::vector<OwnedRows> &rows, StepParams &p,
-              bool self_only) {
+              bool self_only, bool fused) {
     std::memset(&p, 0, sizeof(p));
     p.want_label = label_of((uint32_t)order[k]);
     p.vlabel = dg.vlabel;
+    p.fused = fused ? 1u : 0u;
+    p.bwords = ((uint64_t)dg.n + 255) / 256 * 4;
     rows.resize(cons[k].size());
     int rc;
     for (size_t i = 0; i < cons[k].size(); i++) {
@@ -511,8 +637,9 @@ struct Engine {
       else
         rc = distinct(T.cols[c.bound_pos].p, T.n, &vals);
       if (rc) return rc;
-      if ((rc = rows_for(c.atom, c.reverse, vals, &rows[i]))) return rc;
+      if ((rc = rows_for(c.atom, c.reverse, vals, &rows[i], fused))) return rc;
     }
+    if (fused && p.want_label >= 0 && (rc = label_bitset(p.want_label, p.bwords, &p.lbits))) return rc;
     p.nc = (u32)cons[k].size();
     for (size_t i = 0; i < cons[k].size(); i++) {
       p.c[i].rows = rows[i].view();
@@ -525,9 +652,12 @@ struct Engine {
   int extend(int k, Table &T) {
     if (T.n == 0) return RPQ_OK;
     if (k == (int)n_vars) return emit(T);
+    bool has_self = false;
+    for (auto &c : cons[k]) has_self |= c.bound_pos < 0;
+    const bool fused = k == (int)n_vars - 1 && !materialize && !has_self;
     std::vector<OwnedRows> rows;
     StepParams p;
-    int rc = prepare(k, T, nullptr, 0, rows, p, false);
+    int rc = prepare(k, T, nullptr, 0, rows, p, false, fused);
     if (rc) return rc;
     Buf<u32> cnt;
     Buf<uint8_t> which;
@@ -535,6 +665,7 @@ struct Engine {
     if ((rc = cnt.alloc(ctx, T.n)) || (rc = which.alloc(ctx, T.n)) || (rc = off.alloc(ctx, T.n + 1)) ||
         (rc = tmp.alloc(ctx, scan_tmp_words(T.n + 1))))
       return rc;
+    const double t0 = host_seconds();
     choose_gen<<<grid1(T.n), 256, 0, st>>>(p, T.n, cnt.p, which.p);
     if ((rc = cuda(cudaGetLastError(), "choose_gen"))) return rc;
     if ((rc = cuda(exclusive_scan_u32_to_u64(cnt.p, off.p, T.n, small.p + 4, tmp.p, st), "scan"))) return rc;
@@ -543,9 +674,11 @@ struct Engine {
     if ((rc = cuda(cudaMemcpyAsync(off.p + T.n, small.p + 4, 8, cudaMemcpyDeviceToDevice, st), "copy"))) return rc;
     if ((rc = cuda(cudaStreamSynchronize(st), "sync"))) return rc;
     stats.launches += 2;
-    bool has_self = false;
-    for (auto &c : cons[k]) has_self |= c.bound_pos < 0;
-    if (k == (int)n_vars - 1 && !materialize && !has_self) return count_last(k, T, p, cnt.p, which.p);
+    t_gen += host_seconds() - t0;
+    if (ctx_trace(ctx))
+      std::fprintf(stderr, "[rpq trace] crpq bind k=%d tuples=%llu candidates=%llu\n", k, (unsigned long long)T.n,
+                   (unsigned long long)total);
+    if (fused) return count_last(k, T, p, cnt.p, which.p);
     for (u64 c0 = 0; c0 < total; c0 += CAND_CAP) {
       u64 nc = std::min<u64>(CAND_CAP, total - c0);
       Buf<u32> ct, cv;
@@ -558,7 +691,7 @@ struct Engine {
       StepParams ps = p;
       if (has_self) {
         StepParams tmpp;
-        if ((rc = prepare(k, T, cv.p, nc, self_rows, tmpp, true))) return rc;
+        if ((rc = prepare(k, T, cv.p, nc, self_rows, tmpp, true, false))) return rc;
         for (size_t i = 0; i < cons[k].size(); i++)
           if (cons[k][i].bound_pos < 0) ps.c[i].rows = self_rows[i].view();
       }
@@ -575,7 +708,7 @@ struct Engine {
     if ((rc = nch.alloc(ctx, T.n)) || (rc = coff.alloc(ctx, T.n + 1)) ||
         (rc = tmp.alloc(ctx, scan_tmp_words(T.n + 1))))
       return rc;
-    chunk_counts<<<grid1(T.n), 256, 0, st>>>(cnt, T.n, nch.p);
+    chunk_counts<<<grid1(T.n), 256, 0, st>>>(cnt, which, T.n, p.bwords, nch.p);
     if ((rc = cuda(cudaGetLastError(), "chunk_counts"))) return rc;
     if ((rc = cuda(exclusive_scan_u32_to_u64(nch.p, coff.p, T.n, small.p + 4, tmp.p, st), "scan"))) return rc;
     u64 items = 0, got = 0;
@@ -591,8 +724,10 @@ struct Engine {
     lp.nT = T.n;
     lp.items = items;
     lp.arity = n_vars;
+    lp.newpos = (u32)order[k];
     for (uint32_t v = 0; v < n_vars; v++) lp.dcol[v] = pos[v] < k ? T.cols[pos[v]].p : nullptr;
     lp.acc = small.p;
+    const double t0 = host_seconds();
     if (items) {
       const u64 warps = std::min<u64>(items, 152ull * 64);
       count_last_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(lp);
@@ -602,6 +737,7 @@ struct Engine {
         (rc = cuda(cudaStreamSynchronize(st), "sync")))
       return rc;
     stats.launches += 3;
+    t_join += host_seconds() - t0;
     count += got;
     return RPQ_OK;
   }
@@ -778,7 +914,7 @@ int crpq_eval(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_vars, const int32_t *
     Table T0;  // no columns yet
     std::vector<OwnedRows> rows;
     StepParams p;
-    if ((rc = E.prepare(0, T0, vals.p, nb, rows, p, true))) break;
+    if ((rc = E.prepare(0, T0, vals.p, nb, rows, p, true, false))) break;
     if ((rc = E.bind(0, T0, nullptr, vals.p, nb, p, nullptr))) break;
     rc = E.flush_batch();
   }
@@ -786,6 +922,10 @@ int crpq_eval(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_vars, const int32_t *
     for (auto &c : E.out_chunks) ctx_free(ctx, c.first, c.second * n_vars * 4);
     return rc;
   }
+  if (ctx_trace(ctx))
+    std::fprintf(stderr,
+                 "[rpq trace] crpq rows %.1f ms generators %.1f ms count_last %.1f ms\n", E.t_rows * 1e3,
+                 E.t_gen * 1e3, E.t_join * 1e3);
   // digest and final rows
   u64 dig[2] = {0, 0};
   if ((rc = E.cuda(cudaMemcpyAsync(dig, E.small.p, 16, cudaMemcpyDeviceToHost, st), "copy")) ||

@@ -18,6 +18,23 @@ struct RowChunk {
   u32 *dst = nullptr;
   uint64_t rows = 0;
   uint32_t n_lanes = 0;
+  // lanes whose rows are bitsets over the vertices (RowBitsReq): lane i's
+  // bitset is bits + lane_slot[i] * bwords when lane_slot[i] != NO_SOURCE;
+  // its destinations are listed in dst as well only when lists_kept
+  u64 *bits = nullptr;
+  u32 *lane_slot = nullptr;
+  uint64_t bwords = 0;
+  uint32_t n_bits = 0;
+  bool lists_kept = true;
+};
+
+// Rows of at least min_len destinations come out as bitsets of the vertices
+// (bwords 64-bit words each, bwords a multiple of 4), longest first while
+// the chunk's bitsets take at most half of the budget left; keep_lists: such
+// rows are listed in dst as well.
+struct RowBitsReq {
+  uint64_t min_len = 1;
+  bool keep_lists = true;
 };
 
 int ctx_alloc(rpq_ctx *ctx, void **p, uint64_t bytes);
@@ -28,6 +45,8 @@ int ctx_device(rpq_ctx *ctx);
 int ctx_bfs_blocks(rpq_ctx *ctx, int nw);
 int ctx_sm_share(rpq_ctx *ctx);  // SMs the context's persistent grids may use
 float ctx_alpha(rpq_ctx *ctx);
+double ctx_crpq_bitset_frac(rpq_ctx *ctx);  // rows of at least this fraction of the vertices get a bitset
+uint64_t ctx_budget_left(rpq_ctx *ctx);     // budget bytes not allocated
 bool ctx_trace(rpq_ctx *ctx);              // per-level trace printing (RPQ_TRACE=1)
 // alpha, time limit, spill capacity and batched-engine tuning of `from`
 void ctx_copy_tunables(rpq_ctx *to, const rpq_ctx *from);
@@ -52,7 +71,7 @@ const DevGraph &graph_dev(const rpq_graph *g);
 const HostQuery &query_host(const rpq_query *q);
 int rpq_rows_for_sources(rpq_ctx *ctx, const rpq_graph *g, const rpq_query *q, std::vector<uint32_t> &srcs,
                          bool reverse, std::vector<RowChunk> *chunks, rpq_stats *stats, uint64_t *dsum = nullptr,
-                         uint64_t *dxor = nullptr);
+                         uint64_t *dxor = nullptr, const RowBitsReq *bits_req = nullptr);
 void free_row_chunk(rpq_ctx *ctx, RowChunk &c);
 // One automaton and at most 64 start vertices: a lane group of a
 // multi-automaton launch.

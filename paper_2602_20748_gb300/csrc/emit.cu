@@ -25,6 +25,8 @@
 // complete, the warp stores it: four rows per store instruction, eight lanes
 // per row, 16 bytes per lane -- whole sectors, with only the first and last
 // chunk of a row stored word by word where they are partial.
+#include <algorithm>
+
 #include "device_common.cuh"
 #include "rpq_internal.h"
 
@@ -229,6 +231,14 @@ __global__ void __launch_bounds__(64 * NW, NW == 1 ? 16 : 3) emit_write_kernel(c
   const u64 pos0 = p.off[glane * p.segs + seg];
   u32 *base = p.dst + (pos0 & ~31ull);
   u32 rd = (u32)pos0 & 31u, wr = rd;  // stored / placed words of this row, relative to base
+  // the lane's bitset (a 32-bit word per tile, stored 8 words = 32 bytes per
+  // batch), and whether its destinations are listed as well
+  u32 *bs = nullptr;
+  if (p.lane_slot) {
+    const u32 slot = p.lane_slot[glane];
+    if (slot != NO_SOURCE) bs = reinterpret_cast<u32 *>(p.bits + (u64)slot * p.bwords);
+  }
+  const bool listed = !bs || p.keep_lists;
   const u32 w_begin = seg * EMIT_SEG;
   const u32 n_tiles = min((u32)EMIT_TILES, (p.n - w_begin + 31) / 32);
   u64 pre[4];
@@ -241,8 +251,14 @@ __global__ void __launch_bounds__(64 * NW, NW == 1 ? 16 : 3) emit_write_kernel(c
     if (tb + EMIT_BATCH < n_tiles)  // next batch in flight while this one is placed
       batch_fetch<NW>(p, p.final_mask, g, w_begin + (tb + EMIT_BATCH) * 32,
                       min(EMIT_BATCH, n_tiles - tb - EMIT_BATCH) * 32, pre);
-    for (u32 t = 0; t < nt; t++) {
+    u32 acc[EMIT_BATCH];
+#pragma unroll
+    for (u32 t = 0; t < EMIT_BATCH; t++) {
+      acc[t] = 0;
+      if (t >= nt) continue;  // uniform across the block
       u32 m = warp_transpose32(s_vis[col * EMIT_BV + t * 32 + lane] & valid_cols);
+      acc[t] = m;
+      if (!listed) m = 0;
       const u32 wb = w_begin + (tb + t) * 32 - 1;
       // at most 31 words were pending, so the ring (64) holds this tile's 32
       for (; m; m &= m - 1) myring[wr++ & (EMIT_RING - 1)] = wb + __ffs(m);
@@ -252,6 +268,11 @@ __global__ void __launch_bounds__(64 * NW, NW == 1 ? 16 : 3) emit_write_kernel(c
         ring_flush(R, rd, (rd | 31u) + 1u, base, ring, slots);
         if (full) rd = (rd | 31u) + 1u;
       }
+    }
+    if (bs) {  // the batch's 256 vertices start on a 32-byte boundary of the bitset
+      uint4 *d = reinterpret_cast<uint4 *>(bs + (w_begin + tb * 32) / 32);
+      d[0] = make_uint4(acc[0], acc[1], acc[2], acc[3]);
+      d[1] = make_uint4(acc[4], acc[5], acc[6], acc[7]);
     }
   }
   const u32 R = __ballot_sync(FULL_MASK, wr > rd);  // the partial last chunks
@@ -444,6 +465,19 @@ __global__ void gather_lane_off(const u64 *__restrict__ off, u32 segs, u32 n_lan
                                 u64 *__restrict__ lane_off) {
   for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i <= n_lanes; i += gridDim.x * blockDim.x)
     lane_off[i] = (i == n_lanes) ? *total : off[(u64)i * segs];
+}
+
+__global__ void zero_lane_counts(u32 *__restrict__ cnt, u32 segs, u32 n_lanes, const u32 *__restrict__ lane_slot) {
+  const u64 total = (u64)n_lanes * segs;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (u64)gridDim.x * blockDim.x)
+    if (lane_slot[i / segs] != NO_SOURCE) cnt[i] = 0;
+}
+
+cudaError_t launch_zero_lane_counts(u32 *cnt, u32 segs, u32 n_lanes, const u32 *lane_slot, cudaStream_t st) {
+  const u64 total = (u64)n_lanes * segs;
+  const u64 blocks = std::min<u64>((total + 255) / 256, 152ull * 16);
+  zero_lane_counts<<<(unsigned)std::max<u64>(blocks, 1), 256, 0, st>>>(cnt, segs, n_lanes, lane_slot);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gather_lane_off(const u64 *off, u32 segs, u32 n_lanes, const u64 *total, u64 *lane_off,

@@ -228,6 +228,15 @@ struct EmitParams {
   // * NW + k] holds the lanes of word k of group g whose automaton accepts in
   // state q (final_mask is then the union of the lanes' accepting states)
   const unsigned long long *final_lane;
+  // write pass: lanes whose rows also go out as bitsets over the vertices.
+  // lane_slot[lane] = the lane's bitset index (bitset at bits + slot *
+  // bwords, bwords a multiple of 4), NO_SOURCE for none; nullptr: no
+  // bitsets.  With keep_lists = 0 such lanes write no destinations (their
+  // counts must have been zeroed before the offsets were scanned).
+  const uint32_t *lane_slot;
+  unsigned long long *bits;
+  uint64_t bwords;
+  uint32_t keep_lists;
 };
 constexpr int EMIT_TILES = 128;  // 32-vertex tiles per segment
 constexpr int EMIT_SEG = 32 * EMIT_TILES;
@@ -250,6 +259,9 @@ cudaError_t preload_static_msbfs_kernels();
 cudaError_t preload_static_emit_kernels();
 cudaError_t preload_scan_kernels();
 
+// cnt[lane][*] = 0 for every lane with lane_slot[lane] != NO_SOURCE.
+cudaError_t launch_zero_lane_counts(uint32_t *cnt, uint32_t segs, uint32_t n_lanes, const uint32_t *lane_slot,
+                                    cudaStream_t st);
 cudaError_t launch_gather_lane_off(const unsigned long long *off, uint32_t segs, uint32_t n_lanes,
                                    const unsigned long long *total, unsigned long long *lane_off, cudaStream_t st);
 

@@ -109,6 +109,18 @@ def test_random_crpq(ctx, case):
     # count only: the last variable is bound, counted and digested in one pass
     _, info_c = crpq_gpu(ctx, g, nv, atoms, var_label=var_label, restrict0=restrict0, flags=rpq.RPQ_COUNT_ONLY)
     assert (info_c[0], info_c[2], info_c[3]) == oracle.row_digest(want.rows), atoms
+    # membership tests by binary search only (no bitsets), and by bitsets of
+    # every non-empty row
+    try:
+        for frac in (2.0, 0.0):
+            rpq.rpq_set_option(ctx, "crpq_bitset_frac", frac)
+            rows, _ = crpq_gpu(ctx, g, nv, atoms, var_label=var_label, restrict0=restrict0)
+            assert rows.tolist() == want.rows.tolist(), (frac, atoms)
+            _, info_c = crpq_gpu(ctx, g, nv, atoms, var_label=var_label, restrict0=restrict0,
+                                 flags=rpq.RPQ_COUNT_ONLY)
+            assert (info_c[0], info_c[2], info_c[3]) == oracle.row_digest(want.rows), (frac, atoms)
+    finally:
+        rpq.rpq_set_option(ctx, "crpq_bitset_frac", 1 / 64)
 
 
 def test_crpq_errors(ctx):
@@ -154,6 +166,12 @@ def test_rmat22_triangle_sampled(ctx, rmat22):
     assert (info[0], info[2], info[3]) == oracle.row_digest(want.rows)
     _, info_c = crpq_gpu(ctx, g, 3, TRIANGLE, restrict0=sample, flags=rpq.RPQ_COUNT_ONLY)
     assert (info_c[0], info_c[2], info_c[3]) == oracle.row_digest(want.rows)
+    try:  # binary search only
+        rpq.rpq_set_option(ctx, "crpq_bitset_frac", 2.0)
+        _, info_c = crpq_gpu(ctx, g, 3, TRIANGLE, restrict0=sample, flags=rpq.RPQ_COUNT_ONLY)
+        assert (info_c[0], info_c[2], info_c[3]) == oracle.row_digest(want.rows)
+    finally:
+        rpq.rpq_set_option(ctx, "crpq_bitset_frac", 1 / 64)
     # with vertex labels on y and z
     vlab = [-1, 1, 2]
     want = oracle.crpq(og, 3, TRIANGLE, var_label=vlab, restrict0=sample)
