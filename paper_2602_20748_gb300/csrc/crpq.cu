@@ -306,26 +306,42 @@ struct LastParams {
   u64 *acc;                      // [0] digest sum, [1] digest xor, [5] count
 };
 
-// Digest hash of the tuple (vals with z at position newpos), given pre = the
-// fold over positions 0 .. newpos - 1 when newpos >= 2 (see result_info).
-__device__ __forceinline__ u64 last_hash(const LastParams &lp, const u32 (&vals)[RPQ_MAX_VARS], u64 pre, u32 z) {
-  u64 h;
+constexpr int CL_THREADS = 256;
+constexpr int CL_WARPS = CL_THREADS / 32;
+
+// Per-warp state of an item: the rows of the tuple's constraints and the
+// tuple's bound values (declaration order).
+struct LastWarp {
+  const u32 *row[MAXC];
+  const u64 *bits[MAXC];
+  u32 len[MAXC];
+  u32 vals[RPQ_MAX_VARS];
+};
+
+// Digest hash of the tuple (bound values with z at position newpos), given
+// pre = the fold over positions 0 .. newpos - 1 when newpos >= 2 (see
+// result_info).
+__device__ __forceinline__ u64 last_hash(const LastParams &lp, const LastWarp &sw, u64 pre, u32 z) {
+  if (lp.newpos >= 2 && lp.newpos + 1 == lp.arity) return splitmix64(pre ^ (u64)z);  // the common case
   if (lp.arity == 1) return splitmix64((u64)z);
+  u64 h;
   u32 v;
   if (lp.newpos >= 2) {
     h = splitmix64(pre ^ (u64)z);
     v = lp.newpos + 1;
   } else {
-    const u32 a0 = lp.newpos == 0 ? z : vals[0], a1 = lp.newpos == 1 ? z : vals[1];
+    const u32 a0 = lp.newpos == 0 ? z : sw.vals[0], a1 = lp.newpos == 1 ? z : sw.vals[1];
     h = splitmix64(((u64)a0 << 32) | (u64)a1);
     v = 2;
   }
-  for (; v < lp.arity; v++) h = splitmix64(h ^ (u64)vals[v]);
+  for (; v < lp.arity; v++) h = splitmix64(h ^ (u64)sw.vals[v]);
   return h;
 }
 
-__global__ void count_last_kernel(const LastParams lp) {
+__global__ void __launch_bounds__(CL_THREADS) count_last_kernel(const LastParams lp) {
+  __shared__ LastWarp s_warp[CL_WARPS];
   const StepParams &p = lp.p;
+  LastWarp &sw = s_warp[threadIdx.x >> 5];
   const u64 warp = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
   const u32 lane = lane_id();
@@ -343,38 +359,49 @@ __global__ void count_last_kernel(const LastParams lp) {
     const u64 i = lo;
     const u32 gen = lp.which[i];
     const u32 c = (u32)(t - lp.coff[i]);
-    // rows of the tuple's constraints (lane k looks up constraint k)
-    const u32 *row = nullptr;
-    u32 l = 0;
-    u64 bp = 0;
-    if (lane < p.nc) bp = (u64)lookup(p.c[lane].rows, p.c[lane].col[i], &row, &l);
-    const u32 *rrow[MAXC];
-    u32 rl[MAXC];
-    const u64 *rbits[MAXC];
-#pragma unroll
-    for (int k = 0; k < MAXC; k++) {
-      rrow[k] = (const u32 *)__shfl_sync(FULL_MASK, (u64)row, k);
-      rl[k] = __shfl_sync(FULL_MASK, l, k);
-      rbits[k] = (const u64 *)__shfl_sync(FULL_MASK, bp, k);
-    }
-    // the bound columns of the tuple, declaration order, and their hash prefix
-    u32 vals[RPQ_MAX_VARS];
-#pragma unroll
-    for (int v = 0; v < RPQ_MAX_VARS; v++) vals[v] = (v < (int)lp.arity && lp.dcol[v]) ? lp.dcol[v][i] : 0u;
+    __syncwarp();  // the previous item's readers are done
+    // rows of the tuple's constraints (lane k looks up constraint k), bound values
+    if (lane < p.nc) sw.bits[lane] = lookup(p.c[lane].rows, p.c[lane].col[i], &sw.row[lane], &sw.len[lane]);
+    if (lane < lp.arity) sw.vals[lane] = lp.dcol[lane] ? lp.dcol[lane][i] : 0u;
+    __syncwarp();
     u64 pre = 0;
     if (lp.newpos >= 2) {
-      pre = splitmix64(((u64)vals[0] << 32) | (u64)vals[1]);
-      for (u32 v = 2; v < lp.newpos; v++) pre = splitmix64(pre ^ (u64)vals[v]);
+      pre = splitmix64(((u64)sw.vals[0] << 32) | (u64)sw.vals[1]);
+      for (u32 v = 2; v < lp.newpos; v++) pre = splitmix64(pre ^ (u64)sw.vals[v]);
     }
     if (gen == DENSE) {
+      // words w0 + lane + 32 j of the AND, four per round; a lane walks the
+      // set bits of its four words in one loop, so that lanes wait for the
+      // largest four-word count rather than the largest one-word count
+      const u64 *b0 = sw.bits[0], *b1 = p.nc > 1 ? sw.bits[1] : nullptr;
       const u64 w0 = (u64)c * DENSE_WORDS, w1 = min(p.bwords, w0 + DENSE_WORDS);
-      for (u64 w = w0 + lane; w < w1; w += 32) {
-        u64 m = p.lbits ? p.lbits[w] : ~0ull;
+      for (u64 wb = w0; wb < w1; wb += 128) {
+        u64 m[4];
 #pragma unroll
-        for (int k = 0; k < MAXC; k++)
-          if (k < (int)p.nc) m &= rbits[k][w];
-        for (; m; m &= m - 1) {
-          const u64 h = last_hash(lp, vals, pre, (u32)(w * 64 + (__ffsll((long long)m) - 1)));
+        for (int j = 0; j < 4; j++) {
+          const u64 w = wb + lane + 32 * j;
+          u64 x = 0;
+          if (w < w1) {
+            x = p.lbits ? p.lbits[w] : ~0ull;
+            x &= b0[w];
+            if (b1) x &= b1[w];
+            for (u32 k = 2; k < p.nc; k++) x &= sw.bits[k][w];
+          }
+          m[j] = x;
+        }
+        u64 cur = m[0], base = (wb + lane) * 64;
+        u32 left = 3;
+        for (;;) {
+          while (!cur && left) {  // next word of the four
+            cur = m[1];
+            m[1] = m[2];
+            m[2] = m[3];
+            base += 32 * 64;
+            left--;
+          }
+          if (!cur) break;
+          const u64 h = last_hash(lp, sw, pre, (u32)(base + (__ffsll((long long)cur) - 1)));
+          cur &= cur - 1;
           cnt++;
           hs += h;
           hx ^= h;
@@ -382,14 +409,15 @@ __global__ void count_last_kernel(const LastParams lp) {
       }
       continue;
     }
-    const u32 end = min(rl[gen], (c + 1) * LAST_CHUNK);
+    const u32 *grow = sw.row[gen];
+    const u32 end = min(sw.len[gen], (c + 1) * LAST_CHUNK);
     for (u32 j = c * LAST_CHUNK + lane; j < end; j += 32) {
-      const u32 z = rrow[gen][j];
+      const u32 z = grow[j];
       bool ok = p.want_label < 0 || p.vlabel[z] == (uint8_t)p.want_label;
       for (u32 k = 0; k < p.nc && ok; k++)
-        if (k != gen) ok = member(rrow[k], rl[k], rbits[k], z);
+        if (k != gen) ok = member(sw.row[k], sw.len[k], sw.bits[k], z);
       if (!ok) continue;
-      const u64 h = last_hash(lp, vals, pre, z);
+      const u64 h = last_hash(lp, sw, pre, z);
       cnt++;
       hs += h;
       hx ^= h;
@@ -730,7 +758,7 @@ struct Engine {
     const double t0 = host_seconds();
     if (items) {
       const u64 warps = std::min<u64>(items, 152ull * 64);
-      count_last_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(lp);
+      count_last_kernel<<<(unsigned)((warps * 32 + CL_THREADS - 1) / CL_THREADS), CL_THREADS, 0, st>>>(lp);
       if ((rc = cuda(cudaGetLastError(), "count_last"))) return rc;
     }
     if ((rc = cuda(cudaMemcpyAsync(&got, small.p + 5, 8, cudaMemcpyDeviceToHost, st), "copy")) ||
