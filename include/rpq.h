@@ -113,6 +113,11 @@ int rpq_set_stream(rpq_ctx *ctx, void *cuda_stream);
  *                  below the bottom-up bytes (default 16)
  *   "lane_alpha"   the same for lane-mode launches (one automaton per lane;
  *                  default 2)
+ *   "lane_by_source" 1 (default): bottom-up levels of lane-mode launches
+ *                  whose union automaton has at most 8 states gather a
+ *                  neighbour's frontier words once per (label, source state)
+ *                  and mask them into every target state; 0: once per union
+ *                  transition (same results)
  *   "crpq_bitset_frac" run_crpq: an atom's row with at least this fraction
  *                  of the vertices among its destinations is also written as
  *                  a bitset over the vertices, so that a membership test in

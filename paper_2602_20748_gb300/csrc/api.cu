@@ -60,6 +60,7 @@ struct rpq_ctx {
   float alpha = 16.0f;
   float lane_alpha = 2.0f;  // the same trade-off for lane-mode launches
   unsigned pull_dynamic = 1;  // bottom-up vertex chunks from a cursor
+  unsigned lane_by_source = 1;  // lane-mode light rows gathered per (label, source state)
   double crpq_bitset_frac = 1.0 / 64;  // CRPQ rows of at least this fraction of the vertices get a bitset
   uint64_t time_limit_ns = 20ull * 1000 * 1000 * 1000;
   uint32_t max_groups = 16;
@@ -493,6 +494,7 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
     p.force = force;
     p.alpha = ctx->alpha;
     p.pull_dynamic = ctx->pull_dynamic;
+  p.lane_by_source = ctx->lane_by_source;
     p.time_limit_ns = ctx->time_limit_ns;
     p.q = qd;
 
@@ -870,6 +872,8 @@ int rpq_set_option(rpq_ctx *ctx, const char *name, double value) {
     ctx->lane_alpha = (float)value;
   } else if (n == "pull_dynamic" && (value == 0 || value == 1)) {
     ctx->pull_dynamic = value != 0 ? 1u : 0u;
+  } else if (n == "lane_by_source" && (value == 0 || value == 1)) {
+    ctx->lane_by_source = value != 0 ? 1u : 0u;
   } else if (n == "crpq_bitset_frac" && value >= 0 && value <= 2) {
     ctx->crpq_bitset_frac = value;
   } else if (n == "grid_share" && value > 0 && value <= 1) {
@@ -905,6 +909,8 @@ int rpq_get_option(const rpq_ctx *ctx, const char *name, double *value) {
     *value = ctx->lane_alpha;
   else if (n == "pull_dynamic")
     *value = ctx->pull_dynamic;
+  else if (n == "lane_by_source")
+    *value = ctx->lane_by_source;
   else if (n == "crpq_bitset_frac")
     *value = ctx->crpq_bitset_frac;
   else if (n == "grid_share")
@@ -1483,6 +1489,7 @@ void ctx_copy_tunables(rpq_ctx *to, const rpq_ctx *from) {
   to->alpha = from->alpha;
   to->lane_alpha = from->lane_alpha;
   to->pull_dynamic = from->pull_dynamic;
+  to->lane_by_source = from->lane_by_source;
   to->crpq_bitset_frac = from->crpq_bitset_frac;
   to->time_limit_ns = from->time_limit_ns;
   to->spill_cap = from->spill_cap;
@@ -1782,6 +1789,7 @@ int rpq_lane_stats_multi(rpq_ctx *ctx, const rpq_graph *gr, const std::vector<Mu
   p.force = 0;
   p.alpha = ctx->alpha;
   p.pull_dynamic = ctx->pull_dynamic;
+  p.lane_by_source = ctx->lane_by_source;
   p.time_limit_ns = ctx->time_limit_ns;
   p.q = un;
   p.qg = d_desc;
@@ -2011,6 +2019,7 @@ static int lane_launch(rpq_ctx *ctx, const rpq_graph *gr, const std::vector<Lane
   p.force = 0;
   p.alpha = ctx->alpha;
   p.pull_dynamic = ctx->pull_dynamic;
+  p.lane_by_source = ctx->lane_by_source;
   p.time_limit_ns = ctx->time_limit_ns;
   p.q = un;
   p.alpha = ctx->lane_alpha;

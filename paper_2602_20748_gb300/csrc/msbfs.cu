@@ -149,6 +149,9 @@ __device__ bool grid_barrier(BfsCtl *c, unsigned nblocks, u64 limit_ns) {
 // Automaton modes of a launch: one automaton for every lane, one per lane
 // group (multi), or one per lane (lane mode).
 constexpr int AM_ONE = 0, AM_GROUP = 1, AM_LANE = 2;
+// Lane-mode bottom-up by source state (see pull_level) for unions of at most
+// this many states; larger ones gather per target state.
+constexpr u32 LANE_SRC_Q = 8;
 
 // Automaton of group g: its own in multi mode, else the launch's (the union
 // in lane mode).
@@ -769,6 +772,87 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
       const u32 vt = __shfl_sync(FULL_MASK, tmask, s);
       const bool wv = vq != 0;
       const u32 w = wv ? (u32)(c0 + s) : 0;
+    if constexpr (AM == AM_LANE) {
+      if (p.lane_by_source && Q <= LANE_SRC_Q) {
+        // Lane mode by source state.  Target q2's new lanes are the OR over
+        // its union transitions t = (s, l, q2) and the in-edges (v, w) of
+        // label l of F[s][v] & mask(t); since the mask does not depend on v,
+        // that is the OR over t of mask(t) & (OR over v of F[s][v]).  So the
+        // frontier words of each (label, source state) are gathered once and
+        // ORed over the in-edges, then masked into every target taking a
+        // transition from them (accumulated per lane in shared memory); the
+        // per-target order gathers each (s, v) once per target instead.
+        __shared__ u64 s_lane_acc[BFS_THREADS / 32][LANE_SRC_Q * 2 * 32];
+        u64 *sacc = s_lane_acc[threadIdx.x >> 5];  // [q2][k][lane]
+        u32 wmask = 0;  // targets with lanes to find (uniform within the sub-warp)
+        for (u32 q2 = 0; q2 < Q; q2++) {
+          const bool any = wv && ((vq >> q2) & 1u);
+          u64 vis[PER];
+          load_vis<PER>(p.vis + ((u64)q2 * n + w) * wpv + lane_off, lane_on && any, vis);
+          bool full = true;
+#pragma unroll
+          for (int k = 0; k < PER; k++) {
+            full &= vis[k] == ~0ull;
+            sacc[(q2 * PER + k) * 32 + lane] = 0;
+          }
+          const u32 fb = __ballot_sync(FULL_MASK, full);
+          if (any && (fb & sg_mask) != sg_mask) wmask |= 1u << q2;
+        }
+        u64 lset = 0;  // labels of the work targets' active transitions
+        for (u32 q2 = 0; q2 < Q; q2++)
+          if ((wmask >> q2) & 1u)
+            for (u32 j = p.q.in_begin[q2]; j < p.q.in_begin[q2 + 1]; j++)
+              if ((p.q.in_from[j] & active) && p.q.in_label[j] < p.L) lset |= 1ull << p.q.in_label[j];
+        for (; lset; lset &= lset - 1) {
+          const u32 l = __ffsll((long long)lset) - 1;
+          const u32 *off = p.in_off + (u64)l * n1 + w;
+          const u32 beg = __ldg(off), end = __ldg(off + 1);
+          if (beg == end || (end - beg >= HEAVY_ROW && chunked)) continue;
+          u32 S = 0;  // source states of those transitions on label l
+          for (u32 q2 = 0; q2 < Q; q2++)
+            if ((wmask >> q2) & 1u)
+              for (u32 j = p.q.in_begin[q2]; j < p.q.in_begin[q2 + 1]; j++)
+                if (p.q.in_label[j] == l) S |= p.q.in_from[j] & active;
+          for (; S; S &= S - 1) {
+            const u32 st = __ffs(S) - 1;
+            u64 g[PER], none[PER];
+#pragma unroll
+            for (int k = 0; k < PER; k++) g[k] = none[k] = 0;
+            u32 gat = 0;
+            const u32 ex = gather_row<NW, PER, false, false>(p, F, bits, 1u << st, beg, end, lane_off, lane_on,
+                                                             sg_mask, none, g, gat, nullptr);
+            edges += (li == 0) ? ex : 0;
+            bytes += (li == 0) ? 8 + (u64)ex * (4 + (bits ? 4 : 0)) + (u64)gat * gword : 0;
+            bool nz = false;
+#pragma unroll
+            for (int k = 0; k < PER; k++) nz |= g[k] != 0;
+            if (!nz) continue;
+            for (u32 q2 = 0; q2 < Q; q2++) {
+              if (!((wmask >> q2) & 1u)) continue;
+              for (u32 j = p.q.in_begin[q2]; j < p.q.in_begin[q2 + 1]; j++) {
+                if (p.q.in_label[j] != l || !((p.q.in_from[j] >> st) & 1u)) continue;
+                const u64 *mk = p.la_mask + (u64)p.la_in_t[(u64)j * Q + st] * wpv + lane_off;
+#pragma unroll
+                for (int k = 0; k < PER; k++) sacc[(q2 * PER + k) * 32 + lane] |= g[k] & __ldg(mk + k);
+              }
+            }
+          }
+        }
+        for (u32 q2 = 0; q2 < Q; q2++) {
+          const bool work = ((wmask >> q2) & 1u) != 0;
+          if (!__any_sync(FULL_MASK, work)) continue;
+          u64 vis[PER], acc[PER];
+          load_vis<PER>(p.vis + ((u64)q2 * n + w) * wpv + lane_off, lane_on && work, vis);
+#pragma unroll
+          for (int k = 0; k < PER; k++) acc[k] = sacc[(q2 * PER + k) * 32 + lane];
+          words += (li == 0 && work);
+          bytes += (li == 0 && work) ? gword : 0;
+          pull_finish<NW, PER>(p, app, FB, nlist, nxt, q2, w, stamp, li, lane_on && work, my_g,
+                               ((vh >> q2) & 1u) != 0, vis, acc);
+        }
+        continue;
+      }
+    }
     for (u32 q2 = 0; q2 < Q; q2++) {
       const u32 gb = p.q.in_begin[q2], ge = p.q.in_begin[q2 + 1];
       bool any = wv && ((vq >> q2) & 1u);

@@ -188,6 +188,7 @@ struct BfsParams {
   unsigned int stamp_base;     // claim stamps continue across launches
   unsigned int nblocks;
   unsigned int pull_dynamic;   // bottom-up levels take vertex chunks from a cursor (else round-robin)
+  unsigned int lane_by_source; // lane mode: light bottom-up rows gathered once per (label, source state)
   int force;                   // 0 auto, 1 push only, 2 pull only
   float alpha;                 // push if alpha * push_cost < pull_cost
   unsigned long long time_limit_ns;

@@ -189,6 +189,7 @@ extern "C" int run_rpq_static(rpq_ctx *ctx, const rpq_graph *g, const rpq_query 
   p.force = 0;
   p.alpha = ctx_alpha(ctx);
   p.pull_dynamic = 1;
+  p.lane_by_source = 1;
   p.hchunk = nullptr;  // long rows are scanned in place
   for (uint32_t l = 0; l < dg.L; l++) p.label_edges[l] = dg.label_edges[l];
   p.time_limit_ns = ctx_time_limit_ns(ctx);

@@ -67,6 +67,7 @@ def test_lanes_direct_match_oracle(lanes, alpha):
     rpq.rpq_set_option(c, "batch_direct", 1)
     rpq.rpq_set_option(c, "batch_lanes", lanes)
     rpq.rpq_set_option(c, "alpha", alpha)
+    rpq.rpq_set_option(c, "lane_alpha", alpha)  # lane-mode launches take their own
     n, L = 20000, 4
     src, dst, lab = _graph(n, 160000, L, seed=57)
     g = rpq.load_graph(c, n, L, src, dst, lab)
@@ -130,3 +131,22 @@ def test_autotune_then_batch_match_oracle():
     rpq.rpq_autotune_batch(c, g, qs, sources)
     assert rpq.rpq_get_option(c, "batch_lanes") == 4096
     _check(c, g, og, regexes, sources)
+
+
+@pytest.mark.parametrize("by_source", [0, 1])
+def test_lanes_gather_order_match_oracle(by_source):
+    """Bottom-up levels of lane-mode launches gather a neighbour's frontier
+    words once per (label, source state) and mask them into every target
+    (by_source = 1, unions of up to 8 states), or once per union transition
+    (by_source = 0); both agree with the oracle, with hub rows in the mix."""
+    c = rpq.Context(device=0)
+    rpq.rpq_set_option(c, "batch_direct", 1)
+    rpq.rpq_set_option(c, "lane_by_source", by_source)
+    rpq.rpq_set_option(c, "lane_alpha", 1e9)  # every lane-mode level bottom-up
+    n, L = 12000, 3
+    src, dst, lab = _graph(n, 60000, L, seed=91, hubs=True)
+    g = rpq.load_graph(c, n, L, src, dst, lab)
+    og = oracle.Graph(n, L, src, dst, lab)
+    regexes, sources = _mix(300, L, src, n, seed=93)
+    r = _check(c, g, og, regexes, sources)
+    assert rpq.result_stats(r)["evicted"] == len(regexes)
