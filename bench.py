@@ -62,6 +62,8 @@ def parse_args():
                          "stream of mixed requests on R-MAT 2^24")
     ap.add_argument("--scale", type=int, default=None,
                     help="R-MAT scale (vertices 2^scale, 16 * 2^scale edges); smaller cases are for profiling")
+    ap.add_argument("--full", action="store_true",
+                    help="crpq: also count the whole query (every x value) in one timed call")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: mean arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serve: arrival window (s)")
     ap.add_argument("--drain", type=float, default=10.0, help="serve: time after the window before cancelling (s)")
@@ -591,6 +593,20 @@ def bench_crpq(args, compact: bool = False):
         rpq.run_rpq(ctx, g, q, s_, flags=rpq.RPQ_COUNT_ONLY).free()
         torch.cuda.synchronize()
         per_atom[name] = 1000.0 * (time.perf_counter() - t1)
+    full = None
+    if args.full and not compact:
+        # the whole query: every x value, batches of 4,096 inside one call
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        r = rpq.run_crpq(ctx, g, 3, atoms, flags=rpq.RPQ_COUNT_ONLY)
+        torch.cuda.synchronize()
+        full_s = time.perf_counter() - t1
+        c_, _, hs_, hx_ = rpq.result_info(r)
+        st_ = rpq.result_stats(r)
+        r.free()
+        full = {"x_values": n, "tuples": c_, "seconds": full_s, "tuples_per_s": c_ / full_s,
+                "digest": [hs_, hx_], "atom_product_edges": st_["product_edges"],
+                "bfs_ms": st_["bfs_ms"], "emit_ms": st_["emit_ms"]}
     for q in (qa, qbc, qd):
         q.free()
     g.free()
@@ -599,6 +615,7 @@ def bench_crpq(args, compact: bool = False):
         "tuples_per_s": tuples / (ms * args.steps / 1000.0), "ms_per_step": ms, "x_per_step": B,
         "tuples_per_step": tuples // args.steps, "atom_product_edges_per_step": W // args.steps,
         "per_atom_ms": per_atom,
+        **({"full_query": full} if full else {}),
         "config": {"workload": "rmat22-triangle-crpq", "atoms": ["x -a-> y", "x -b.c*-> z", "y -d*-> z"],
                    "vertices": n, "generated_edges": 1 << 26, "labels": 10, "zipf_s": 1.1, "vertex_labels": 5,
                    "mode": "count only", "generation_s": round(gen_s, 1)},
