@@ -2062,9 +2062,10 @@ static int lane_launch(rpq_ctx *ctx, const rpq_graph *gr, const std::vector<Lane
     std::fprintf(stderr, "[rpq trace] lanes k=%u G=%u NW=%d Q=%u T=%u levels=%llu W=%llu\n", k, G, nw, Q, T,
                  (unsigned long long)hctl.levels, (unsigned long long)hctl.stats[ST_W]);
     for (uint32_t l = 0; l < nl; l++)
-      std::fprintf(stderr, "[rpq trace]   level %2u %s n=%10llu mf=%12llu %9.3f ms\n", l,
+      std::fprintf(stderr, "[rpq trace]   level %2u %s n=%10llu mf=%12llu %9.3f ms (commit %7.3f ms)\n", l,
                    hctl.trace_mode[l] == 1 ? "push" : "pull", (unsigned long long)hctl.trace_n[l],
-                   (unsigned long long)hctl.trace_mf[l], (hctl.trace_t[l + 1] - hctl.trace_t[l]) * 1e-6);
+                   (unsigned long long)hctl.trace_mf[l], (hctl.trace_t[l + 1] - hctl.trace_t[l]) * 1e-6,
+                   hctl.trace_c[l] ? (hctl.trace_t[l + 1] - hctl.trace_c[l]) * 1e-6 : 0.0);
   }
   if (stats) {
     float ms_bfs = 0, ms_emit = 0;

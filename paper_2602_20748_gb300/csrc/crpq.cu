@@ -389,23 +389,29 @@ __global__ void __launch_bounds__(CL_THREADS) count_last_kernel(const LastParams
           }
           m[j] = x;
         }
-        u64 cur = m[0], base = (wb + lane) * 64;
-        u32 left = 3;
+        // the eight 32-bit halves in vertex order: half k covers vertices
+        // base0 + (k / 2) * 2048 + (k % 2) * 32 ..
+        u32 hm[7];
+#pragma unroll
+        for (int k = 0; k < 7; k++) hm[k] = (u32)(m[(k + 1) >> 1] >> (((k + 1) & 1) * 32));
+        u32 cur = (u32)m[0], k = 0, c32 = 0;
+        const u32 base0 = (u32)((wb + lane) * 64);
         for (;;) {
-          while (!cur && left) {  // next word of the four
-            cur = m[1];
-            m[1] = m[2];
-            m[2] = m[3];
-            base += 32 * 64;
-            left--;
+          while (!cur && k < 7) {  // next half of the four words
+            cur = hm[0];
+#pragma unroll
+            for (int t = 0; t < 6; t++) hm[t] = hm[t + 1];
+            k++;
           }
           if (!cur) break;
-          const u64 h = last_hash(lp, sw, pre, (u32)(base + (__ffsll((long long)cur) - 1)));
+          const u32 z = base0 + (k >> 1) * 2048 + (k & 1) * 32 + (__ffs(cur) - 1);
+          const u64 h = last_hash(lp, sw, pre, z);
           cur &= cur - 1;
-          cnt++;
+          c32++;
           hs += h;
           hx ^= h;
         }
+        cnt += c32;
       }
       continue;
     }

@@ -190,11 +190,17 @@ __device__ __forceinline__ u32 la_degsum(const BfsParams &p, u32 q, u32 v, u32 g
   u32 s = 0, r = 0;
   const u32 n1 = p.n + 1;
   const u64 gw = (u64)p.G * NW;
+  // the union's transitions of a state are ordered by label, so the label's
+  // out-degree of v is read once for all its targets
+  u32 last_l = 0xFFFFFFFFu, d = 0;
   for (u32 t = p.la_out_begin[q]; t < p.la_out_begin[q + 1]; t++) {
     const u32 l = p.la_trans[t] & 0xFFFFu;
     if (l >= p.L) continue;
-    const u32 *off = p.out_off + (u64)l * n1 + v;
-    const u32 d = __ldg(off + 1) - __ldg(off);
+    if (l != last_l) {
+      const u32 *off = p.out_off + (u64)l * n1 + v;
+      d = __ldg(off + 1) - __ldg(off);
+      last_l = l;
+    }
     const u64 *mk = p.la_mask + t * gw + (u64)g * NW;
     u32 c = 0;
 #pragma unroll
@@ -884,16 +890,11 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
       const u64 base = ((u64)q2 * n + w) * wpv + lane_off;
       u64 vis[PER];
       load_vis<PER>(p.vis + base, lane_on && any, vis);
-      bool full = true;
-#pragma unroll
-      for (int k = 0; k < PER; k++) full &= vis[k] == ~0ull;
-      const u32 fb = __ballot_sync(FULL_MASK, full);
-      const bool work = any && (fb & sg_mask) != sg_mask;
-      if (!__any_sync(FULL_MASK, work)) continue;
       u64 acc[PER];
 #pragma unroll
       for (int k = 0; k < PER; k++) acc[k] = 0;
-      if (work) {
+      // the in-rows' gathers into acc
+      auto gather_all = [&]() {
         for (u32 j = gb; j < ge; j++) {
           const u32 l = p.q.in_label[j];
           const u32 from = p.q.in_from[j] & active;
@@ -914,6 +915,31 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
         }
         words += (li == 0);
         bytes += (li == 0) ? gword : 0;
+      };
+      // whether every lane of the sub-warp's vertex is visited; a warp-wide
+      // ballot, so every lane of the warp must call it
+      auto all_visited = [&]() {
+        bool full = true;
+#pragma unroll
+        for (int k = 0; k < PER; k++) full &= vis[k] == ~0ull;
+        return (__ballot_sync(FULL_MASK, full) & sg_mask) == sg_mask;
+      };
+      bool work;
+      if constexpr (EARLY) {
+        // the gathers stop early on the visited words: read them first
+        const bool allv = all_visited();
+        work = any && !allv;
+        if (!__any_sync(FULL_MASK, work)) continue;
+        if (work) gather_all();
+      } else {
+        // the gathers do not read the visited words, so they are issued while
+        // those are in flight (a vertex whose lanes turn out all visited
+        // gathered for nothing: rare where many lanes never reach anything)
+        if (!__any_sync(FULL_MASK, any)) continue;
+        if (any) gather_all();
+        const bool allv = all_visited();
+        work = any && !allv;
+        if (!__any_sync(FULL_MASK, work)) continue;
       }
       pull_finish<NW, PER>(p, app, FB, nlist, nxt, q2, w, stamp, li, lane_on && work, my_g, ((vh >> q2) & 1u) != 0,
                            vis, acc);
