@@ -294,8 +294,11 @@ __global__ void digest_rows(const ColPtrs cols, u32 arity, u64 n, u64 *__restric
 constexpr u32 LAST_CHUNK = 256;
 constexpr u32 DENSE_WORDS = 2048;
 
+constexpr u64 ITEM_BLOCK = 16;  // consecutive items a warp takes at a time
+
 struct LastParams {
   StepParams p;
+  unsigned long long *cursor;    // next unclaimed item (zero at launch)
   const uint8_t *which;          // generating constraint per tuple, or DENSE
   const u32 *cnt;                // its row length
   const u64 *coff;               // exclusive scan of the tuples' item counts
@@ -342,33 +345,59 @@ __global__ void __launch_bounds__(CL_THREADS) count_last_kernel(const LastParams
   __shared__ LastWarp s_warp[CL_WARPS];
   const StepParams &p = lp.p;
   LastWarp &sw = s_warp[threadIdx.x >> 5];
-  const u64 warp = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
   const u32 lane = lane_id();
   u64 cnt = 0, hs = 0, hx = 0;
-  for (u64 t = warp; t < lp.items; t += nwarps) {
-    // the tuple of item t: the largest i with coff[i] <= t
-    u64 lo = 0, hi = lp.nT;
-    while (hi - lo > 1) {
-      const u64 mid = (lo + hi) >> 1;
-      if (lp.coff[mid] <= t)
-        lo = mid;
-      else
-        hi = mid;
+  // Warps take blocks of ITEM_BLOCK consecutive items from a cursor: the
+  // tuple of a block's first item is found by one binary search over coff,
+  // and a tuple's rows are looked up once for all its items in the block.
+  u64 i = 0, cur_beg = 0, nxt_beg = 0, t = 0, te = 0;
+  u32 gen = 0;
+  u64 pre = 0;
+  for (;;) {
+    if (t == te) {  // next block
+      u64 tb = 0;
+      if (lane == 0) tb = atomicAdd(lp.cursor, (unsigned long long)ITEM_BLOCK);
+      tb = __shfl_sync(FULL_MASK, tb, 0);
+      if (tb >= lp.items) break;
+      t = tb;
+      te = min(lp.items, tb + ITEM_BLOCK);
+      // the tuple of item t: the largest i with coff[i] <= t
+      u64 lo = 0, hi = lp.nT;
+      while (hi - lo > 1) {
+        const u64 mid = (lo + hi) >> 1;
+        if (lp.coff[mid] <= t)
+          lo = mid;
+        else
+          hi = mid;
+      }
+      i = lo;
+      cur_beg = lp.coff[i];
+      nxt_beg = i + 1 < lp.nT ? lp.coff[i + 1] : ~0ull;
+      gen = 0xFFFFFFFFu;  // rows not looked up yet
     }
-    const u64 i = lo;
-    const u32 gen = lp.which[i];
-    const u32 c = (u32)(t - lp.coff[i]);
-    __syncwarp();  // the previous item's readers are done
-    // rows of the tuple's constraints (lane k looks up constraint k), bound values
-    if (lane < p.nc) sw.bits[lane] = lookup(p.c[lane].rows, p.c[lane].col[i], &sw.row[lane], &sw.len[lane]);
-    if (lane < lp.arity) sw.vals[lane] = lp.dcol[lane] ? lp.dcol[lane][i] : 0u;
-    __syncwarp();
-    u64 pre = 0;
-    if (lp.newpos >= 2) {
-      pre = splitmix64(((u64)sw.vals[0] << 32) | (u64)sw.vals[1]);
-      for (u32 v = 2; v < lp.newpos; v++) pre = splitmix64(pre ^ (u64)sw.vals[v]);
+    if (t >= nxt_beg) {  // the next tuple with items (tuples without items are skipped)
+      do {
+        ++i;
+        cur_beg = nxt_beg;
+        nxt_beg = i + 1 < lp.nT ? lp.coff[i + 1] : ~0ull;
+      } while (t >= nxt_beg);
+      gen = 0xFFFFFFFFu;
     }
+    if (gen == 0xFFFFFFFFu) {
+      gen = lp.which[i];
+      __syncwarp();  // the previous tuple's readers are done
+      // rows of the tuple's constraints (lane k looks up constraint k), bound values
+      if (lane < p.nc) sw.bits[lane] = lookup(p.c[lane].rows, p.c[lane].col[i], &sw.row[lane], &sw.len[lane]);
+      if (lane < lp.arity) sw.vals[lane] = lp.dcol[lane] ? lp.dcol[lane][i] : 0u;
+      __syncwarp();
+      pre = 0;
+      if (lp.newpos >= 2) {
+        pre = splitmix64(((u64)sw.vals[0] << 32) | (u64)sw.vals[1]);
+        for (u32 v = 2; v < lp.newpos; v++) pre = splitmix64(pre ^ (u64)sw.vals[v]);
+      }
+    }
+    const u32 c = (u32)(t - cur_beg);
+    t++;
     if (gen == DENSE) {
       // words w0 + lane + 32 j of the AND, four per round; a lane walks the
       // set bits of its four words in one loop, so that lanes wait for the
@@ -400,7 +429,7 @@ __global__ void __launch_bounds__(CL_THREADS) count_last_kernel(const LastParams
           while (!cur && k < 7) {  // next half of the four words
             cur = hm[0];
 #pragma unroll
-            for (int t = 0; t < 6; t++) hm[t] = hm[t + 1];
+            for (int r = 0; r < 6; r++) hm[r] = hm[r + 1];
             k++;
           }
           if (!cur) break;
@@ -747,7 +776,7 @@ struct Engine {
     if ((rc = cuda(exclusive_scan_u32_to_u64(nch.p, coff.p, T.n, small.p + 4, tmp.p, st), "scan"))) return rc;
     u64 items = 0, got = 0;
     if ((rc = cuda(cudaMemcpyAsync(&items, small.p + 4, 8, cudaMemcpyDeviceToHost, st), "copy")) ||
-        (rc = cuda(cudaMemsetAsync(small.p + 5, 0, 8, st), "memset")) || (rc = cuda(cudaStreamSynchronize(st), "sync")))
+        (rc = cuda(cudaMemsetAsync(small.p + 5, 0, 16, st), "memset")) || (rc = cuda(cudaStreamSynchronize(st), "sync")))
       return rc;
     LastParams lp;
     std::memset(&lp, 0, sizeof(lp));
@@ -761,6 +790,7 @@ struct Engine {
     lp.newpos = (u32)order[k];
     for (uint32_t v = 0; v < n_vars; v++) lp.dcol[v] = pos[v] < k ? T.cols[pos[v]].p : nullptr;
     lp.acc = small.p;
+    lp.cursor = reinterpret_cast<unsigned long long *>(small.p + 6);
     const double t0 = host_seconds();
     if (items) {
       const u64 warps = std::min<u64>(items, 152ull * 64);
