@@ -494,7 +494,7 @@ int eval_rpq(rpq_ctx *ctx, const rpq_graph *gr, const rpq_query *qr, const std::
     p.force = force;
     p.alpha = ctx->alpha;
     p.pull_dynamic = ctx->pull_dynamic;
-  p.lane_by_source = ctx->lane_by_source;
+    p.lane_by_source = ctx->lane_by_source;
     p.time_limit_ns = ctx->time_limit_ns;
     p.q = qd;
 
