@@ -329,7 +329,12 @@ typedef struct {
  * means no constraint.  Every variable must occur in some atom, and the
  * atoms must connect all variables.  restrict0 (may be NULL) limits
  * variable 0 to the listed vertices -- a batch of the full query.  Rows are
- * n_vars-tuples in declaration order.  flags as for run_rpq.
+ * n_vars-tuples in declaration order.  flags as for run_rpq.  Variables are
+ * bound one at a time (values of variable 0 in batches of 4,096); each atom
+ * is evaluated from the distinct values its bound end takes, and its long
+ * rows are also held as bitsets over the vertices (option
+ * "crpq_bitset_frac").  With RPQ_COUNT_ONLY the last variable is bound,
+ * counted and digested in one pass, without materializing tuples.
  * Errors: INVALID_ARG, OUT_OF_BUDGET, CUDA, TIMEOUT. */
 int run_crpq(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_vars, const int32_t *var_label, const crpq_atom *atoms,
              uint32_t n_atoms, const uint32_t *restrict0, uint32_t n_restrict0, uint32_t flags,
