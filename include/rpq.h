@@ -333,7 +333,8 @@ typedef struct {
  * bound one at a time (values of variable 0 in batches of 4,096); each atom
  * is evaluated from the distinct values its bound end takes, and its long
  * rows are also held as bitsets over the vertices (option
- * "crpq_bitset_frac").  With RPQ_COUNT_ONLY the last variable is bound,
+ * "crpq_bitset_frac").  With RPQ_COUNT_ONLY the last variable (unless an
+ * atom loops on it) is bound,
  * counted and digested in one pass, without materializing tuples.
  * Errors: INVALID_ARG, OUT_OF_BUDGET, CUDA, TIMEOUT. */
 int run_crpq(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_vars, const int32_t *var_label, const crpq_atom *atoms,
