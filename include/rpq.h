@@ -334,8 +334,8 @@ typedef struct {
  * is evaluated from the distinct values its bound end takes, and its long
  * rows are also held as bitsets over the vertices (option
  * "crpq_bitset_frac").  With RPQ_COUNT_ONLY the last variable (unless an
- * atom loops on it) is bound,
- * counted and digested in one pass, without materializing tuples.
+ * atom loops on it) is bound, counted and digested in one pass, without
+ * materializing tuples.
  * Errors: INVALID_ARG, OUT_OF_BUDGET, CUDA, TIMEOUT. */
 int run_crpq(rpq_ctx *ctx, const rpq_graph *g, uint32_t n_vars, const int32_t *var_label, const crpq_atom *atoms,
              uint32_t n_atoms, const uint32_t *restrict0, uint32_t n_restrict0, uint32_t flags,
