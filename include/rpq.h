@@ -113,6 +113,9 @@ int rpq_set_stream(rpq_ctx *ctx, void *cuda_stream);
  *                  below the bottom-up bytes (default 16)
  *   "lane_alpha"   the same for lane-mode launches (one automaton per lane;
  *                  default 2)
+ *   "pull_dynamic" 1 (default): bottom-up levels take chunks of 32 vertices
+ *                  from a shared cursor; 0: warp k takes chunks k, k + warps,
+ *                  ... (same results)
  *   "lane_by_source" 1 (default): bottom-up levels of lane-mode launches
  *                  whose union automaton has at most 8 states gather a
  *                  neighbour's frontier words once per (label, source state)
