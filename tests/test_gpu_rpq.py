@@ -341,3 +341,21 @@ def test_edgeless_start_vertices_skipped(ctx, regex, flags):
     assert st["product_edges"] == want.W and st["product_vertices"] == want.N
     if flags == "rows":
         assert np.array_equal(rpq.fetch_pairs(r), want.rows)
+
+
+def test_static_chunk_order_matches_oracle():
+    """pull_dynamic = 0: bottom-up levels take their 32-vertex chunks
+    round-robin instead of from the cursor; every level bottom-up, hubs in
+    both directions -- the rows and the work counter equal the oracle's."""
+    c = rpq.Context(device=0)
+    rpq.rpq_set_option(c, "pull_dynamic", 0)
+    n = 4000
+    rs, rd, rl = synth.random_graph(n, 6000, 3, seed=79)
+    src = np.concatenate([np.arange(1, 3001), np.ones(2500), rs]).astype(np.uint32)
+    dst = np.concatenate([np.zeros(3000), np.arange(1500, 4000), rd]).astype(np.uint32)
+    lab = np.concatenate([np.zeros(3000), np.ones(2500), rl]).astype(np.uint16)
+    g = rpq.load_graph(c, n, 3, src, dst, lab)
+    og = oracle.Graph(n, 3, src, dst, lab)
+    sample = np.arange(0, n, 7, dtype=np.uint32)
+    for regex in ("a.b", "(a|b)*", "(a.b)+"):
+        check(c, g, og, regex, sources=sample, mode=MODES["pull"])
