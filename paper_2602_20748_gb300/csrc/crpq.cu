@@ -14,12 +14,19 @@
 //     end (reversed language over in-edges) from the distinct y values.  Both
 //     give, per bound value, a sorted row of admissible values for the new
 //     variable.  A self-loop atom x -rho-> x is checked once x is bound.
+//     Rows are referenced where the emission wrote them; a row holding at
+//     least crpq_bitset_frac of the vertices is also written as a bitset over
+//     the vertices (a direct-address membership table).
 //   * Binding a variable: per partial tuple, the constraint with the shortest
-//     row generates the candidates (the smallest-first intersection of worst
-//     case optimal joins); every other constraint is a membership test by
-//     binary search in its sorted row; vertex labels are tested too.  The
-//     surviving (tuple, value) pairs are compacted into the next table.
-//     Candidates are processed in slices of bounded size.
+//     listed row generates the candidates (the smallest-first intersection of
+//     worst case optimal joins); every other constraint is a membership test,
+//     one load in a bitset or a binary search in a sorted row; vertex labels
+//     are tested too.  The surviving (tuple, value) pairs are compacted into
+//     the next table.  Candidates are processed in slices of bounded size.
+//   * The last variable of a count-only query (no self-loop on it) is bound,
+//     counted and digested in one pass (count_last_kernel); its long rows are
+//     kept as bitsets only, and a tuple whose rows are all bitsets is
+//     extended by a word-by-word AND of them.
 //   * Complete tuples of a batch are sorted lexicographically in declaration
 //     order (stable LSD passes over the columns) and digested.
 #include <algorithm>
