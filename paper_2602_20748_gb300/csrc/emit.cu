@@ -24,7 +24,9 @@
 // position.  Whenever a row's current 128-byte-aligned chunk of the output is
 // complete, the warp stores it: four rows per store instruction, eight lanes
 // per row, 16 bytes per lane -- whole sectors, with only the first and last
-// chunk of a row stored word by word where they are partial.
+// chunk of a row stored word by word where they are partial.  Lanes given a
+// bitset (lane_slot) also store their transposed tile words there, 32 bytes
+// per lane per batch of 256 vertices, and with keep_lists = 0 write no list.
 #include <algorithm>
 
 #include "device_common.cuh"
