@@ -704,6 +704,12 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
   const u64 gword = 8ull * NW * p.G;  // bytes of the G words of one (state, vertex)
   u64 edges = 0, words = 0, bytes = 0;
   Appender app;
+  // lane mode by source state: this warp's per-target accumulators
+  u64 *lane_acc = nullptr;
+  if constexpr (AM == AM_LANE) {
+    __shared__ u64 s_lane_acc[BFS_THREADS / 32][LANE_SRC_Q * 2 * 32];
+    lane_acc = s_lane_acc[threadIdx.x >> 5];
+  }
 
   // A warp takes 32 consecutive vertices at a time: lane i first finds, with
   // coalesced reads of the in-row offsets, the target states into which
@@ -788,8 +794,7 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
         // ORed over the in-edges, then masked into every target taking a
         // transition from them (accumulated per lane in shared memory); the
         // per-target order gathers each (s, v) once per target instead.
-        __shared__ u64 s_lane_acc[BFS_THREADS / 32][LANE_SRC_Q * 2 * 32];
-        u64 *sacc = s_lane_acc[threadIdx.x >> 5];  // [q2][k][lane]
+        u64 *sacc = lane_acc;  // [q2][k][lane]
         u32 wmask = 0;  // targets with lanes to find (uniform within the sub-warp)
         for (u32 q2 = 0; q2 < Q; q2++) {
           const bool any = wv && ((vq >> q2) & 1u);
@@ -954,7 +959,107 @@ __device__ void pull_level(const BfsParams &p, int lp, u32 cur, u32 nxt, u32 act
     }
   }
 
-  if (chunked) {
+  bool chunks_done = !chunked;
+  if constexpr (AM == AM_LANE) {
+    if (chunked && p.lane_by_source && Q <= LANE_SRC_Q) {
+      // Long in-rows by source state: an item is a chunk of a label's long
+      // in-rows; its frontier words are gathered once per active source
+      // state with a transition on that label and masked into every target
+      // taking one (the light rows' scheme, see above).
+      u64 lact = 0;  // labels with an active transition
+      for (u32 j = 0; j < p.q.in_begin[Q]; j++)
+        if ((p.q.in_from[j] & active) && p.q.in_label[j] < p.L) lact |= 1ull << p.q.in_label[j];
+      for (;;) {
+        u64 it = 0;
+        if (lane == 0) it = atomicAdd(&p.ctl->heavy_cursor[cur], 1ull);
+        it = __shfl_sync(FULL_MASK, it, 0);
+        u64 acc_base = 0, ci = 0;
+        u32 ls = 0;
+        bool found = false;
+        for (u64 lb = lact; lb; lb &= lb - 1) {
+          const u32 l = __ffsll((long long)lb) - 1;
+          const u64 cnt = p.hchunk_off[l + 1] - p.hchunk_off[l];
+          if (it < acc_base + cnt) {
+            found = true;
+            ls = l;
+            ci = p.hchunk_off[l] + (it - acc_base);
+            break;
+          }
+          acc_base += cnt;
+        }
+        if (!found) break;
+        const u32 *rec = p.hchunk + 3 * ci;
+        const u32 w = __ldg(rec), beg = __ldg(rec + 1), end = __ldg(rec + 2);
+        // targets with a transition on ls from an active state and lanes not
+        // yet visited (the whole warp works on vertex w)
+        u32 wmask = 0;
+        for (u32 q2 = 0; q2 < Q; q2++) {
+          bool has = false;
+          for (u32 j = p.q.in_begin[q2]; j < p.q.in_begin[q2 + 1]; j++)
+            has |= p.q.in_label[j] == ls && (p.q.in_from[j] & active) != 0;
+          u64 vis[PER];
+          load_vis<PER>(p.vis + ((u64)q2 * n + w) * wpv + lane_off, lane_on && has, vis);
+          bool full = true;
+#pragma unroll
+          for (int k = 0; k < PER; k++) {
+            full &= vis[k] == ~0ull;
+            lane_acc[(q2 * PER + k) * 32 + lane] = 0;
+          }
+          const u32 fbal = __ballot_sync(FULL_MASK, full);  // every lane, before the test
+          if (has && fbal != FULL_MASK) wmask |= 1u << q2;
+        }
+        if (!wmask) continue;
+        u32 S = 0;
+        for (u32 q2 = 0; q2 < Q; q2++)
+          if ((wmask >> q2) & 1u)
+            for (u32 j = p.q.in_begin[q2]; j < p.q.in_begin[q2 + 1]; j++)
+              if (p.q.in_label[j] == ls) S |= p.q.in_from[j] & active;
+        // the sub-warps take consecutive slices of the chunk's edges
+        const u32 len = end - beg, per = (len + VPW - 1) / VPW;
+        const u32 sb = beg + min(len, sg * per), se = beg + min(len, (sg + 1) * per);
+        u64 ex_tot = 0, gat_tot = 0;
+        for (; S; S &= S - 1) {
+          const u32 st = __ffs(S) - 1;
+          u64 g[PER], none[PER];
+#pragma unroll
+          for (int k = 0; k < PER; k++) g[k] = none[k] = 0;
+          u32 gat = 0;
+          ex_tot += gather_row<NW, PER, false, false>(p, F, bits, 1u << st, sb, se, lane_off, lane_on, sg_mask,
+                                                      none, g, gat, nullptr);
+          gat_tot += gat;
+          for (u32 o = SW; o < 32; o <<= 1) {
+#pragma unroll
+            for (int k = 0; k < PER; k++) g[k] |= __shfl_xor_sync(FULL_MASK, g[k], o);
+          }
+          for (u32 q2 = 0; q2 < Q; q2++) {
+            if (!((wmask >> q2) & 1u)) continue;
+            for (u32 j = p.q.in_begin[q2]; j < p.q.in_begin[q2 + 1]; j++) {
+              if (p.q.in_label[j] != ls || !((p.q.in_from[j] >> st) & 1u)) continue;
+              const u64 *mk = p.la_mask + (u64)p.la_in_t[(u64)j * Q + st] * wpv + lane_off;
+#pragma unroll
+              for (int k = 0; k < PER; k++) lane_acc[(q2 * PER + k) * 32 + lane] |= g[k] & __ldg(mk + k);
+            }
+          }
+        }
+        const u64 ex_all = warp_sum((u64)(li == 0 ? ex_tot : 0));
+        const u64 gat_all = warp_sum((u64)(li == 0 ? gat_tot : 0));
+        edges += (lane == 0) ? ex_all : 0;
+        bytes += (lane == 0) ? 12 + ex_all * (4 + (bits ? 4 : 0)) + gat_all * gword : 0;
+        for (u32 q2 = 0; q2 < Q; q2++) {
+          if (!((wmask >> q2) & 1u)) continue;  // uniform across the warp
+          u64 vis[PER], acc[PER];
+          load_vis<PER>(p.vis + ((u64)q2 * n + w) * wpv + lane_off, lane_on, vis);
+#pragma unroll
+          for (int k = 0; k < PER; k++) acc[k] = lane_acc[(q2 * PER + k) * 32 + lane];
+          words += (lane == 0);
+          bytes += (lane == 0) ? gword : 0;
+          pull_finish<NW, PER>(p, app, FB, nlist, nxt, q2, w, stamp, li, lane_on && sg == 0, my_g, true, vis, acc);
+        }
+      }
+      chunks_done = true;
+    }
+  }
+  if (!chunks_done) {
     for (;;) {
       u64 it = 0;
       if (lane == 0) it = atomicAdd(&p.ctl->heavy_cursor[cur], 1ull);
