@@ -65,8 +65,8 @@ def parse_args():
     ap.add_argument("--full", action="store_true",
                     help="crpq: also count the whole query (every x value) in one timed call")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: mean arrivals per second")
-    ap.add_argument("--serve-seconds", type=float, default=10.0, help="serve: arrival window (s)")
-    ap.add_argument("--drain", type=float, default=10.0, help="serve: time after the window before cancelling (s)")
+    ap.add_argument("--serve-seconds", type=float, default=20.0, help="serve: arrival window (s)")
+    ap.add_argument("--drain", type=float, default=20.0, help="serve: time after the window before cancelling (s)")
     return ap.parse_args()
 
 
