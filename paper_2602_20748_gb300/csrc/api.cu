@@ -1963,12 +1963,36 @@ static int lane_launch(rpq_ctx *ctx, const rpq_graph *gr, const std::vector<Lane
   int rc = ensure_workspace(ctx, words, lists, claims, G * K);
   if (rc) return rc;
   Workspace &w = ctx->ws;
+  // the union's transitions grouped by (state, label) -- consecutive in
+  // `trans` -- with the OR of each group's lane masks (the commit counts a
+  // group's lanes with one mask)
+  std::vector<uint16_t> grp_begin(Q + 1, 0);
+  std::vector<uint32_t> grp;
+  std::vector<u64> gmask;
+  for (uint32_t q = 0; q < Q; q++) {
+    grp_begin[q] = (uint16_t)grp.size();
+    for (uint32_t t = out_begin[q]; t < out_begin[q + 1];) {
+      const uint32_t l = trans[t] & 0xFFFFu;
+      const size_t base = gmask.size();
+      gmask.resize(base + GW, 0);
+      uint32_t c = 0;
+      for (; t < out_begin[q + 1] && (trans[t] & 0xFFFFu) == l; t++, c++)
+        for (uint64_t k = 0; k < GW; k++) gmask[base + k] |= mask[(size_t)t * GW + k];
+      grp.push_back(l | (c << 16));
+    }
+  }
+  grp_begin[Q] = (uint16_t)grp.size();
+  if (grp.empty()) {  // no transition: keep the buffers non-empty
+    grp.push_back(0xFFFFu);
+    gmask.assign(GW, 0);
+  }
   // one upload buffer for the tables
   const size_t b_ob = (Q + 1) * 2, b_tr = std::max<size_t>(1, T) * 4, b_it = in_t.size() * 2;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t o_mask = 0, o_fin = o_mask + al(mask.size() * 8), o_emp = o_fin + al(fin.size() * 8),
                o_ob = o_emp + al(empty_q.size() * 8), o_tr = o_ob + al(b_ob), o_it = o_tr + al(b_tr),
-               o_ls = o_it + al(b_it), tbytes = o_ls + al(24ull * G * K);
+               o_gm = o_it + al(b_it), o_gb = o_gm + al(gmask.size() * 8), o_gr = o_gb + al(grp_begin.size() * 2),
+               o_ls = o_gr + al(grp.size() * 4), tbytes = o_ls + al(24ull * G * K);
   std::vector<unsigned char> host(o_ls);
   std::memcpy(host.data() + o_mask, mask.data(), mask.size() * 8);
   std::memcpy(host.data() + o_fin, fin.data(), fin.size() * 8);
@@ -1976,6 +2000,9 @@ static int lane_launch(rpq_ctx *ctx, const rpq_graph *gr, const std::vector<Lane
   std::memcpy(host.data() + o_ob, out_begin.data(), b_ob);
   if (T) std::memcpy(host.data() + o_tr, trans.data(), b_tr);
   std::memcpy(host.data() + o_it, in_t.data(), b_it);
+  std::memcpy(host.data() + o_gm, gmask.data(), gmask.size() * 8);
+  std::memcpy(host.data() + o_gb, grp_begin.data(), grp_begin.size() * 2);
+  std::memcpy(host.data() + o_gr, grp.data(), grp.size() * 4);
   unsigned char *dt = nullptr;
   if ((rc = dalloc(ctx, &dt, tbytes))) return rc;
   cudaStream_t st = ctx->stream;
@@ -2027,6 +2054,9 @@ static int lane_launch(rpq_ctx *ctx, const rpq_graph *gr, const std::vector<Lane
   p.la_trans = reinterpret_cast<const unsigned int *>(dt + o_tr);
   p.la_mask = reinterpret_cast<const unsigned long long *>(dt + o_mask);
   p.la_in_t = reinterpret_cast<const unsigned short *>(dt + o_it);
+  p.la_grp_begin = reinterpret_cast<const unsigned short *>(dt + o_gb);
+  p.la_grp = reinterpret_cast<const unsigned int *>(dt + o_gr);
+  p.la_gmask = reinterpret_cast<const unsigned long long *>(dt + o_gm);
   EmitParams ep{};
   ep.vis = w.vis;
   ep.n = n;

@@ -187,27 +187,25 @@ __device__ __forceinline__ u32 degsum(const BfsParams &p, const QueryDesc &qd, u
 template <int NW>
 __device__ __forceinline__ u32 la_degsum(const BfsParams &p, u32 q, u32 v, u32 g, const Word<NW> &m, u64 &W,
                                          u32 *rows) {
+  // per (state, label) group: its transitions' lanes are disjoint, so the
+  // lanes of m taking any of them are popc(m & OR of their masks); the
+  // degree sum and row count still count every transition
   u32 s = 0, r = 0;
   const u32 n1 = p.n + 1;
   const u64 gw = (u64)p.G * NW;
-  // the union's transitions of a state are ordered by label, so the label's
-  // out-degree of v is read once for all its targets
-  u32 last_l = 0xFFFFFFFFu, d = 0;
-  for (u32 t = p.la_out_begin[q]; t < p.la_out_begin[q + 1]; t++) {
-    const u32 l = p.la_trans[t] & 0xFFFFu;
+  for (u32 gi = p.la_grp_begin[q]; gi < p.la_grp_begin[q + 1]; gi++) {
+    const u32 e = p.la_grp[gi];
+    const u32 l = e & 0xFFFFu, c = e >> 16;
     if (l >= p.L) continue;
-    if (l != last_l) {
-      const u32 *off = p.out_off + (u64)l * n1 + v;
-      d = __ldg(off + 1) - __ldg(off);
-      last_l = l;
-    }
-    const u64 *mk = p.la_mask + t * gw + (u64)g * NW;
-    u32 c = 0;
+    const u32 *off = p.out_off + (u64)l * n1 + v;
+    const u32 d = __ldg(off + 1) - __ldg(off);
+    const u64 *mk = p.la_gmask + gi * gw + (u64)g * NW;
+    u32 lanes = 0;
 #pragma unroll
-    for (int k = 0; k < NW; k++) c += __popcll(m.w[k] & __ldg(mk + k));
-    W += (u64)c * d;
-    s += d;
-    r++;
+    for (int k = 0; k < NW; k++) lanes += __popcll(m.w[k] & __ldg(mk + k));
+    W += (u64)lanes * d;
+    s += c * d;
+    r += c;
   }
   *rows = r;
   return s;

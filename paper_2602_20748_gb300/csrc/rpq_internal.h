@@ -184,6 +184,13 @@ struct BfsParams {
   const unsigned int *la_trans;
   const unsigned long long *la_mask;
   const unsigned short *la_in_t;
+  // the union's transitions grouped by (state, label): groups la_grp_begin[q]
+  // .. la_grp_begin[q + 1] of state q, la_grp[i] = label | (transitions << 16),
+  // la_gmask[i * G * NW ..] the OR of the group's lane masks (a lane's own DFA
+  // takes at most one transition per (state, label), so the masks are disjoint)
+  const unsigned short *la_grp_begin;
+  const unsigned int *la_grp;
+  const unsigned long long *la_gmask;
   BfsCtl *ctl;
   unsigned int stamp_base;     // claim stamps continue across launches
   unsigned int nblocks;
